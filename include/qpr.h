@@ -1,0 +1,165 @@
+/*
+ * qpr.h -- C ABI of the GB300 quantum PageRank solver.
+ *
+ * The solver integrates the quantum-stochastic-walk Lindblad equation
+ * (Eq. 1 / Eq. S7 of "TensorFlow Solver for Quantum PageRank in Large-Scale
+ * Networks")
+ *
+ *   d rho/dt = -(1-omega) i [H, rho]
+ *              + omega sum_ij ( L_ij rho L_ij^dag - 1/2 {L_ij^dag L_ij, rho} ),
+ *   L_ij = sqrt(G_ij) |i><j|,
+ *
+ * directly on the N x N complex density matrix with classical RK4
+ * (Supplementary Note 2, fourth-order scheme), never forming the N^2 x N^2
+ * superoperator of Eq. 2. H and G come from a weighted directed edge list
+ * (Supplementary Note 1): A_ij = w for a link j -> i, H_ij = -max(A_ij, A_ji)
+ * (Eq. S6), G = alpha S + (1 - alpha) F with S the column-normalised
+ * adjacency and F_ij = 1/(N-1) off the diagonal (Eq. S2, Eq. S4).
+ *
+ * Conventions shared by every entry point:
+ *   - A density matrix is N x N complex128, row-major, (re, im) interleaved
+ *     (the layout of a C99 `double complex` array or a torch.complex128
+ *     tensor). A rho argument may point to device memory or to host memory
+ *     (pageable or pinned); the library detects which and copies as needed.
+ *   - Every input density matrix is first made exactly Hermitian,
+ *     (rho + rho^dag)/2, and divided by its real trace; every output density
+ *     matrix has unit real trace.
+ *   - All work runs on the context's CUDA stream (qpr_options.cuda_stream, or
+ *     a stream the context creates). The calls return when their results are
+ *     complete and visible to the host.
+ *   - Entry points never abort and never trap. They return a status; the
+ *     message of the last failure is qpr_last_error(ctx). After a CUDA error
+ *     the context is poisoned: every later call returns QPR_E_CUDA.
+ *   - Memory passed in is owned by the caller; the context owns its own
+ *     device buffers until qpr_destroy.
+ */
+#ifndef QPR_H
+#define QPR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QPR_API __attribute__((visibility("default")))
+#else
+#define QPR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qpr_ctx qpr_ctx;
+
+typedef enum {
+    QPR_OK = 0,
+    QPR_E_ARG = 1,           /* invalid argument (null pointer, dt <= 0, alpha/omega outside [0,1], ...) */
+    QPR_E_GRAPH = 2,         /* invalid edge list (index outside [0,n), negative or non-finite weight) */
+    QPR_E_CUDA = 3,          /* CUDA runtime error; the context is poisoned */
+    QPR_E_OOM = 4,           /* device or host allocation failed */
+    QPR_E_UNSTABLE = 5,      /* dt outside the RK4 stability estimate (qpr_evolve only) */
+    QPR_E_NOT_CONVERGED = 6, /* max_steps reached before the residual fell below tol */
+    QPR_E_TIMEOUT = 7,       /* a device-side wait gave up */
+    QPR_E_NONFINITE = 8      /* a NaN or Inf appeared in the state or the residual */
+} qpr_status;
+
+enum { QPR_FP64 = 0, QPR_SPLIT_BF16 = 1 };
+/* Diagonal of H. Eq. S6 prints H_ii = -outDeg(i); the symmetrised-adjacency
+ * form with a zero diagonal is the default because the printed diagonal
+ * makes RK4 at dt = 0.01 unstable on heavy-tailed weighted graphs. */
+enum { QPR_HDIAG_ZERO = 0, QPR_HDIAG_NEG_OUTDEG = 1 };
+/* Column of S for a node without out-links: F's column, 1/(N-1) off the
+ * diagonal (default), or the uniform column 1/N. */
+enum { QPR_DANGLING_F = 0, QPR_DANGLING_UNIFORM = 1 };
+
+typedef struct {
+    int32_t precision;   /* QPR_FP64 (default) */
+    int32_t h_diag;      /* QPR_HDIAG_ZERO (default) or QPR_HDIAG_NEG_OUTDEG */
+    int32_t dangling;    /* QPR_DANGLING_F (default) or QPR_DANGLING_UNIFORM */
+    int32_t graph_steps; /* RK4 steps per captured CUDA graph launch (default 32; 0 = no graphs) */
+    void *cuda_stream;   /* cudaStream_t to run on; NULL = the context creates its own */
+    int32_t device;      /* CUDA device ordinal (default: the current device) */
+    int32_t reserved[7];
+} qpr_options;
+
+typedef struct {
+    int64_t steps;       /* RK4 steps taken (the step index n at which the residual passed) */
+    int64_t substeps_m;  /* dt was split into m equal substeps for stability */
+    double t;            /* integrated time, steps * dt / m */
+    double residual;     /* ||f(rho_n)||_F of the returned state (FP64) */
+    double trace_before; /* Re tr of the unnormalised state before the last division */
+    double seconds;      /* wall time of the call */
+    int32_t converged;   /* 1 if residual < tol */
+    int32_t reserved[3];
+} qpr_stats;
+
+/* Fill *opt with the defaults listed above. */
+QPR_API qpr_status qpr_default_options(qpr_options *opt);
+
+/* Build a solver context from a weighted directed edge list.
+ * n       number of nodes (>= 2; F needs N - 1 > 0, Eq. S2).
+ * m       number of edges (>= 0); edge e is the link src[e] -> dst[e] with
+ *         weight w[e] (w == NULL: unit weights). Host arrays.
+ * alpha   damping of the Google matrix, in [0, 1] (Eq. S4's q).
+ * omega   quantum/classical mixing, in [0, 1] (Eq. 1).
+ * Duplicate links sum their weights; self-loops and zero weights are dropped.
+ * Errors: QPR_E_ARG (n < 2, alpha/omega outside [0,1], null pointers),
+ * QPR_E_GRAPH (index outside [0,n), weight negative or not finite),
+ * QPR_E_OOM, QPR_E_CUDA. On error *out is NULL. */
+QPR_API qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, const int64_t *dst,
+                      const double *w, double alpha, double omega, const qpr_options *opt);
+
+/* Free the context and its device buffers. NULL is ignored. */
+QPR_API void qpr_destroy(qpr_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none). ctx may be NULL
+ * (the message of the last failed qpr_create on this thread). */
+QPR_API const char *qpr_last_error(const qpr_ctx *ctx);
+QPR_API const char *qpr_status_string(qpr_status s);
+
+/* Number of nodes and the estimated spectral spread lambda_max - lambda_min
+ * of H used by the RK4 step-size check. */
+QPR_API int64_t qpr_n(const qpr_ctx *ctx);
+QPR_API double qpr_h_spread(const qpr_ctx *ctx);
+
+/* Largest dt for which the context considers one RK4 step stable: it needs
+ * dt * ((1 - omega) * spread(H) + 2 omega) <= 2.5, a half-disk inside RK4's
+ * stability region. */
+QPR_API double qpr_max_stable_dt(const qpr_ctx *ctx);
+
+/* out = f(rho), one evaluation of the Lindblad right-hand side (Eq. S7) on
+ * the Hermitian part of rho, without trace normalisation. rho and out: N x N
+ * complex128, host or device; they may not alias. */
+QPR_API qpr_status qpr_rhs(qpr_ctx *ctx, const void *rho, void *out);
+
+/* *resid_out = ||f(rho)||_F over all N^2 entries, in FP64, for the
+ * Hermitian part of rho, without trace normalisation. */
+QPR_API qpr_status qpr_residual(qpr_ctx *ctx, const void *rho, double *resid_out);
+
+/* Fixed-step RK4: rho <- the state after `steps` steps of length dt, each
+ * step followed by division by the real trace. rho is read and overwritten
+ * in place (host or device). QPR_E_UNSTABLE if dt exceeds
+ * qpr_max_stable_dt(ctx). steps == 0 returns the normalised input. */
+QPR_API qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps);
+
+/* RK4 from the initial state in rho (for example I/N) until the first step
+ * index n with ||f(rho_n)||_F < tol, or
+ * until max_steps steps were taken. rho_n (unit trace) is written back to
+ * rho. If dt exceeds the stability estimate, each step is split into the
+ * smallest number m of equal substeps that passes; stats->substeps_m
+ * reports m and steps counts substeps.
+ * Returns QPR_OK when converged, QPR_E_NOT_CONVERGED when max_steps was
+ * reached (rho then holds the last state), QPR_E_NONFINITE on NaN/Inf.
+ * out may be NULL. */
+QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int64_t max_steps,
+                            qpr_stats *out);
+
+/* p[i] = Re rho_ii (the probability at node i); p: N doubles, host or
+ * device. rank (nullable): N int64 node indices in descending order of p,
+ * ties to the lower index (the ranking of the main text's airline study). */
+QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPR_H */

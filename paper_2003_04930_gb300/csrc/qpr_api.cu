@@ -1,0 +1,678 @@
+// Host runtime and C ABI of the solver: argument validation, operator
+// assembly (Supplementary Note 1), the RK4 driver with CUDA-graph capture and
+// device-side stop decision, and the host/device pointer handling.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "qpr_internal.cuh"
+
+using qpr::Ctl;
+
+struct qpr_ctx {
+    int device = 0;
+    int64_t n = 0;
+    int np = 0;
+    double alpha = 0.0, omega = 0.0;
+    qpr_options opt{};
+    double spread = 0.0;   // estimated lambda_max - lambda_min of H
+    double cmax = 1.0;     // max column sum of G
+    // device operators
+    double *d_H = nullptr;
+    int *d_sptr = nullptr, *d_scol = nullptr;
+    double *d_sval = nullptr;
+    unsigned char *d_dang = nullptr;
+    double *d_c = nullptr;
+    // device work
+    double *d_state = nullptr;  // y, z, ya, yb: 2 planes each
+    double *d_g = nullptr;
+    double *d_partials = nullptr;
+    int2 *d_pairs = nullptr;
+    Ctl *d_ctl = nullptr;
+    double *d_io = nullptr;     // staging for host density matrices (interleaved)
+    double *d_p = nullptr;      // populations staging
+    Ctl *h_ctl = nullptr;       // pinned
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    qpr::DevOps ops{};
+    qpr::Work work{};
+    std::string err;
+    bool poisoned = false;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const char *kStatusNames[] = {"QPR_OK",         "QPR_E_ARG",           "QPR_E_GRAPH",
+                              "QPR_E_CUDA",     "QPR_E_OOM",           "QPR_E_UNSTABLE",
+                              "QPR_E_NOT_CONVERGED", "QPR_E_TIMEOUT",  "QPR_E_NONFINITE"};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+qpr_status fail(qpr_ctx *ctx, qpr_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+qpr_status cuda_fail(qpr_ctx *ctx, cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, QPR_E_OOM, msg);
+    if (ctx) ctx->poisoned = true;
+    return fail(ctx, QPR_E_CUDA, msg);
+}
+
+#define QPR_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// A pointer the kernels can read directly: device or managed memory.
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Power iteration for the extreme eigenvalues of the symmetric CSR matrix
+// H; returns an estimate of lambda_max - lambda_min (with a 2% margin, and
+// never above the Gershgorin bound).
+double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
+                       const std::vector<double> &val) {
+    if (val.empty()) return 0.0;
+    auto matvec = [&](const std::vector<double> &x, std::vector<double> &y, double shift) {
+        for (int64_t i = 0; i < n; ++i) {
+            double s = -shift * x[i];
+            for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
+            y[i] = s;
+        }
+    };
+    auto dominant = [&](double shift) {
+        std::vector<double> x(n), y(n);
+        for (int64_t i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * sin(0.7 * (double)i + 0.1);
+        double lam = 0.0;
+        for (int it = 0; it < 400; ++it) {
+            double nx = 0.0;
+            for (double v : x) nx += v * v;
+            nx = sqrt(nx);
+            if (nx == 0.0) return 0.0;
+            for (double &v : x) v /= nx;
+            matvec(x, y, shift);
+            double rq = 0.0;
+            for (int64_t i = 0; i < n; ++i) rq += x[i] * y[i];
+            lam = rq;
+            x.swap(y);
+        }
+        return lam;
+    };
+    double gersh = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) r += fabs(val[q]);
+        gersh = std::max(gersh, r);
+    }
+    const double l1 = dominant(0.0);
+    const double l2 = dominant(l1);  // eigenvalue of H - l1 I farthest from 0
+    double spread = fabs(l2) * 1.02 + 1e-12;
+    return std::min(spread, 2.0 * gersh);
+}
+
+qpr_status sync_ctx(qpr_ctx *ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    return QPR_OK;
+}
+
+void enqueue_step(qpr_ctx *ctx) {
+    const qpr::Work &w = ctx->work;
+    const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
+    for (int s = 1; s <= 4; ++s) {
+        qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
+        qpr::launch_stage_fp64(s, ctx->ops, w, ctx->stream);
+    }
+}
+
+qpr_status ensure_graph(qpr_ctx *ctx) {
+    if (ctx->graph || ctx->opt.graph_steps <= 0) return QPR_OK;
+    cudaGraph_t g = nullptr;
+    QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < ctx->opt.graph_steps; ++s) enqueue_step(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->graph_steps = ctx->opt.graph_steps;
+    return QPR_OK;
+}
+
+// Bring a caller density matrix (host or device) into the y planes.
+qpr_status import_rho(qpr_ctx *ctx, const void *rho, double *planes) {
+    const size_t bytes = (size_t)ctx->n * ctx->n * 2 * sizeof(double);
+    const double *src = (const double *)rho;
+    if (!is_device_ptr(rho)) {
+        QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_io, rho, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->d_io;
+    }
+    qpr::launch_import(src, (int)ctx->n, ctx->np, planes, ctx->stream);
+    return QPR_OK;
+}
+
+qpr_status export_rho(qpr_ctx *ctx, const double *planes, int use_scale, void *rho) {
+    const size_t bytes = (size_t)ctx->n * ctx->n * 2 * sizeof(double);
+    if (is_device_ptr(rho)) {
+        qpr::launch_export(planes, (int)ctx->n, ctx->np, ctx->d_ctl, use_scale, (double *)rho, ctx->stream);
+    } else {
+        qpr::launch_export(planes, (int)ctx->n, ctx->np, ctx->d_ctl, use_scale, ctx->d_io, ctx->stream);
+        QPR_CUDA(ctx, cudaMemcpyAsync(rho, ctx->d_io, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return QPR_OK;
+}
+
+qpr_status check_usable(qpr_ctx *ctx) {
+    if (!ctx) return QPR_E_ARG;
+    if (ctx->poisoned) return fail(ctx, QPR_E_CUDA, "context poisoned by an earlier CUDA error: " + ctx->err);
+    return QPR_OK;
+}
+
+// Run RK4 steps until the device sets `done`. Leaves the unnormalised state
+// in y and 1 / tr(y) in ctl->scale.
+qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->max_steps = max_steps;
+    h->tol = tol;
+    h->dt = dt;
+    h->scale = 1.0;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    qpr_status st = ensure_graph(ctx);
+    if (st != QPR_OK) return st;
+    const int chunk = ctx->graph ? ctx->graph_steps : 1;
+    // Each stage-2 gain kernel stops the run once max_steps is reached, so
+    // the loop ends after at most ceil((max_steps + 1) / chunk) launches.
+    for (;;) {
+        if (ctx->graph) {
+            QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        } else {
+            enqueue_step(ctx);
+        }
+        QPR_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+        st = sync_ctx(ctx);
+        if (st != QPR_OK) return st;
+        if (h->done) break;
+        (void)chunk;
+    }
+    return QPR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qpr_status qpr_default_options(qpr_options *opt) {
+    if (!opt) return QPR_E_ARG;
+    memset(opt, 0, sizeof(*opt));
+    opt->precision = QPR_FP64;
+    opt->h_diag = QPR_HDIAG_ZERO;
+    opt->dangling = QPR_DANGLING_F;
+    opt->graph_steps = 32;
+    opt->cuda_stream = nullptr;
+    opt->device = -1;
+    return QPR_OK;
+}
+
+const char *qpr_status_string(qpr_status s) {
+    if ((int)s < 0 || (int)s > 8) return "QPR_E_UNKNOWN";
+    return kStatusNames[(int)s];
+}
+
+const char *qpr_last_error(const qpr_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+int64_t qpr_n(const qpr_ctx *ctx) { return ctx ? ctx->n : 0; }
+double qpr_h_spread(const qpr_ctx *ctx) { return ctx ? ctx->spread : 0.0; }
+
+double qpr_max_stable_dt(const qpr_ctx *ctx) {
+    if (!ctx) return 0.0;
+    const double rate = (1.0 - ctx->omega) * ctx->spread + 2.0 * ctx->omega * ctx->cmax;
+    return rate > 0.0 ? 2.5 / rate : INFINITY;
+}
+
+void qpr_destroy(qpr_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard dg(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    cudaFree(ctx->d_H);
+    cudaFree(ctx->d_sptr);
+    cudaFree(ctx->d_scol);
+    cudaFree(ctx->d_sval);
+    cudaFree(ctx->d_dang);
+    cudaFree(ctx->d_c);
+    cudaFree(ctx->d_state);
+    cudaFree(ctx->d_g);
+    cudaFree(ctx->d_partials);
+    cudaFree(ctx->d_pairs);
+    cudaFree(ctx->d_ctl);
+    cudaFree(ctx->d_io);
+    cudaFree(ctx->d_p);
+    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+    if (ctx->ev) cudaEventDestroy(ctx->ev);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, const int64_t *dst,
+                      const double *w, double alpha, double omega, const qpr_options *opt) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return QPR_E_ARG;
+    }
+    *out = nullptr;
+    qpr_options o;
+    qpr_default_options(&o);
+    if (opt) o = *opt;
+    auto arg_err = [&](qpr_status st, const std::string &msg) {
+        g_create_error = msg;
+        return st;
+    };
+    if (n < 2) return arg_err(QPR_E_ARG, "n must be at least 2");
+    if (n > 65536) return arg_err(QPR_E_ARG, "n above 65536 is not supported");
+    if (m < 0 || (m > 0 && (!src || !dst))) return arg_err(QPR_E_ARG, "edge arrays missing");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return arg_err(QPR_E_ARG, "alpha must lie in [0, 1]");
+    if (!(omega >= 0.0 && omega <= 1.0)) return arg_err(QPR_E_ARG, "omega must lie in [0, 1]");
+    if (o.precision != QPR_FP64) return arg_err(QPR_E_ARG, "unsupported precision");
+    if (o.h_diag != QPR_HDIAG_ZERO && o.h_diag != QPR_HDIAG_NEG_OUTDEG)
+        return arg_err(QPR_E_ARG, "unknown h_diag mode");
+    if (o.dangling != QPR_DANGLING_F && o.dangling != QPR_DANGLING_UNIFORM)
+        return arg_err(QPR_E_ARG, "unknown dangling mode");
+    if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
+    for (int64_t e = 0; e < m; ++e) {
+        const double we = w ? w[e] : 1.0;
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+            return arg_err(QPR_E_GRAPH, "edge " + std::to_string(e) + " has a node index outside [0, n)");
+        if (!std::isfinite(we) || we < 0.0)
+            return arg_err(QPR_E_GRAPH, "edge " + std::to_string(e) + " has a negative or non-finite weight");
+    }
+
+    // ---- adjacency: A_ij = w for the link j -> i; duplicates sum ----
+    struct Ent { int64_t i, j; double a; };
+    std::vector<Ent> ents;
+    ents.reserve((size_t)m);
+    for (int64_t e = 0; e < m; ++e) {
+        const double we = w ? w[e] : 1.0;
+        if (src[e] == dst[e] || we == 0.0) continue;
+        ents.push_back({dst[e], src[e], we});
+    }
+    std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) {
+        return x.i != y.i ? x.i < y.i : x.j < y.j;
+    });
+    std::vector<Ent> A;
+    for (const Ent &x : ents) {
+        if (!A.empty() && A.back().i == x.i && A.back().j == x.j) A.back().a += x.a;
+        else A.push_back(x);
+    }
+    std::vector<double> outdeg(n, 0.0);
+    for (const Ent &x : A) outdeg[x.j] += x.a;
+
+    // ---- H (Eq. S6): H_ij = -max(A_ij, A_ji) off the diagonal ----
+    std::vector<Ent> Hs;
+    Hs.reserve(A.size() * 2);
+    for (const Ent &x : A) {
+        Hs.push_back({x.i, x.j, x.a});
+        Hs.push_back({x.j, x.i, x.a});
+    }
+    std::sort(Hs.begin(), Hs.end(), [](const Ent &x, const Ent &y) {
+        return x.i != y.i ? x.i < y.i : x.j < y.j;
+    });
+    std::vector<Ent> Hu;  // unique (i, j) with -max
+    for (const Ent &x : Hs) {
+        if (!Hu.empty() && Hu.back().i == x.i && Hu.back().j == x.j) Hu.back().a = std::max(Hu.back().a, x.a);
+        else Hu.push_back(x);
+    }
+    std::vector<int64_t> hptr(n + 1, 0);
+    std::vector<int> hcol;
+    std::vector<double> hval;
+    {
+        size_t q = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            hptr[i] = (int64_t)hcol.size();
+            bool diag_done = false;
+            const double hd = (o.h_diag == QPR_HDIAG_NEG_OUTDEG) ? -outdeg[i] : 0.0;
+            while (q < Hu.size() && Hu[q].i == i) {
+                if (!diag_done && Hu[q].j > i) {
+                    if (hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
+                    diag_done = true;
+                }
+                hcol.push_back((int)Hu[q].j);
+                hval.push_back(-Hu[q].a);
+                ++q;
+            }
+            if (!diag_done && hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
+        }
+        hptr[n] = (int64_t)hcol.size();
+    }
+
+    // ---- S restricted to columns with out-links, CSR by rows ----
+    std::vector<int> sptr(n + 1, 0), scol;
+    std::vector<double> sval;
+    scol.reserve(A.size());
+    sval.reserve(A.size());
+    {
+        size_t q = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            sptr[i] = (int)scol.size();
+            while (q < A.size() && A[q].i == i) {
+                scol.push_back((int)A[q].j);
+                sval.push_back(A[q].a / outdeg[A[q].j]);
+                ++q;
+            }
+        }
+        sptr[n] = (int)scol.size();
+    }
+    std::vector<unsigned char> dang(n);
+    for (int64_t j = 0; j < n; ++j) dang[j] = (outdeg[j] > 0.0) ? 0 : 1;
+
+    qpr_ctx *ctx = new (std::nothrow) qpr_ctx();
+    if (!ctx) return arg_err(QPR_E_OOM, "host allocation failed");
+    ctx->n = n;
+    ctx->alpha = alpha;
+    ctx->omega = omega;
+    ctx->opt = o;
+    ctx->np = (int)(((n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
+    ctx->spread = estimate_spread(n, hptr, hcol, hval);
+    // column sums of G: alpha * (column sum of S) + (1 - alpha) * 1
+    std::vector<double> c(ctx->np, 0.0);
+    {
+        std::vector<double> scs(n, 0.0);
+        for (size_t q = 0; q < sval.size(); ++q) scs[scol[q]] += sval[q];
+        const double fcol = (double)(n - 1) / (double)(n - 1);
+        double cmax = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double sj = dang[j] ? 1.0 : scs[j];
+            c[j] = alpha * sj + (1.0 - alpha) * fcol;
+            cmax = std::max(cmax, c[j]);
+        }
+        ctx->cmax = cmax;
+    }
+
+    if (o.device < 0) {
+        if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return arg_err(QPR_E_CUDA, "no CUDA device available");
+        }
+    } else {
+        ctx->device = o.device;
+    }
+    DeviceGuard dg(ctx->device);
+    auto bail = [&](qpr_status st) {
+        g_create_error = ctx->err;
+        qpr_destroy(ctx);
+        return st;
+    };
+#define CREATE_CUDA(call)                                            \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call)); \
+    } while (0)
+    if (getenv("QPR_FAULT") && strcmp(getenv("QPR_FAULT"), "oom") == 0) {
+        ctx->err = "injected allocation failure (QPR_FAULT=oom)";
+        return bail(QPR_E_OOM);
+    }
+    CREATE_CUDA(qpr::init_stage_fp64());
+    const int np = ctx->np;
+    const size_t plane = (size_t)np * np;
+    // dense H, np x np with zero padding
+    {
+        std::vector<double> Hd(plane, 0.0);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = hptr[i]; q < hptr[i + 1]; ++q) Hd[(size_t)i * np + hcol[q]] = hval[q];
+        CREATE_CUDA(cudaMalloc(&ctx->d_H, plane * sizeof(double)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_H, Hd.data(), plane * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CREATE_CUDA(cudaMalloc(&ctx->d_sptr, (n + 1) * sizeof(int)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_scol, std::max<size_t>(1, scol.size()) * sizeof(int)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_sval, std::max<size_t>(1, sval.size()) * sizeof(double)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_dang, n));
+    CREATE_CUDA(cudaMalloc(&ctx->d_c, np * sizeof(double)));
+    CREATE_CUDA(cudaMemcpy(ctx->d_sptr, sptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if (!scol.empty()) {
+        CREATE_CUDA(cudaMemcpy(ctx->d_scol, scol.data(), scol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMemcpy(ctx->d_sval, sval.data(), sval.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CREATE_CUDA(cudaMemcpy(ctx->d_dang, dang.data(), n, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(ctx->d_c, c.data(), np * sizeof(double), cudaMemcpyHostToDevice));
+
+    const int T = np / qpr::kTileFp64;
+    std::vector<int2> pairs;
+    pairs.reserve((size_t)T * (T + 1) / 2);
+    for (int I = 0; I < T; ++I)
+        for (int J = I + 1; J < T; ++J) pairs.push_back(make_int2(I, J));
+    for (int I = 0; I < T; ++I) pairs.push_back(make_int2(I, I));
+    CREATE_CUDA(cudaMalloc(&ctx->d_pairs, pairs.size() * sizeof(int2)));
+    CREATE_CUDA(cudaMemcpy(ctx->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMalloc(&ctx->d_state, 8 * plane * sizeof(double)));
+    CREATE_CUDA(cudaMemset(ctx->d_state, 0, 8 * plane * sizeof(double)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_g, np * sizeof(double)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_partials, pairs.size() * sizeof(double)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_ctl, sizeof(Ctl)));
+    CREATE_CUDA(cudaMemset(ctx->d_ctl, 0, sizeof(Ctl)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_io, (size_t)n * n * 2 * sizeof(double)));
+    CREATE_CUDA(cudaMalloc(&ctx->d_p, n * sizeof(double)));
+    CREATE_CUDA(cudaMallocHost(&ctx->h_ctl, sizeof(Ctl)));
+    CREATE_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    CREATE_CUDA(cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming));
+#undef CREATE_CUDA
+
+    qpr::DevOps &ops = ctx->ops;
+    ops.n = (int)n;
+    ops.np = np;
+    ops.alpha = alpha;
+    ops.omega = omega;
+    ops.dangling = o.dangling;
+    ops.H = ctx->d_H;
+    ops.s_ptr = ctx->d_sptr;
+    ops.s_col = ctx->d_scol;
+    ops.s_val = ctx->d_sval;
+    ops.dang = ctx->d_dang;
+    ops.c = ctx->d_c;
+    qpr::Work &wk = ctx->work;
+    wk.y = ctx->d_state;
+    wk.z = ctx->d_state + 2 * plane;
+    wk.ya = ctx->d_state + 4 * plane;
+    wk.yb = ctx->d_state + 6 * plane;
+    wk.g = ctx->d_g;
+    wk.partials = ctx->d_partials;
+    wk.pairs = ctx->d_pairs;
+    wk.npairs = (int)pairs.size();
+    wk.tiles = T;
+    wk.ctl = ctx->d_ctl;
+    *out = ctx;
+    return QPR_OK;
+}
+
+// Make the context stream wait for work the caller queued on its stream.
+static qpr_status begin_call(qpr_ctx *ctx) {
+    qpr_status st = check_usable(ctx);
+    if (st != QPR_OK) return st;
+    cudaStream_t user = (cudaStream_t)ctx->opt.cuda_stream;
+    QPR_CUDA(ctx, cudaEventRecord(ctx->ev, user));
+    QPR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev, 0));
+    return QPR_OK;
+}
+
+static qpr_status rhs_impl(qpr_ctx *ctx, const void *rho, void *out, double *resid) {
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho) return fail(ctx, QPR_E_ARG, "rho is NULL");
+    st = import_rho(ctx, rho, ctx->work.y);
+    if (st != QPR_OK) return st;
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->scale = 1.0;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    qpr::launch_gain(0, ctx->ops, ctx->work.y, ctx->work, ctx->stream);
+    qpr::launch_stage_fp64(0, ctx->ops, ctx->work, ctx->stream);
+    if (out) {
+        st = export_rho(ctx, ctx->work.z, 0, out);
+        if (st != QPR_OK) return st;
+    }
+    std::vector<double> part(ctx->work.npairs);
+    if (resid)
+        QPR_CUDA(ctx, cudaMemcpyAsync(part.data(), ctx->d_partials, part.size() * sizeof(double),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (resid) {
+        double s = 0.0;
+        for (double v : part) s += v;
+        *resid = sqrt(s);
+    }
+    return QPR_OK;
+}
+
+qpr_status qpr_rhs(qpr_ctx *ctx, const void *rho, void *out) {
+    if (!ctx) return QPR_E_ARG;
+    if (!out) return fail(ctx, QPR_E_ARG, "out is NULL");
+    DeviceGuard dg(ctx->device);
+    return rhs_impl(ctx, rho, out, nullptr);
+}
+
+qpr_status qpr_residual(qpr_ctx *ctx, const void *rho, double *resid_out) {
+    if (!ctx) return QPR_E_ARG;
+    if (!resid_out) return fail(ctx, QPR_E_ARG, "resid_out is NULL");
+    DeviceGuard dg(ctx->device);
+    return rhs_impl(ctx, rho, nullptr, resid_out);
+}
+
+qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho) return fail(ctx, QPR_E_ARG, "rho is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, QPR_E_ARG, "dt must be positive and finite");
+    if (steps < 0) return fail(ctx, QPR_E_ARG, "steps must be non-negative");
+    if (dt > qpr_max_stable_dt(ctx))
+        return fail(ctx, QPR_E_UNSTABLE, "dt exceeds the RK4 stability estimate " +
+                                             std::to_string(qpr_max_stable_dt(ctx)));
+    st = import_rho(ctx, rho, ctx->work.y);
+    if (st != QPR_OK) return st;
+    st = run_rk4(ctx, dt, 0.0, steps);
+    if (st != QPR_OK) return st;
+    if (ctx->h_ctl->status == qpr::kCtlNonFinite)
+        return fail(ctx, QPR_E_NONFINITE, "non-finite trace or residual during the integration");
+    st = export_rho(ctx, ctx->work.y, 1, rho);
+    if (st != QPR_OK) return st;
+    return sync_ctx(ctx);
+}
+
+qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int64_t max_steps,
+                            qpr_stats *out) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho) return fail(ctx, QPR_E_ARG, "rho is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, QPR_E_ARG, "dt must be positive and finite");
+    if (!(tol > 0.0)) return fail(ctx, QPR_E_ARG, "tol must be positive");
+    if (max_steps < 0) return fail(ctx, QPR_E_ARG, "max_steps must be non-negative");
+    const double dmax = qpr_max_stable_dt(ctx);
+    int64_t m = 1;
+    if (dt > dmax) m = (int64_t)ceil(dt / dmax);
+    const double h = dt / (double)m;
+    st = import_rho(ctx, rho, ctx->work.y);
+    if (st != QPR_OK) return st;
+    st = run_rk4(ctx, h, tol, max_steps);
+    if (st != QPR_OK) return st;
+    const Ctl c = *ctx->h_ctl;
+    st = export_rho(ctx, ctx->work.y, 1, rho);
+    if (st != QPR_OK) return st;
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->steps = c.step;
+        out->substeps_m = m;
+        out->t = (double)c.step * h;
+        out->residual = c.resid;
+        out->trace_before = c.trace;
+        out->converged = (c.status == qpr::kCtlConverged) ? 1 : 0;
+        out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (c.status == qpr::kCtlNonFinite) return fail(ctx, QPR_E_NONFINITE, "non-finite trace or residual");
+    if (c.status != qpr::kCtlConverged)
+        return fail(ctx, QPR_E_NOT_CONVERGED, "max_steps reached with residual " + std::to_string(c.resid));
+    return QPR_OK;
+}
+
+qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho || !p) return fail(ctx, QPR_E_ARG, "rho or p is NULL");
+    const int64_t n = ctx->n;
+    const double *src = (const double *)rho;
+    if (!is_device_ptr(rho)) {
+        QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_io, rho, (size_t)n * n * 2 * sizeof(double),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->d_io;
+    }
+    qpr::launch_diag(src, (int)n, ctx->d_p, ctx->stream);
+    std::vector<double> ph(n);
+    QPR_CUDA(ctx, cudaMemcpyAsync(ph.data(), ctx->d_p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    const bool p_dev = is_device_ptr(p);
+    if (p_dev)
+        QPR_CUDA(ctx, cudaMemcpyAsync(p, ctx->d_p, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (!p_dev) memcpy(p, ph.data(), n * sizeof(double));
+    if (rank) {
+        std::vector<int64_t> r(n);
+        std::iota(r.begin(), r.end(), 0);
+        std::stable_sort(r.begin(), r.end(), [&](int64_t a, int64_t b) { return ph[a] > ph[b]; });
+        if (is_device_ptr(rank)) {
+            QPR_CUDA(ctx, cudaMemcpy(rank, r.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+        } else {
+            memcpy(rank, r.data(), n * sizeof(int64_t));
+        }
+    }
+    return QPR_OK;
+}
+
+}  // extern "C"

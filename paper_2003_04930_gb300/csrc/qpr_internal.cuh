@@ -1,0 +1,82 @@
+// Internal declarations shared by the solver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qpr.h"
+
+namespace qpr {
+
+// Device control block. The host writes tol, dt and max_steps before a
+// solve; the kernels read them (so a captured CUDA graph serves every dt)
+// and write the stop decision and the residual. Kernels of a step read
+// `done` on entry and return at once when it is set.
+struct Ctl {
+    int done;           // 1: every later kernel returns immediately
+    int status;         // kCtlRunning / kCtlConverged / kCtlMaxSteps / kCtlNonFinite
+    long long step;     // completed RK4 steps in this solve
+    long long max_steps;
+    double tol;         // stop when ||f(y_n)||_F < tol (0: never)
+    double dt;
+    double scale;       // 1 / Re tr(y) of the current step (set by the stage-1 gain kernel)
+    double trace;       // Re tr(y) of the current step
+    double resid;       // residual of step index `resid_step`
+    long long resid_step;
+};
+
+enum { kCtlRunning = 0, kCtlConverged = 1, kCtlMaxSteps = 2, kCtlNonFinite = 3 };
+
+// Operators on the device (built once by qpr_create).
+struct DevOps {
+    int n;                // nodes
+    int np;               // padded edge of every N x N plane (multiple of kPadFp64)
+    double alpha, omega;
+    int dangling;         // QPR_DANGLING_F / QPR_DANGLING_UNIFORM
+    const double *H;      // np x np row-major, zero padding
+    const int *s_ptr;     // CSR of S restricted to columns with out-links: n + 1 row pointers
+    const int *s_col;
+    const double *s_val;  // A_ij / outDeg(j)
+    const unsigned char *dang;  // n flags: column j has no out-links
+    const double *c;      // np column sums of G (0 on padding)
+};
+
+// RK4 work buffers. Every state buffer holds two np x np FP64 planes,
+// real part first, then imaginary part.
+struct Work {
+    double *y;            // state at the start of a step (unnormalised)
+    double *z;            // RK4 accumulator
+    double *ya, *yb;      // stage inputs (ping-pong)
+    double *g;            // gain G p of the current stage, np entries
+    double *partials;     // one residual partial per stage-kernel CTA
+    int2 *pairs;          // tile pairs (I, J), I <= J, off-diagonal first
+    int npairs;
+    int tiles;            // np / kTileFp64
+    Ctl *ctl;
+};
+
+constexpr int kTileFp64 = 32;
+constexpr int kPadFp64 = 32;
+
+// ---- kernels (aux_kernels.cu) ----
+// Hermitise an interleaved complex128 n x n matrix into two np x np planes.
+void launch_import(const double *rho_il, int n, int np, double *planes, cudaStream_t s);
+// planes * ctl->scale (use_scale) -> interleaved complex128 n x n.
+void launch_export(const double *planes, int n, int np, const Ctl *ctl, int use_scale,
+                   double *rho_il, cudaStream_t s);
+// p[i] = Re rho_ii of an interleaved complex128 matrix.
+void launch_diag(const double *rho_il, int n, double *p, cudaStream_t s);
+// g = G p_s for stage `stage` (0: plain right-hand side, 1..4: RK4 stages).
+void launch_gain(int stage, const DevOps &ops, const double *yin, const Work &w, cudaStream_t s);
+
+// ---- FP64 tile-pair stage kernel (stage_fp64.cu) ----
+// stage 0: out = f(yin) into w.z, residual partials.
+// stage 1..4: one classical RK4 stage with the fused update.
+void launch_stage_fp64(int stage, const DevOps &ops, const Work &w, cudaStream_t s);
+// Opt in to the kernel's dynamic shared memory on the current device.
+cudaError_t init_stage_fp64();
+
+}  // namespace qpr

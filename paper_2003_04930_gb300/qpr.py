@@ -1,0 +1,222 @@
+"""Thin Python binding of the C ABI in ``include/qpr.h`` (ctypes).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libqpr.so``. Density matrices may be torch complex128 CUDA tensors
+(passed by device pointer) or NumPy complex128 arrays (host memory; the
+library copies them in and out). There is no CPU fallback: if the library
+cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqpr.so")
+
+QPR_OK, QPR_E_ARG, QPR_E_GRAPH, QPR_E_CUDA, QPR_E_OOM, QPR_E_UNSTABLE, QPR_E_NOT_CONVERGED, \
+    QPR_E_TIMEOUT, QPR_E_NONFINITE = range(9)
+QPR_FP64, QPR_SPLIT_BF16 = 0, 1
+QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
+QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
+
+# every entry point declared in include/qpr.h
+EXPORTED = (
+    "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
+    "qpr_n", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
+    "qpr_steady_state", "qpr_populations",
+)
+
+
+class qpr_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("h_diag", ctypes.c_int32), ("dangling", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class qpr_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("substeps_m", ctypes.c_int64), ("t", ctypes.c_double),
+                ("residual", ctypes.c_double), ("trace_before", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("converged", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in
+                ("steps", "substeps_m", "t", "residual", "trace_before", "seconds", "converged")}
+
+
+class QprError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqpr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i64, f64, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    lib.qpr_default_options.argtypes = [ctypes.POINTER(qpr_options)]
+    lib.qpr_default_options.restype = st
+    lib.qpr_create.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, f64, f64, ctypes.POINTER(qpr_options)]
+    lib.qpr_create.restype = st
+    lib.qpr_destroy.argtypes = [vp]
+    lib.qpr_destroy.restype = None
+    lib.qpr_last_error.argtypes = [vp]
+    lib.qpr_last_error.restype = ctypes.c_char_p
+    lib.qpr_status_string.argtypes = [st]
+    lib.qpr_status_string.restype = ctypes.c_char_p
+    lib.qpr_n.argtypes = [vp]
+    lib.qpr_n.restype = i64
+    lib.qpr_h_spread.argtypes = [vp]
+    lib.qpr_h_spread.restype = f64
+    lib.qpr_max_stable_dt.argtypes = [vp]
+    lib.qpr_max_stable_dt.restype = f64
+    lib.qpr_rhs.argtypes = [vp, vp, vp]
+    lib.qpr_rhs.restype = st
+    lib.qpr_residual.argtypes = [vp, vp, ctypes.POINTER(f64)]
+    lib.qpr_residual.restype = st
+    lib.qpr_evolve.argtypes = [vp, vp, f64, i64]
+    lib.qpr_evolve.restype = st
+    lib.qpr_steady_state.argtypes = [vp, vp, f64, f64, i64, ctypes.POINTER(qpr_stats)]
+    lib.qpr_steady_state.restype = st
+    lib.qpr_populations.argtypes = [vp, vp, vp, vp]
+    lib.qpr_populations.restype = st
+    _lib = lib
+    return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load_library().qpr_status_string(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor (device or host) or a NumPy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check_rho(rho, n):
+    dt = getattr(rho, "dtype", None)
+    ok = (str(dt) in ("torch.complex128", "complex128"))
+    if not ok or tuple(rho.shape) != (n, n):
+        raise ValueError(f"rho must be a contiguous ({n}, {n}) complex128 array or tensor")
+
+
+class Solver:
+    """One problem (graph, alpha, omega) bound to a CUDA device."""
+
+    def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
+                 dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1):
+        lib = load_library()
+        self._lib = lib
+        self.n = int(n)
+        src = np.ascontiguousarray(src, dtype=np.int64)
+        dst = np.ascontiguousarray(dst, dtype=np.int64)
+        self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        opt = qpr_options()
+        lib.qpr_default_options(ctypes.byref(opt))
+        opt.precision, opt.h_diag, opt.dangling = int(precision), int(h_diag), int(dangling)
+        opt.graph_steps = int(graph_steps)
+        opt.device = int(device)
+        if stream is not None:
+            opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        h = ctypes.c_void_p()
+        st = lib.qpr_create(ctypes.byref(h), self.n, int(src.shape[0]), _ptr(src), _ptr(dst),
+                            _ptr(self._w), float(alpha), float(omega), ctypes.byref(opt))
+        if st != QPR_OK:
+            raise QprError(st, lib.qpr_last_error(None).decode())
+        self._h = h
+        self.alpha, self.omega = float(alpha), float(omega)
+
+    @classmethod
+    def from_edges(cls, g, **kw):
+        return cls(g.n, g.src, g.dst, g.w, **kw)
+
+    def _raise(self, st):
+        if st != QPR_OK:
+            raise QprError(st, self._lib.qpr_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qpr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def h_spread(self) -> float:
+        return float(self._lib.qpr_h_spread(self._h))
+
+    @property
+    def max_stable_dt(self) -> float:
+        return float(self._lib.qpr_max_stable_dt(self._h))
+
+    def rhs(self, rho, out):
+        _check_rho(rho, self.n)
+        _check_rho(out, self.n)
+        self._raise(self._lib.qpr_rhs(self._h, _ptr(rho), _ptr(out)))
+        return out
+
+    def residual(self, rho) -> float:
+        _check_rho(rho, self.n)
+        r = ctypes.c_double(0.0)
+        self._raise(self._lib.qpr_residual(self._h, _ptr(rho), ctypes.byref(r)))
+        return float(r.value)
+
+    def evolve(self, rho, dt: float, steps: int):
+        """In place: rho <- rho after `steps` RK4 steps."""
+        _check_rho(rho, self.n)
+        self._raise(self._lib.qpr_evolve(self._h, _ptr(rho), float(dt), int(steps)))
+        return rho
+
+    def steady_state(self, rho, dt: float, tol: float, max_steps: int, check: bool = True):
+        """In place: rho <- first state with ||f||_F < tol. Returns the stats
+        dict (and raises on failure when ``check``)."""
+        _check_rho(rho, self.n)
+        stats = qpr_stats()
+        st = self._lib.qpr_steady_state(self._h, _ptr(rho), float(dt), float(tol), int(max_steps),
+                                        ctypes.byref(stats))
+        d = stats.as_dict()
+        d["status"] = int(st)
+        if check and st not in (QPR_OK,):
+            self._raise(st)
+        return d
+
+    def populations(self, rho, with_rank: bool = False):
+        _check_rho(rho, self.n)
+        p = np.zeros(self.n)
+        rank = np.zeros(self.n, dtype=np.int64) if with_rank else None
+        self._raise(self._lib.qpr_populations(self._h, _ptr(rho), _ptr(p), _ptr(rank)))
+        return (p, rank) if with_rank else p
