@@ -70,15 +70,23 @@ enum { QPR_HDIAG_ZERO = 0, QPR_HDIAG_NEG_OUTDEG = 1 };
 /* Column of S for a node without out-links: F's column, 1/(N-1) off the
  * diagonal (default), or the uniform column 1/N. */
 enum { QPR_DANGLING_F = 0, QPR_DANGLING_UNIFORM = 1 };
+/* How the O(N^2)-per-row product H rho of each RK4 stage is formed.
+ * DENSE: tensor-core GEMM of the dense N x N H against [Re rho | Im rho]
+ * (4 N^3 flops per stage). SPARSE: CSR H times rho in FP64 (4 nnz(H) N
+ * flops per stage, bandwidth bound). AUTO picks SPARSE when H has fewer than
+ * N^2 / 8 nonzeros. Both produce the same FP64 right-hand side up to
+ * summation order. */
+enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
 
 typedef struct {
     int32_t precision;   /* QPR_FP64 (default) */
     int32_t h_diag;      /* QPR_HDIAG_ZERO (default) or QPR_HDIAG_NEG_OUTDEG */
     int32_t dangling;    /* QPR_DANGLING_F (default) or QPR_DANGLING_UNIFORM */
     int32_t graph_steps; /* RK4 steps per captured CUDA graph launch (default 32; 0 = no graphs) */
-    void *cuda_stream;   /* cudaStream_t to run on; NULL = the context creates its own */
-    int32_t device;      /* CUDA device ordinal (default: the current device) */
-    int32_t reserved[7];
+    void *cuda_stream;   /* cudaStream_t the caller's inputs are ordered on (NULL = legacy default stream) */
+    int32_t device;      /* CUDA device ordinal (default -1: the current device) */
+    int32_t backend;     /* QPR_BACKEND_AUTO (default), QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE */
+    int32_t reserved[6];
 } qpr_options;
 
 typedef struct {
@@ -88,6 +96,7 @@ typedef struct {
     double residual;     /* ||f(rho_n)||_F of the returned state (FP64) */
     double trace_before; /* Re tr of the unnormalised state before the last division */
     double seconds;      /* wall time of the call */
+    int64_t kernel_launches; /* kernels this call launched (early-exit launches included) */
     int32_t converged;   /* 1 if residual < tol */
     int32_t reserved[3];
 } qpr_stats;
@@ -117,8 +126,10 @@ QPR_API const char *qpr_last_error(const qpr_ctx *ctx);
 QPR_API const char *qpr_status_string(qpr_status s);
 
 /* Number of nodes and the estimated spectral spread lambda_max - lambda_min
- * of H used by the RK4 step-size check. */
+ * of H used by the RK4 step-size check. qpr_backend: the backend in use
+ * (QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE). */
 QPR_API int64_t qpr_n(const qpr_ctx *ctx);
+QPR_API int32_t qpr_backend(const qpr_ctx *ctx);
 QPR_API double qpr_h_spread(const qpr_ctx *ctx);
 
 /* Largest dt for which the context considers one RK4 step stable: it needs
@@ -152,6 +163,14 @@ QPR_API qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps)
  * out may be NULL. */
 QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int64_t max_steps,
                             qpr_stats *out);
+
+/* Per-kernel timing of the RK4 step on the context's stream. Runs `steps`
+ * RK4 steps from rho (rho itself is not modified) without CUDA graphs,
+ * bracketing every kernel launch with CUDA events, and writes the mean
+ * durations in milliseconds: ms_out[0] one stage kernel (H rho plus the fused
+ * epilogue), ms_out[1] one gain kernel (G p), ms_out[2] one whole step.
+ * Meant for roofline measurements; steps >= 1. */
+QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out);
 
 /* p[i] = Re rho_ii (the probability at node i); p: N doubles, host or
  * device. rank (nullable): N int64 node indices in descending order of p,

@@ -26,6 +26,9 @@ struct qpr_ctx {
     double cmax = 1.0;     // max column sum of G
     // device operators
     double *d_H = nullptr;
+    int *d_hptr = nullptr, *d_hcol = nullptr;
+    double *d_hval = nullptr;
+    int backend = QPR_BACKEND_SPARSE;
     int *d_sptr = nullptr, *d_scol = nullptr;
     double *d_sval = nullptr;
     unsigned char *d_dang = nullptr;
@@ -47,6 +50,7 @@ struct qpr_ctx {
     qpr::Work work{};
     std::string err;
     bool poisoned = false;
+    int64_t launches = 0;  // kernels launched by the current call
 };
 
 namespace {
@@ -148,12 +152,17 @@ qpr_status sync_ctx(qpr_ctx *ctx) {
     return QPR_OK;
 }
 
+void launch_stage(qpr_ctx *ctx, int s) {
+    if (ctx->backend == QPR_BACKEND_DENSE) qpr::launch_stage_fp64(s, ctx->ops, ctx->work, ctx->stream);
+    else qpr::launch_stage_sparse(s, ctx->ops, ctx->work, ctx->stream);
+}
+
 void enqueue_step(qpr_ctx *ctx) {
     const qpr::Work &w = ctx->work;
     const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
     for (int s = 1; s <= 4; ++s) {
         qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
-        qpr::launch_stage_fp64(s, ctx->ops, w, ctx->stream);
+        launch_stage(ctx, s);
     }
 }
 
@@ -183,11 +192,13 @@ qpr_status import_rho(qpr_ctx *ctx, const void *rho, double *planes) {
         src = ctx->d_io;
     }
     qpr::launch_import(src, (int)ctx->n, ctx->np, planes, ctx->stream);
+    ctx->launches += 1;
     return QPR_OK;
 }
 
 qpr_status export_rho(qpr_ctx *ctx, const double *planes, int use_scale, void *rho) {
     const size_t bytes = (size_t)ctx->n * ctx->n * 2 * sizeof(double);
+    ctx->launches += 1;
     if (is_device_ptr(rho)) {
         qpr::launch_export(planes, (int)ctx->n, ctx->np, ctx->d_ctl, use_scale, (double *)rho, ctx->stream);
     } else {
@@ -224,11 +235,11 @@ qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         } else {
             enqueue_step(ctx);
         }
+        ctx->launches += 8 * (int64_t)chunk;
         QPR_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
         st = sync_ctx(ctx);
         if (st != QPR_OK) return st;
         if (h->done) break;
-        (void)chunk;
     }
     return QPR_OK;
 }
@@ -246,6 +257,7 @@ qpr_status qpr_default_options(qpr_options *opt) {
     opt->graph_steps = 32;
     opt->cuda_stream = nullptr;
     opt->device = -1;
+    opt->backend = QPR_BACKEND_AUTO;
     return QPR_OK;
 }
 
@@ -260,6 +272,7 @@ const char *qpr_last_error(const qpr_ctx *ctx) {
 }
 
 int64_t qpr_n(const qpr_ctx *ctx) { return ctx ? ctx->n : 0; }
+int32_t qpr_backend(const qpr_ctx *ctx) { return ctx ? ctx->backend : 0; }
 double qpr_h_spread(const qpr_ctx *ctx) { return ctx ? ctx->spread : 0.0; }
 
 double qpr_max_stable_dt(const qpr_ctx *ctx) {
@@ -274,6 +287,9 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     cudaFree(ctx->d_H);
+    cudaFree(ctx->d_hptr);
+    cudaFree(ctx->d_hcol);
+    cudaFree(ctx->d_hval);
     cudaFree(ctx->d_sptr);
     cudaFree(ctx->d_scol);
     cudaFree(ctx->d_sval);
@@ -319,6 +335,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     if (o.dangling != QPR_DANGLING_F && o.dangling != QPR_DANGLING_UNIFORM)
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
+    if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
     for (int64_t e = 0; e < m; ++e) {
         const double we = w ? w[e] : 1.0;
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
@@ -413,6 +430,10 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ctx->opt = o;
     ctx->np = (int)(((n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
     ctx->spread = estimate_spread(n, hptr, hcol, hval);
+    if (o.backend == QPR_BACKEND_AUTO)
+        ctx->backend = ((double)hval.size() < (double)n * (double)n / 8.0) ? QPR_BACKEND_SPARSE : QPR_BACKEND_DENSE;
+    else
+        ctx->backend = o.backend;
     // column sums of G: alpha * (column sum of S) + (1 - alpha) * 1
     std::vector<double> c(ctx->np, 0.0);
     {
@@ -453,6 +474,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return bail(QPR_E_OOM);
     }
     CREATE_CUDA(qpr::init_stage_fp64());
+    CREATE_CUDA(qpr::init_stage_sparse());
     const int np = ctx->np;
     const size_t plane = (size_t)np * np;
     // dense H, np x np with zero padding
@@ -462,6 +484,18 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
             for (int64_t q = hptr[i]; q < hptr[i + 1]; ++q) Hd[(size_t)i * np + hcol[q]] = hval[q];
         CREATE_CUDA(cudaMalloc(&ctx->d_H, plane * sizeof(double)));
         CREATE_CUDA(cudaMemcpy(ctx->d_H, Hd.data(), plane * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    {
+        std::vector<int> hptr32(n + 1);
+        for (int64_t i = 0; i <= n; ++i) hptr32[i] = (int)hptr[i];
+        CREATE_CUDA(cudaMalloc(&ctx->d_hptr, (n + 1) * sizeof(int)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_hcol, std::max<size_t>(1, hcol.size()) * sizeof(int)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_hval, std::max<size_t>(1, hval.size()) * sizeof(double)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_hptr, hptr32.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        if (!hcol.empty()) {
+            CREATE_CUDA(cudaMemcpy(ctx->d_hcol, hcol.data(), hcol.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CREATE_CUDA(cudaMemcpy(ctx->d_hval, hval.data(), hval.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
     }
     CREATE_CUDA(cudaMalloc(&ctx->d_sptr, (n + 1) * sizeof(int)));
     CREATE_CUDA(cudaMalloc(&ctx->d_scol, std::max<size_t>(1, scol.size()) * sizeof(int)));
@@ -504,6 +538,9 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ops.omega = omega;
     ops.dangling = o.dangling;
     ops.H = ctx->d_H;
+    ops.h_ptr = ctx->d_hptr;
+    ops.h_col = ctx->d_hcol;
+    ops.h_val = ctx->d_hval;
     ops.s_ptr = ctx->d_sptr;
     ops.s_col = ctx->d_scol;
     ops.s_val = ctx->d_sval;
@@ -528,6 +565,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
 static qpr_status begin_call(qpr_ctx *ctx) {
     qpr_status st = check_usable(ctx);
     if (st != QPR_OK) return st;
+    ctx->launches = 0;
     cudaStream_t user = (cudaStream_t)ctx->opt.cuda_stream;
     QPR_CUDA(ctx, cudaEventRecord(ctx->ev, user));
     QPR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev, 0));
@@ -545,7 +583,7 @@ static qpr_status rhs_impl(qpr_ctx *ctx, const void *rho, void *out, double *res
     h->scale = 1.0;
     QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
     qpr::launch_gain(0, ctx->ops, ctx->work.y, ctx->work, ctx->stream);
-    qpr::launch_stage_fp64(0, ctx->ops, ctx->work, ctx->stream);
+    launch_stage(ctx, 0);
     if (out) {
         st = export_rho(ctx, ctx->work.z, 0, out);
         if (st != QPR_OK) return st;
@@ -632,11 +670,63 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
         out->residual = c.resid;
         out->trace_before = c.trace;
         out->converged = (c.status == qpr::kCtlConverged) ? 1 : 0;
+        out->kernel_launches = ctx->launches;
         out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     if (c.status == qpr::kCtlNonFinite) return fail(ctx, QPR_E_NONFINITE, "non-finite trace or residual");
     if (c.status != qpr::kCtlConverged)
         return fail(ctx, QPR_E_NOT_CONVERGED, "max_steps reached with residual " + std::to_string(c.resid));
+    return QPR_OK;
+}
+
+qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho || !ms_out || steps < 1) return fail(ctx, QPR_E_ARG, "rho/ms_out NULL or steps < 1");
+    if (!(dt > 0.0) || dt > qpr_max_stable_dt(ctx)) return fail(ctx, QPR_E_ARG, "dt not positive or unstable");
+    st = import_rho(ctx, rho, ctx->work.y);
+    if (st != QPR_OK) return st;
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->max_steps = steps + 1;
+    h->tol = 0.0;
+    h->dt = dt;
+    h->scale = 1.0;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<cudaEvent_t> ev(8 * steps + 1);
+    for (auto &e : ev) QPR_CUDA(ctx, cudaEventCreate(&e));
+    const qpr::Work &w = ctx->work;
+    const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
+    int q = 0;
+    QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
+    for (int64_t k = 0; k < steps; ++k) {
+        for (int s = 1; s <= 4; ++s) {
+            qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
+            QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
+            launch_stage(ctx, s);
+            QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
+        }
+    }
+    st = sync_ctx(ctx);
+    double stage_ms = 0.0, gain_ms = 0.0, total_ms = 0.0;
+    if (st == QPR_OK) {
+        for (int i = 0; i + 1 < q; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            if (i % 2 == 0) gain_ms += ms;
+            else stage_ms += ms;
+        }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, ev[0], ev[q - 1]);
+        total_ms = tot;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != QPR_OK) return st;
+    ms_out[0] = stage_ms / (4.0 * steps);
+    ms_out[1] = gain_ms / (4.0 * steps);
+    ms_out[2] = total_ms / (double)steps;
     return QPR_OK;
 }
 

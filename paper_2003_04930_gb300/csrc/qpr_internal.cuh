@@ -37,6 +37,9 @@ struct DevOps {
     double alpha, omega;
     int dangling;         // QPR_DANGLING_F / QPR_DANGLING_UNIFORM
     const double *H;      // np x np row-major, zero padding
+    const int *h_ptr;     // CSR of H (same values; zeros skipped): n + 1 row pointers
+    const int *h_col;
+    const double *h_val;
     const int *s_ptr;     // CSR of S restricted to columns with out-links: n + 1 row pointers
     const int *s_col;
     const double *s_val;  // A_ij / outDeg(j)
@@ -78,5 +81,9 @@ void launch_gain(int stage, const DevOps &ops, const double *yin, const Work &w,
 void launch_stage_fp64(int stage, const DevOps &ops, const Work &w, cudaStream_t s);
 // Opt in to the kernel's dynamic shared memory on the current device.
 cudaError_t init_stage_fp64();
+
+// ---- sparse (CSR H) FP64 stage kernel (stage_sparse.cu), same contract ----
+void launch_stage_sparse(int stage, const DevOps &ops, const Work &w, cudaStream_t s);
+cudaError_t init_stage_sparse();
 
 }  // namespace qpr

@@ -26,6 +26,7 @@
 //
 // The FP64 tensor path is mma.sync m8n8k4 (DMMA): tcgen05 has no f64 kind.
 #include "qpr_internal.cuh"
+#include "stage_epilogue.cuh"
 
 namespace qpr {
 namespace {
@@ -41,6 +42,7 @@ constexpr int LDX = 2 * TS + 1;        // epilogue X tile row (odd: conflict-fre
 constexpr int LDO = TS + 1;
 constexpr int NTHREADS = 128;
 
+static_assert(TS == kEpiTS && NTHREADS == kEpiThreads && LDO == kEpiLDO, "epilogue geometry");
 static_assert(2 * TS * LDX + 4 * TS * LDO <= 2 * STAGE_DBL, "epilogue must fit in the pipeline buffers");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -76,12 +78,6 @@ __device__ __forceinline__ void load_chunk(double *st, const double *__restrict_
         const double *src = base + (size_t)(tile * TS + r) * np + (size_t)kc * KC + sg * 2;
         cp_async16(st + p * PANEL + r * LDS + sg * 2, src);
     }
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <int STAGE>
@@ -173,94 +169,8 @@ stage_fp64_kernel(DevOps ops, Work w) {
                 if (!diag) sX2[r * LDX + cidx] = acc2[mt][nt][i];
             }
     __syncthreads();
-    const double *X2 = diag ? sX1 : sX2;
-
-    const double om = ops.omega, cm = 1.0 - om;
-    const double scale = ctl->scale;
-    const double gsig = (STAGE == 1) ? scale : 1.0;                 // stage-1 input is unnormalised y
-    const double ysig = (STAGE >= 1 && STAGE <= 3) ? scale : 1.0;  // Y1 = y / tr(y)
-    const double dt = ctl->dt;
-    double nrm = 0.0;
-
-    for (int e = tid; e < TS * TS; e += NTHREADS) {
-        const int a = e / TS, b = e - (e / TS) * TS;
-        const int ga = I * TS + a, gb = J * TS + b;
-        const size_t off = (size_t)ga * np + gb;
-        const double Aab = sX1[a * LDX + b], Bab = -sX1[a * LDX + TS + b];
-        const double Aba = X2[b * LDX + a], Bba = -X2[b * LDX + TS + a];
-        const double ysr = gsig * yin[off], ysi = gsig * yin[plane + off];
-        const double hc = 0.5 * (ops.c[ga] + ops.c[gb]);
-        double kr = cm * gsig * (Bab + Bba) - om * hc * ysr;
-        const double ki = -cm * gsig * (Aab - Aba) - om * hc * ysi;
-        if (ga == gb) kr += om * w.g[ga];
-        if (STAGE <= 1) nrm += kr * kr + ki * ki;
-
-        double o0, o1, o2 = 0.0, o3 = 0.0;
-        if (STAGE == 0) {
-            o0 = kr; o1 = ki;
-            w.z[off] = o0; w.z[plane + off] = o1;
-        } else if (STAGE <= 3) {
-            const double y1r = ysig * w.y[off], y1i = ysig * w.y[plane + off];
-            if (STAGE == 1) {
-                o0 = y1r + (dt / 6.0) * kr;
-                o1 = y1i + (dt / 6.0) * ki;
-            } else {
-                o0 = w.z[off] + (dt / 3.0) * kr;
-                o1 = w.z[plane + off] + (dt / 3.0) * ki;
-            }
-            const double cst = (STAGE == 3) ? dt : 0.5 * dt;
-            o2 = y1r + cst * kr;
-            o3 = y1i + cst * ki;
-            double *yn = (STAGE == 2) ? w.yb : w.ya;
-            w.z[off] = o0; w.z[plane + off] = o1;
-            yn[off] = o2; yn[plane + off] = o3;
-        } else {
-            o0 = w.z[off] + (dt / 6.0) * kr;
-            o1 = w.z[plane + off] + (dt / 6.0) * ki;
-            w.y[off] = o0; w.y[plane + off] = o1;
-        }
-        sO[0 * TS * LDO + a * LDO + b] = o0;
-        sO[1 * TS * LDO + a * LDO + b] = o1;
-        if (STAGE >= 1 && STAGE <= 3) {
-            sO[2 * TS * LDO + a * LDO + b] = o2;
-            sO[3 * TS * LDO + a * LDO + b] = o3;
-        }
-    }
-
-    if (STAGE <= 1) {
-        __shared__ double red[NTHREADS / 32];
-        nrm = warp_sum(nrm);
-        if (lane == 0) red[warp] = nrm;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int q = 0; q < NTHREADS / 32; ++q) s += red[q];
-            w.partials[blockIdx.x] = diag ? s : 2.0 * s;
-        }
-    }
-
-    if (!diag) {
-        __syncthreads();
-        // tile (J, I) = conjugate transpose of tile (I, J)
-        double *d0, *d1, *d2 = nullptr, *d3 = nullptr;
-        if (STAGE == 0) { d0 = w.z; d1 = w.z + plane; }
-        else if (STAGE <= 3) {
-            double *yn = (STAGE == 2) ? w.yb : w.ya;
-            d0 = w.z; d1 = w.z + plane; d2 = yn; d3 = yn + plane;
-        } else { d0 = w.y; d1 = w.y + plane; }
-        for (int e = tid; e < TS * TS; e += NTHREADS) {
-            const int b = e / TS, a = e - (e / TS) * TS;
-            const size_t off = (size_t)(J * TS + b) * np + I * TS + a;
-            d0[off] = sO[0 * TS * LDO + a * LDO + b];
-            d1[off] = -sO[1 * TS * LDO + a * LDO + b];
-            if (STAGE >= 1 && STAGE <= 3) {
-                d2[off] = sO[2 * TS * LDO + a * LDO + b];
-                d3[off] = -sO[3 * TS * LDO + a * LDO + b];
-            }
-        }
-    }
-
-    if (STAGE == 4 && blockIdx.x == 0 && tid == 0) ctl->step += 1;
+    __shared__ double red[NTHREADS / 32];
+    stage_epilogue<STAGE>(ops, w, I, J, diag, sX1, sX2, LDX, sO, red);
 }
 
 template <int STAGE>

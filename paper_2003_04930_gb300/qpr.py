@@ -21,30 +21,32 @@ QPR_OK, QPR_E_ARG, QPR_E_GRAPH, QPR_E_CUDA, QPR_E_OOM, QPR_E_UNSTABLE, QPR_E_NOT
 QPR_FP64, QPR_SPLIT_BF16 = 0, 1
 QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
+QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
 
 # every entry point declared in include/qpr.h
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
-    "qpr_n", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
-    "qpr_steady_state", "qpr_populations",
+    "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
+    "qpr_steady_state", "qpr_populations", "qpr_profile_step",
 )
 
 
 class qpr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("h_diag", ctypes.c_int32), ("dangling", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("device", ctypes.c_int32), ("backend", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class qpr_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("substeps_m", ctypes.c_int64), ("t", ctypes.c_double),
                 ("residual", ctypes.c_double), ("trace_before", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("converged", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k in
-                ("steps", "substeps_m", "t", "residual", "trace_before", "seconds", "converged")}
+                ("steps", "substeps_m", "t", "residual", "trace_before", "seconds", "kernel_launches",
+                 "converged")}
 
 
 class QprError(RuntimeError):
@@ -77,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_status_string.restype = ctypes.c_char_p
     lib.qpr_n.argtypes = [vp]
     lib.qpr_n.restype = i64
+    lib.qpr_backend.argtypes = [vp]
+    lib.qpr_backend.restype = ctypes.c_int32
     lib.qpr_h_spread.argtypes = [vp]
     lib.qpr_h_spread.restype = f64
     lib.qpr_max_stable_dt.argtypes = [vp]
@@ -89,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_evolve.restype = st
     lib.qpr_steady_state.argtypes = [vp, vp, f64, f64, i64, ctypes.POINTER(qpr_stats)]
     lib.qpr_steady_state.restype = st
+    lib.qpr_profile_step.argtypes = [vp, vp, f64, i64, ctypes.POINTER(f64)]
+    lib.qpr_profile_step.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
     _lib = lib
@@ -128,7 +134,8 @@ class Solver:
     """One problem (graph, alpha, omega) bound to a CUDA device."""
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
-                 dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1):
+                 dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
+                 backend=QPR_BACKEND_AUTO):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -140,6 +147,7 @@ class Solver:
         opt.precision, opt.h_diag, opt.dangling = int(precision), int(h_diag), int(dangling)
         opt.graph_steps = int(graph_steps)
         opt.device = int(device)
+        opt.backend = int(backend)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         h = ctypes.c_void_p()
@@ -174,6 +182,10 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+    @property
+    def backend(self) -> int:
+        return int(self._lib.qpr_backend(self._h))
 
     @property
     def h_spread(self) -> float:
@@ -220,3 +232,11 @@ class Solver:
         rank = np.zeros(self.n, dtype=np.int64) if with_rank else None
         self._raise(self._lib.qpr_populations(self._h, _ptr(rho), _ptr(p), _ptr(rank)))
         return (p, rank) if with_rank else p
+
+    def profile_step(self, rho, dt: float, steps: int):
+        """Mean per-launch durations (ms) of the stage kernel and the gain
+        kernel, and of one whole RK4 step, timed with CUDA events."""
+        _check_rho(rho, self.n)
+        ms = (ctypes.c_double * 3)()
+        self._raise(self._lib.qpr_profile_step(self._h, _ptr(rho), float(dt), int(steps), ms))
+        return {"stage_ms": ms[0], "gain_ms": ms[1], "step_ms": ms[2]}

@@ -30,19 +30,24 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _pair(g, **kw):
-    return Oracle.from_edges(g, **kw), Solver.from_edges(g, **kw)
+def _pair(g, backend=Q.QPR_BACKEND_AUTO, **kw):
+    return Oracle.from_edges(g, **kw), Solver.from_edges(g, backend=backend, **kw)
+
+
+BACKENDS = [Q.QPR_BACKEND_DENSE, Q.QPR_BACKEND_SPARSE]
 
 
 def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
 
 
+@pytest.mark.parametrize("backend", BACKENDS)
 @pytest.mark.parametrize("n", [2, 16, 33, 64, 100, 150])
 @pytest.mark.parametrize("omega", [0.0, 0.5, 1.0])
-def test_rhs_parity(n, omega):
+def test_rhs_parity(n, omega, backend):
     g = graphs.heavy_tailed(n, 40 + n) if n > 8 else graphs.erdos_renyi(n, 0.5, 1)
-    o, s = _pair(g, alpha=0.85, omega=omega)
+    o, s = _pair(g, backend, alpha=0.85, omega=omega)
+    assert s.backend == backend
     rho = graphs.random_hermitian(n, 7)
     f_ref = o.rhs(rho)
     out = torch.zeros((n, n), dtype=torch.complex128, device=DEV)
@@ -56,10 +61,11 @@ def test_rhs_parity(n, omega):
     assert abs(r - np.linalg.norm(f_ref)) <= 1e-12 * np.linalg.norm(f_ref)
 
 
+@pytest.mark.parametrize("backend", BACKENDS)
 @pytest.mark.parametrize("h_diag,dangling", [(0, 1), (1, 0), (1, 1)])
-def test_rhs_parity_modes(h_diag, dangling):
+def test_rhs_parity_modes(h_diag, dangling, backend):
     g = graphs.erdos_renyi(70, 0.05, 3)  # sparse: several dangling nodes
-    o, s = _pair(g, alpha=0.7, omega=0.6, h_diag=h_diag, dangling=dangling)
+    o, s = _pair(g, backend, alpha=0.7, omega=0.6, h_diag=h_diag, dangling=dangling)
     rho = graphs.random_density(70, 8)
     f_ref = o.rhs(rho)
     out = torch.zeros((70, 70), dtype=torch.complex128, device=DEV)
@@ -67,11 +73,12 @@ def test_rhs_parity_modes(h_diag, dangling):
     assert np.abs(out.cpu().numpy() - f_ref).max() <= 1e-13 * max(1.0, np.abs(f_ref).max()) * 5
 
 
-def test_config1_trajectory_parity():
+@pytest.mark.parametrize("backend", BACKENDS)
+def test_config1_trajectory_parity(backend):
     # N = 16 ER (p = 0.25, seed 0), alpha = 0.85, omega = 0.8, rho0 = I/N,
     # dt = 0.01 to t = 100
     g = graphs.erdos_renyi(16, 0.25, 0)
-    o, s = _pair(g, alpha=0.85, omega=0.8)
+    o, s = _pair(g, backend, alpha=0.85, omega=0.8)
     rho0 = graphs.maximally_mixed(16)
     ref = o.evolve(rho0, 0.01, 10000)
     rho = _dev(rho0)
@@ -81,11 +88,12 @@ def test_config1_trajectory_parity():
     assert abs(np.trace(got).real - 1.0) < 1e-14
 
 
+@pytest.mark.parametrize("backend", BACKENDS)
 @pytest.mark.parametrize("n", [64, 97, 200])
 @pytest.mark.parametrize("omega", [0.2, 0.5, 0.8, 1.0])
-def test_trajectory_parity_heavy_tailed(n, omega):
+def test_trajectory_parity_heavy_tailed(n, omega, backend):
     g = graphs.heavy_tailed(n, 1)
-    o, s = _pair(g, alpha=0.85, omega=omega)
+    o, s = _pair(g, backend, alpha=0.85, omega=omega)
     rho0 = graphs.random_density(n, 3, rank=2)
     ref = o.evolve(rho0, 0.01, 150)
     rho = _dev(rho0)
@@ -183,11 +191,12 @@ def test_nan_input_reported():
     assert stats["status"] == Q.QPR_E_NONFINITE
 
 
-def test_airline_size_short_trajectory():
+@pytest.mark.parametrize("backend", BACKENDS)
+def test_airline_size_short_trajectory(backend):
     # N = 922 heavy-tailed graph (seed 1) in the launch configuration the
     # benchmark times; a few steps against the oracle
     g = graphs.heavy_tailed(922, 1)
-    o, s = _pair(g, alpha=0.85, omega=0.8)
+    o, s = _pair(g, backend, alpha=0.85, omega=0.8)
     rho0 = graphs.maximally_mixed(922)
     ref = o.evolve(rho0, 0.01, 3)
     d = _dev(rho0)
@@ -195,3 +204,28 @@ def test_airline_size_short_trajectory():
     got = d.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 1e-10
     assert abs(s.residual(d) - o.residual(ref)) <= 1e-11 * max(1.0, o.residual(ref))
+
+
+def test_backends_agree_bitwise_independent_of_graph_chunking():
+    # the number of steps per captured graph does not change the result
+    g = graphs.heavy_tailed(80, 4)
+    rho0 = _dev(graphs.random_density(80, 5))
+    outs = []
+    for gs in (0, 1, 7, 32):
+        s = Solver.from_edges(g, alpha=0.85, omega=0.5, graph_steps=gs)
+        r = rho0.clone()
+        st = s.steady_state(r, 0.01, 1e-6, 100000)
+        outs.append((st["steps"], r.cpu().numpy()))
+    for st, r in outs[1:]:
+        assert st == outs[0][0]
+        np.testing.assert_array_equal(r, outs[0][1])
+
+
+def test_profile_step_reports_positive_times():
+    g = graphs.heavy_tailed(128, 3)
+    s = Solver.from_edges(g, alpha=0.85, omega=0.8)
+    rho = _dev(graphs.maximally_mixed(128))
+    before = rho.clone()
+    p = s.profile_step(rho, 0.01, 3)
+    assert p["stage_ms"] > 0 and p["gain_ms"] > 0 and p["step_ms"] >= 4 * (p["stage_ms"] + p["gain_ms"]) * 0.5
+    assert torch.equal(rho, before)
