@@ -177,6 +177,43 @@ QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, in
  * ties to the lower index (the ranking of the main text's airline study). */
 QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank);
 
+/* ---- right-hand side without any allocation ----
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: hosts that hand out all device memory from
+ * their own pool and forbid libraries from allocating, services held to a
+ * fixed device-memory budget, and code that must not allocate after
+ * start-up. It computes out = f(rho) exactly as qpr_rhs does (sparse CSR
+ * stage kernel), but every input and output is the caller's and the scratch
+ * lives in a file-scope __device__ array sized for N <= QPR_NOALLOC_MAX_N
+ * (about 2.1 MB, resident on every device that loads the library until the
+ * process exits). It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * n            nodes, 2 <= n <= QPR_NOALLOC_MAX_N (else QPR_E_ARG).
+ * h_ptr/h_col/h_val   CSR of H (Eq. S6) on the device: n + 1 row pointers,
+ *              column indices, values, rows in any column order.
+ * s_ptr/s_col/s_val   CSR of S on the device, the column-normalised
+ *              adjacency A_ij / outDeg(j), holding only columns j with
+ *              outDeg(j) > 0; dangling_flags (n bytes, device) marks the
+ *              columns without out-links, which take F's column
+ *              (QPR_DANGLING_F) or the uniform column (QPR_DANGLING_UNIFORM).
+ * alpha, omega in [0, 1].
+ * rho, out     N x N complex128 row-major on the device; must not alias.
+ * cuda_stream  stream the work is queued on (NULL: legacy default stream).
+ * The call only queues work and returns; out is ready when the stream
+ * reaches that point. Errors: QPR_E_ARG (n outside [2, QPR_NOALLOC_MAX_N], a
+ * NULL pointer, alpha/omega/dangling_mode out of range), QPR_E_CUDA.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls on a device share the scratch array
+ * and each leaves its contents behind; calls whose GPU work overlaps (other
+ * streams, other threads) race on it and must be serialised by the caller. */
+#define QPR_NOALLOC_MAX_N 256
+QPR_API qpr_status qpr_rhs_noalloc(int64_t n, const int32_t *h_ptr, const int32_t *h_col, const double *h_val,
+                                   const int32_t *s_ptr, const int32_t *s_col, const double *s_val,
+                                   const uint8_t *dangling_flags, double alpha, double omega,
+                                   int32_t dangling_mode, const void *rho, void *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,8 +27,9 @@ QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
     "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
-    "qpr_steady_state", "qpr_populations", "qpr_profile_step",
+    "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc",
 )
+QPR_NOALLOC_MAX_N = 256
 
 
 class qpr_options(ctypes.Structure):
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_steady_state.restype = st
     lib.qpr_profile_step.argtypes = [vp, vp, f64, i64, ctypes.POINTER(f64)]
     lib.qpr_profile_step.restype = st
+    lib.qpr_rhs_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, f64, f64, ctypes.c_int32, vp, vp, vp]
+    lib.qpr_rhs_noalloc.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
     _lib = lib
