@@ -1,0 +1,42 @@
+"""Run a few RK4 steps of one workload, for profiler captures.
+
+    python -m paper_2003_04930_gb300.profile_case --n 922 --omega 0.8 --backend sparse --steps 5
+
+Builds the heavy-tailed graph (seed 1 unless --seed), evolves rho0 = I/N by
+`--steps` RK4 steps of dt = 0.01 through qpr_evolve (one CUDA graph launch
+per 32 steps, or plain launches with --graph-steps 0), and prints the
+per-kernel timing of qpr_profile_step. Exit status 0 on success.
+"""
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=922)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--omega", type=float, default=0.8)
+    ap.add_argument("--backend", choices=["auto", "dense", "sparse"], default="sparse")
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--graph-steps", type=int, default=0)
+    a = ap.parse_args()
+    import torch
+    from paper_2003_04930_gb300 import Solver, graphs, qpr
+    from paper_2003_04930_gb300.build import build_library
+    build_library()
+    be = {"auto": qpr.QPR_BACKEND_AUTO, "dense": qpr.QPR_BACKEND_DENSE, "sparse": qpr.QPR_BACKEND_SPARSE}
+    g = graphs.heavy_tailed(a.n, a.seed)
+    s = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=be[a.backend], graph_steps=a.graph_steps)
+    rho = torch.from_numpy(graphs.maximally_mixed(a.n)).cuda()
+    s.evolve(rho, 0.01, a.steps)
+    torch.cuda.synchronize()
+    print(json.dumps(s.profile_step(rho, 0.01, 2)))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
