@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-steps", type=int, default=400000)
     ap.add_argument("--backend", choices=["auto", "dense", "sparse"], default="auto")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--ref-refresh", type=int, default=32)
+    ap.add_argument("--no-fp64-sparse", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense-projection", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle RK4 steps per sample (0: auto)")
@@ -220,8 +223,10 @@ def run_ours(a):
 
     backend = {"auto": qpr.QPR_BACKEND_AUTO, "dense": qpr.QPR_BACKEND_DENSE,
                "sparse": qpr.QPR_BACKEND_SPARSE}[a.backend]
+    prec = {"fp64": qpr.QPR_FP64, "mixed": qpr.QPR_MIXED}[a.precision]
     g = graphs.heavy_tailed(a.n, a.seed)
-    s = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=backend, device=local)
+    s = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=backend, device=local, precision=prec,
+                          ref_refresh=a.ref_refresh)
     rho0 = torch.from_numpy(graphs.maximally_mixed(a.n)).to(dev)
     rho = torch.empty_like(rho0)
     flush = torch.empty(64 * 2**20, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
@@ -268,12 +273,19 @@ def run_ours(a):
     peaks, peak_src = load_peaks()
     n = a.n
     if s.backend == qpr.QPR_BACKEND_SPARSE:
-        # algorithmic bytes per stage launch: on average 4 of the N x N
-        # complex128 matrices (stage input, y or Z, outputs) read or written
-        alg = 4 * 16 * n * n
+        if prec == qpr.QPR_MIXED:
+            # mean over the 4 stages of the N x N planes read or written: FP32
+            # delta/D/F32/S planes (8 N^2 bytes each) and, at stage 4, the FP64
+            # y (read and written) and R: (32 + 48 + 48 + 80) / 4 = 52 N^2 bytes
+            alg = 52 * n * n
+            kname = "stage_mixed_sparse_kernel"
+        else:
+            # mean of 4 complex128 N x N matrices per stage (input, y or Z, outputs)
+            alg = 4 * 16 * n * n
+            kname = "stage_sparse_kernel"
         ach = alg / (prof["stage_ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "stage_sparse_kernel",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": kname,
                 "alg_bytes_per_launch": alg, "launch_ms": prof["stage_ms"],
                 "peak_source": f"hbm_gbs of {peak_src}",
                 "note": "state buffers are L2-resident at this N, so the HBM fraction can exceed 1"}
@@ -286,10 +298,13 @@ def run_ours(a):
                 "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
                 "peak_source": f"bf16_tflops of {peak_src} x nominal FP64/BF16 ratio 1.25/2250"}
 
+    form = {(qpr.QPR_FP64, 1): "fp64 dense DMMA", (qpr.QPR_FP64, 2): "fp64 sparse CSR",
+            (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas + fp64 reference/accumulation/residual"}[
+        (prec, s.backend)]
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(a), backend={1: "dense-dmma", 2: "sparse-csr"}[s.backend],
+            "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",
+            "config": dict(workload_config(a), form=form, ref_refresh=a.ref_refresh,
                            parallelism=f"replicas{world}"),
             "rk4_steps_to_converge": steps_conv, "rk4_steps_per_s": steps_conv / (total / a.steps),
             "residual": stats[-1]["residual"], "roofline": roof, "clocks": clocks,
@@ -307,6 +322,22 @@ def run_ours(a):
             "frac_of_fp64_peak": flops / (pd["stage_ms"] * 1e-3) / 1e12 / fp64_peak,
             "fp64_peak_tflops": fp64_peak, "peak_source": f"bf16_tflops of {peak_src} x 1.25/2250"}
         sd.close()
+
+    # the exact FP64 sparse form on the same problem, one solve
+    if not a.no_fp64_sparse and (prec != qpr.QPR_FP64 or s.backend != qpr.QPR_BACKEND_SPARSE):
+        sf = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=qpr.QPR_BACKEND_SPARSE, device=local)
+        rho.copy_(rho0)
+        sf.steady_state(rho, a.dt, a.tol, a.max_steps)
+        rho.copy_(rho0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stf = sf.steady_state(rho, a.dt, a.tol, a.max_steps)
+        e1.record()
+        e1.synchronize()
+        line["fp64_sparse"] = {"time_to_steady_state_s": e0.elapsed_time(e1) / 1e3, "steps": stf["steps"]}
+        sf.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     host = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)

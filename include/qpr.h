@@ -62,7 +62,17 @@ typedef enum {
     QPR_E_NONFINITE = 8      /* a NaN or Inf appeared in the state or the residual */
 } qpr_status;
 
-enum { QPR_FP64 = 0, QPR_SPLIT_BF16 = 1 };
+/* Arithmetic of the RK4 stages.
+ * QPR_FP64: every stage in FP64 (the plain form).
+ * QPR_MIXED: RK4 in delta form against an exact FP64 reference. Every
+ *   ref_refresh steps the state is renormalised, R = y / tr(y), and F = f(R)
+ *   is evaluated exactly in FP64, which also gives the exact residual ||F||_F.
+ *   In between, each stage evaluates only f(Y_s - R) (f is linear) in FP32
+ *   (or split BF16 on tensor cores for the dense backend), and FP64 is kept
+ *   for the RK accumulation into rho. A residual that passes the FP32-accurate
+ *   per-step estimate is confirmed by an exact FP64 refresh before the solve
+ *   stops, so the returned state satisfies the FP64 stop rule. */
+enum { QPR_FP64 = 0, QPR_MIXED = 1 };
 /* Diagonal of H. Eq. S6 prints H_ii = -outDeg(i); the symmetrised-adjacency
  * form with a zero diagonal is the default because the printed diagonal
  * makes RK4 at dt = 0.01 unstable on heavy-tailed weighted graphs. */
@@ -79,14 +89,15 @@ enum { QPR_DANGLING_F = 0, QPR_DANGLING_UNIFORM = 1 };
 enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
 
 typedef struct {
-    int32_t precision;   /* QPR_FP64 (default) */
+    int32_t precision;   /* QPR_FP64 (default) or QPR_MIXED */
     int32_t h_diag;      /* QPR_HDIAG_ZERO (default) or QPR_HDIAG_NEG_OUTDEG */
     int32_t dangling;    /* QPR_DANGLING_F (default) or QPR_DANGLING_UNIFORM */
     int32_t graph_steps; /* RK4 steps per captured CUDA graph launch (default 32; 0 = no graphs) */
     void *cuda_stream;   /* cudaStream_t the caller's inputs are ordered on (NULL = legacy default stream) */
     int32_t device;      /* CUDA device ordinal (default -1: the current device) */
     int32_t backend;     /* QPR_BACKEND_AUTO (default), QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE */
-    int32_t reserved[6];
+    int32_t ref_refresh; /* QPR_MIXED: steps between exact FP64 reference refreshes (default 32) */
+    int32_t reserved[5];
 } qpr_options;
 
 typedef struct {

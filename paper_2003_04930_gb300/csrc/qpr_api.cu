@@ -35,6 +35,10 @@ struct qpr_ctx {
     double *d_c = nullptr;
     // device work
     double *d_state = nullptr;  // y, z, ya, yb: 2 planes each
+    double *d_mix64 = nullptr;  // mixed form: R, F (2 planes each)
+    float *d_mix32 = nullptr;   // mixed form: F32, D, da, db, S (2 planes each)
+    float *d_g32 = nullptr, *d_hval32 = nullptr, *d_c32 = nullptr;
+    qpr::MixedWork mw{};
     double *d_g = nullptr;
     double *d_partials = nullptr;
     int2 *d_pairs = nullptr;
@@ -244,6 +248,77 @@ qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     return QPR_OK;
 }
 
+void enqueue_mixed_block(qpr_ctx *ctx, int steps) {
+    qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+    for (int k = 0; k < steps; ++k)
+        for (int s = 1; s <= 4; ++s) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream);
+}
+
+qpr_status ensure_mixed_graph(qpr_ctx *ctx) {
+    if (ctx->graph || ctx->opt.graph_steps <= 0) return QPR_OK;
+    cudaGraph_t g = nullptr;
+    QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_mixed_block(ctx, ctx->opt.ref_refresh);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->graph_steps = ctx->opt.ref_refresh;
+    return QPR_OK;
+}
+
+qpr_status read_ctl(qpr_ctx *ctx) {
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_ctx(ctx);
+}
+
+// Mixed form: blocks of (exact refresh + ref_refresh delta steps) until the
+// device stops. A stop on the FP32-accurate estimate is confirmed by an exact
+// refresh at the same step; the run always ends with a refresh, so R holds
+// the normalised returned state and resid_exact its exact FP64 residual.
+qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->max_steps = max_steps;
+    h->tol = tol;
+    h->dt = dt;
+    h->scale = 1.0;
+    h->resid_exact_step = -1;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    qpr_status st = ensure_mixed_graph(ctx);
+    if (st != QPR_OK) return st;
+    const int block = ctx->opt.ref_refresh;
+    for (;;) {
+        if (ctx->graph) {
+            QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        } else {
+            enqueue_mixed_block(ctx, block);
+        }
+        ctx->launches += qpr::kMixedLaunchesPerRefresh + qpr::kMixedLaunchesPerStep * (int64_t)block;
+        st = read_ctl(ctx);
+        if (st != QPR_OK) return st;
+        if (!h->done) continue;
+        if (h->status == qpr::kCtlNonFinite) return QPR_OK;
+        if (h->resid_exact_step == h->step) return QPR_OK;  // stopped by an exact refresh at this step
+        // confirm (or finish) with an exact refresh at the current step
+        h->done = 0;
+        const int prev = h->status;
+        h->status = qpr::kCtlRunning;
+        QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+        qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+        ctx->launches += qpr::kMixedLaunchesPerRefresh;
+        st = read_ctl(ctx);
+        if (st != QPR_OK) return st;
+        if (h->done) return QPR_OK;  // converged, max steps or non-finite, decided exactly
+        if (prev == qpr::kCtlMaxSteps) return QPR_OK;
+        // the estimate passed but the exact residual did not: keep stepping
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -258,6 +333,7 @@ qpr_status qpr_default_options(qpr_options *opt) {
     opt->cuda_stream = nullptr;
     opt->device = -1;
     opt->backend = QPR_BACKEND_AUTO;
+    opt->ref_refresh = 32;
     return QPR_OK;
 }
 
@@ -296,6 +372,11 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_dang);
     cudaFree(ctx->d_c);
     cudaFree(ctx->d_state);
+    cudaFree(ctx->d_mix64);
+    cudaFree(ctx->d_mix32);
+    cudaFree(ctx->d_g32);
+    cudaFree(ctx->d_hval32);
+    cudaFree(ctx->d_c32);
     cudaFree(ctx->d_g);
     cudaFree(ctx->d_partials);
     cudaFree(ctx->d_pairs);
@@ -329,7 +410,11 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     if (m < 0 || (m > 0 && (!src || !dst))) return arg_err(QPR_E_ARG, "edge arrays missing");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return arg_err(QPR_E_ARG, "alpha must lie in [0, 1]");
     if (!(omega >= 0.0 && omega <= 1.0)) return arg_err(QPR_E_ARG, "omega must lie in [0, 1]");
-    if (o.precision != QPR_FP64) return arg_err(QPR_E_ARG, "unsupported precision");
+    if (o.precision != QPR_FP64 && o.precision != QPR_MIXED) return arg_err(QPR_E_ARG, "unsupported precision");
+    if (o.precision == QPR_MIXED && o.backend == QPR_BACKEND_DENSE)
+        return arg_err(QPR_E_ARG, "the mixed form runs on the sparse backend");
+    if (o.precision == QPR_MIXED && (o.ref_refresh < 1 || o.ref_refresh > 4096))
+        return arg_err(QPR_E_ARG, "ref_refresh outside [1, 4096]");
     if (o.h_diag != QPR_HDIAG_ZERO && o.h_diag != QPR_HDIAG_NEG_OUTDEG)
         return arg_err(QPR_E_ARG, "unknown h_diag mode");
     if (o.dangling != QPR_DANGLING_F && o.dangling != QPR_DANGLING_UNIFORM)
@@ -430,7 +515,9 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ctx->opt = o;
     ctx->np = (int)(((n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
     ctx->spread = estimate_spread(n, hptr, hcol, hval);
-    if (o.backend == QPR_BACKEND_AUTO)
+    if (o.precision == QPR_MIXED)
+        ctx->backend = QPR_BACKEND_SPARSE;
+    else if (o.backend == QPR_BACKEND_AUTO)
         ctx->backend = ((double)hval.size() < (double)n * (double)n / 8.0) ? QPR_BACKEND_SPARSE : QPR_BACKEND_DENSE;
     else
         ctx->backend = o.backend;
@@ -522,6 +609,23 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     CREATE_CUDA(cudaMemset(ctx->d_state, 0, 8 * plane * sizeof(double)));
     CREATE_CUDA(cudaMalloc(&ctx->d_g, np * sizeof(double)));
     CREATE_CUDA(cudaMalloc(&ctx->d_partials, pairs.size() * sizeof(double)));
+    {
+        std::vector<float> hv32(std::max<size_t>(1, hval.size()));
+        for (size_t q = 0; q < hval.size(); ++q) hv32[q] = (float)hval[q];
+        std::vector<float> c32(np);
+        for (int j = 0; j < np; ++j) c32[j] = (float)c[j];
+        CREATE_CUDA(cudaMalloc(&ctx->d_hval32, hv32.size() * sizeof(float)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_hval32, hv32.data(), hv32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_c32, np * sizeof(float)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_c32, c32.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (o.precision == QPR_MIXED) {
+        CREATE_CUDA(cudaMalloc(&ctx->d_mix64, 4 * plane * sizeof(double)));
+        CREATE_CUDA(cudaMemset(ctx->d_mix64, 0, 4 * plane * sizeof(double)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 10 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 10 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_g32, np * sizeof(float)));
+    }
     CREATE_CUDA(cudaMalloc(&ctx->d_ctl, sizeof(Ctl)));
     CREATE_CUDA(cudaMemset(ctx->d_ctl, 0, sizeof(Ctl)));
     CREATE_CUDA(cudaMalloc(&ctx->d_io, (size_t)n * n * 2 * sizeof(double)));
@@ -546,6 +650,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ops.s_val = ctx->d_sval;
     ops.dang = ctx->d_dang;
     ops.c = ctx->d_c;
+    ops.c32 = ctx->d_c32;
+    ops.h_val32 = ctx->d_hval32;
     qpr::Work &wk = ctx->work;
     wk.y = ctx->d_state;
     wk.z = ctx->d_state + 2 * plane;
@@ -557,6 +663,24 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     wk.npairs = (int)pairs.size();
     wk.tiles = T;
     wk.ctl = ctx->d_ctl;
+    if (o.precision == QPR_MIXED) {
+        qpr::MixedWork &mw = ctx->mw;
+        mw.y = wk.y;
+        mw.R = ctx->d_mix64;
+        mw.F = ctx->d_mix64 + 2 * plane;
+        mw.F32 = ctx->d_mix32;
+        mw.D = ctx->d_mix32 + 2 * plane;
+        mw.da = ctx->d_mix32 + 4 * plane;
+        mw.db = ctx->d_mix32 + 6 * plane;
+        mw.S = ctx->d_mix32 + 8 * plane;
+        mw.g = ctx->d_g32;
+        mw.g64 = ctx->d_g;
+        mw.partials = ctx->d_partials;
+        mw.pairs = ctx->d_pairs;
+        mw.npairs = (int)pairs.size();
+        mw.tiles = T;
+        mw.ctl = ctx->d_ctl;
+    }
     *out = ctx;
     return QPR_OK;
 }
@@ -629,11 +753,12 @@ qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps) {
                                              std::to_string(qpr_max_stable_dt(ctx)));
     st = import_rho(ctx, rho, ctx->work.y);
     if (st != QPR_OK) return st;
-    st = run_rk4(ctx, dt, 0.0, steps);
+    const bool mixed = ctx->opt.precision == QPR_MIXED;
+    st = mixed ? run_mixed(ctx, dt, 0.0, steps) : run_rk4(ctx, dt, 0.0, steps);
     if (st != QPR_OK) return st;
     if (ctx->h_ctl->status == qpr::kCtlNonFinite)
         return fail(ctx, QPR_E_NONFINITE, "non-finite trace or residual during the integration");
-    st = export_rho(ctx, ctx->work.y, 1, rho);
+    st = mixed ? export_rho(ctx, ctx->mw.R, 0, rho) : export_rho(ctx, ctx->work.y, 1, rho);
     if (st != QPR_OK) return st;
     return sync_ctx(ctx);
 }
@@ -655,10 +780,12 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
     const double h = dt / (double)m;
     st = import_rho(ctx, rho, ctx->work.y);
     if (st != QPR_OK) return st;
-    st = run_rk4(ctx, h, tol, max_steps);
+    const bool mixed = ctx->opt.precision == QPR_MIXED;
+    st = mixed ? run_mixed(ctx, h, tol, max_steps) : run_rk4(ctx, h, tol, max_steps);
     if (st != QPR_OK) return st;
-    const Ctl c = *ctx->h_ctl;
-    st = export_rho(ctx, ctx->work.y, 1, rho);
+    Ctl c = *ctx->h_ctl;
+    if (mixed) c.resid = c.resid_exact;
+    st = mixed ? export_rho(ctx, ctx->mw.R, 0, rho) : export_rho(ctx, ctx->work.y, 1, rho);
     if (st != QPR_OK) return st;
     st = sync_ctx(ctx);
     if (st != QPR_OK) return st;
@@ -699,13 +826,17 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     for (auto &e : ev) QPR_CUDA(ctx, cudaEventCreate(&e));
     const qpr::Work &w = ctx->work;
     const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
+    const bool mixed = ctx->opt.precision == QPR_MIXED;
+    if (mixed) qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
     int q = 0;
     QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
     for (int64_t k = 0; k < steps; ++k) {
         for (int s = 1; s <= 4; ++s) {
-            qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
+            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1);
+            else qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
             QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
-            launch_stage(ctx, s);
+            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2);
+            else launch_stage(ctx, s);
             QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
         }
     }

@@ -26,9 +26,13 @@ struct Ctl {
     double trace;       // Re tr(y) of the current step
     double resid;       // residual of step index `resid_step`
     long long resid_step;
+    double resid_exact; // exact FP64 residual of the last reference refresh (mixed form)
+    long long resid_exact_step;
 };
 
-enum { kCtlRunning = 0, kCtlConverged = 1, kCtlMaxSteps = 2, kCtlNonFinite = 3 };
+// kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
+// the host confirms it with an exact FP64 refresh.
+enum { kCtlRunning = 0, kCtlConverged = 1, kCtlMaxSteps = 2, kCtlNonFinite = 3, kCtlCandidate = 4 };
 
 // Operators on the device (built once by qpr_create).
 struct DevOps {
@@ -40,11 +44,13 @@ struct DevOps {
     const int *h_ptr;     // CSR of H (same values; zeros skipped): n + 1 row pointers
     const int *h_col;
     const double *h_val;
+    const float *h_val32; // the same values rounded to FP32 (mixed form)
     const int *s_ptr;     // CSR of S restricted to columns with out-links: n + 1 row pointers
     const int *s_col;
     const double *s_val;  // A_ij / outDeg(j)
     const unsigned char *dang;  // n flags: column j has no out-links
     const double *c;      // np column sums of G (0 on padding)
+    const float *c32;     // the same in FP32 (mixed form)
 };
 
 // RK4 work buffers. Every state buffer holds two np x np FP64 planes,
@@ -58,6 +64,22 @@ struct Work {
     int2 *pairs;          // tile pairs (I, J), I <= J, off-diagonal first
     int npairs;
     int tiles;            // np / kTileFp64
+    Ctl *ctl;
+};
+
+// Buffers of the mixed-precision form (stage_mixed.cu). FP64: y (shared
+// with Work), the reference R = y / tr(y) of the last refresh and F = f(R).
+// FP32 (two np x np planes each): F32 = F, D = y - R, the stage deltas da/db
+// and the RK4 sum S.
+struct MixedWork {
+    double *y, *R, *F;
+    float *F32, *D, *da, *db, *S;
+    float *g;             // gain of the stage delta, np
+    double *g64;          // FP64 gain used by the refresh, np
+    double *partials;
+    int2 *pairs;
+    int npairs;
+    int tiles;
     Ctl *ctl;
 };
 
@@ -85,5 +107,16 @@ cudaError_t init_stage_fp64();
 // ---- sparse (CSR H) FP64 stage kernel (stage_sparse.cu), same contract ----
 void launch_stage_sparse(int stage, const DevOps &ops, const Work &w, cudaStream_t s);
 cudaError_t init_stage_sparse();
+
+// ---- mixed-precision form (stage_mixed.cu) ----
+// Reference refresh: R = y = y / tr(y), F = f(R) exactly (FP64), D = 0, exact
+// residual and stop decision.
+void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s);
+// One RK4 stage: parts & 1 launches the gain of the stage delta, parts & 2
+// the FP32 sparse stage kernel (3 = both, in that order).
+void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+// Kernel launches per RK4 step and per refresh of the mixed form.
+constexpr int kMixedLaunchesPerStep = 8;
+constexpr int kMixedLaunchesPerRefresh = 5;
 
 }  // namespace qpr

@@ -1,6 +1,6 @@
 """Run a few RK4 steps of one workload, for profiler captures.
 
-    python -m paper_2003_04930_gb300.profile_case --n 922 --omega 0.8 --backend sparse --steps 5
+    python -m paper_2003_04930_gb300.profile_case --n 922 --omega 0.8 --backend sparse --steps 5 [--precision mixed]
 
 Builds the heavy-tailed graph (seed 1 unless --seed), evolves rho0 = I/N by
 `--steps` RK4 steps of dt = 0.01 through qpr_evolve (one CUDA graph launch
@@ -23,6 +23,7 @@ def main():
     ap.add_argument("--backend", choices=["auto", "dense", "sparse"], default="sparse")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--graph-steps", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     a = ap.parse_args()
     import torch
     from paper_2003_04930_gb300 import Solver, graphs, qpr
@@ -30,7 +31,9 @@ def main():
     build_library()
     be = {"auto": qpr.QPR_BACKEND_AUTO, "dense": qpr.QPR_BACKEND_DENSE, "sparse": qpr.QPR_BACKEND_SPARSE}
     g = graphs.heavy_tailed(a.n, a.seed)
-    s = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=be[a.backend], graph_steps=a.graph_steps)
+    prec = {"fp64": qpr.QPR_FP64, "mixed": qpr.QPR_MIXED}[a.precision]
+    s = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=be[a.backend], graph_steps=a.graph_steps,
+                          precision=prec)
     rho = torch.from_numpy(graphs.maximally_mixed(a.n)).cuda()
     s.evolve(rho, 0.01, a.steps)
     torch.cuda.synchronize()

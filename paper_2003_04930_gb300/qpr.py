@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqpr.so")
 
 QPR_OK, QPR_E_ARG, QPR_E_GRAPH, QPR_E_CUDA, QPR_E_OOM, QPR_E_UNSTABLE, QPR_E_NOT_CONVERGED, \
     QPR_E_TIMEOUT, QPR_E_NONFINITE = range(9)
-QPR_FP64, QPR_SPLIT_BF16 = 0, 1
+QPR_FP64, QPR_MIXED = 0, 1
 QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
 QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
@@ -35,7 +35,8 @@ QPR_NOALLOC_MAX_N = 256
 class qpr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("h_diag", ctypes.c_int32), ("dangling", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("backend", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("device", ctypes.c_int32), ("backend", ctypes.c_int32),
+                ("ref_refresh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class qpr_stats(ctypes.Structure):
@@ -138,7 +139,7 @@ class Solver:
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -151,6 +152,7 @@ class Solver:
         opt.graph_steps = int(graph_steps)
         opt.device = int(device)
         opt.backend = int(backend)
+        opt.ref_refresh = int(ref_refresh)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         h = ctypes.c_void_p()
