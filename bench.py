@@ -272,7 +272,17 @@ def run_ours(a):
     prof = s.profile_step(rho, a.dt, 20)
     peaks, peak_src = load_peaks()
     n = a.n
-    if s.backend == qpr.QPR_BACKEND_SPARSE:
+    if s.backend == qpr.QPR_BACKEND_DENSE and prec == qpr.QPR_MIXED:
+        # split-BF16 GEMM: 6 BF16 products of H (np x np) with [Re | Im] delta
+        # (np x 2 np), 2 flops per multiply-add, executed on the padded np
+        npad = ((n + 127) // 128) * 128
+        flops = 6 * 2.0 * npad * (2 * npad) * npad
+        ach = flops / (prof["stage_ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "stage_mixed_tc_kernel (tcgen05)",
+                "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
+                "peak_source": f"bf16_tflops of {peak_src}"}
+    elif s.backend == qpr.QPR_BACKEND_SPARSE:
         if prec == qpr.QPR_MIXED:
             # mean over the 4 stages of the N x N planes read or written: FP32
             # delta/D/F32/S planes (8 N^2 bytes each) and, at stage 4, the FP64
@@ -299,6 +309,8 @@ def run_ours(a):
                 "peak_source": f"bf16_tflops of {peak_src} x nominal FP64/BF16 ratio 1.25/2250"}
 
     form = {(qpr.QPR_FP64, 1): "fp64 dense DMMA", (qpr.QPR_FP64, 2): "fp64 sparse CSR",
+            (qpr.QPR_MIXED, 1): "mixed: split-BF16 tcgen05 GEMM deltas (FP32 accumulate) + fp64 "
+                                "reference/accumulation/residual",
             (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas + fp64 reference/accumulation/residual"}[
         (prec, s.backend)]
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,

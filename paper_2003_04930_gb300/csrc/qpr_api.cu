@@ -38,6 +38,10 @@ struct qpr_ctx {
     double *d_mix64 = nullptr;  // mixed form: R, F (2 planes each)
     float *d_mix32 = nullptr;   // mixed form: F32, D, da, db, S (2 planes each)
     float *d_g32 = nullptr, *d_hval32 = nullptr, *d_c32 = nullptr;
+    __nv_bfloat16 *d_hsplit = nullptr;  // dense mixed form: H split into 3 BF16 planes
+    __nv_bfloat16 *d_dsplit = nullptr;  // dense mixed form: 3 delta-split buffers of 6 planes
+    int2 *d_pairs_tc = nullptr;
+    qpr::TcMaps tcmaps{};
     qpr::MixedWork mw{};
     double *d_g = nullptr;
     double *d_partials = nullptr;
@@ -301,6 +305,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         ctx->launches += qpr::kMixedLaunchesPerRefresh + qpr::kMixedLaunchesPerStep * (int64_t)block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
         if (!h->done) continue;
         if (h->status == qpr::kCtlNonFinite) return QPR_OK;
         if (h->resid_exact_step == h->step) return QPR_OK;  // stopped by an exact refresh at this step
@@ -313,6 +318,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         ctx->launches += qpr::kMixedLaunchesPerRefresh;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
         if (h->done) return QPR_OK;  // converged, max steps or non-finite, decided exactly
         if (prev == qpr::kCtlMaxSteps) return QPR_OK;
         // the estimate passed but the exact residual did not: keep stepping
@@ -377,6 +383,9 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_g32);
     cudaFree(ctx->d_hval32);
     cudaFree(ctx->d_c32);
+    cudaFree(ctx->d_hsplit);
+    cudaFree(ctx->d_dsplit);
+    cudaFree(ctx->d_pairs_tc);
     cudaFree(ctx->d_g);
     cudaFree(ctx->d_partials);
     cudaFree(ctx->d_pairs);
@@ -411,8 +420,6 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     if (!(alpha >= 0.0 && alpha <= 1.0)) return arg_err(QPR_E_ARG, "alpha must lie in [0, 1]");
     if (!(omega >= 0.0 && omega <= 1.0)) return arg_err(QPR_E_ARG, "omega must lie in [0, 1]");
     if (o.precision != QPR_FP64 && o.precision != QPR_MIXED) return arg_err(QPR_E_ARG, "unsupported precision");
-    if (o.precision == QPR_MIXED && o.backend == QPR_BACKEND_DENSE)
-        return arg_err(QPR_E_ARG, "the mixed form runs on the sparse backend");
     if (o.precision == QPR_MIXED && (o.ref_refresh < 1 || o.ref_refresh > 4096))
         return arg_err(QPR_E_ARG, "ref_refresh outside [1, 4096]");
     if (o.h_diag != QPR_HDIAG_ZERO && o.h_diag != QPR_HDIAG_NEG_OUTDEG)
@@ -514,10 +521,12 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ctx->omega = omega;
     ctx->opt = o;
     ctx->np = (int)(((n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
+    const bool tc = (o.precision == QPR_MIXED) &&
+                    (o.backend == QPR_BACKEND_DENSE ||
+                     (o.backend == QPR_BACKEND_AUTO && (double)hval.size() >= (double)n * (double)n / 8.0));
+    if (tc) ctx->np = (int)(((n + qpr::kTileTc - 1) / qpr::kTileTc) * qpr::kTileTc);
     ctx->spread = estimate_spread(n, hptr, hcol, hval);
-    if (o.precision == QPR_MIXED)
-        ctx->backend = QPR_BACKEND_SPARSE;
-    else if (o.backend == QPR_BACKEND_AUTO)
+    if (o.backend == QPR_BACKEND_AUTO)
         ctx->backend = ((double)hval.size() < (double)n * (double)n / 8.0) ? QPR_BACKEND_SPARSE : QPR_BACKEND_DENSE;
     else
         ctx->backend = o.backend;
@@ -619,6 +628,37 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         CREATE_CUDA(cudaMalloc(&ctx->d_c32, np * sizeof(float)));
         CREATE_CUDA(cudaMemcpy(ctx->d_c32, c32.data(), np * sizeof(float), cudaMemcpyHostToDevice));
     }
+    int npairs_tc = 0;
+    if (tc) {
+        CREATE_CUDA(qpr::init_mixed_tc());
+        // H = H0 + H1 + H2, each the BF16 rounding of what the previous left
+        std::vector<__nv_bfloat16> hs(3 * plane, __float2bfloat16_rn(0.0f));
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t q = hptr[i]; q < hptr[i + 1]; ++q) {
+                const double h = hval[q];
+                const __nv_bfloat16 h0 = __double2bfloat16(h);
+                const double r1 = h - (double)__bfloat162float(h0);
+                const __nv_bfloat16 h1 = __double2bfloat16(r1);
+                const double r2 = r1 - (double)__bfloat162float(h1);
+                const __nv_bfloat16 h2 = __double2bfloat16(r2);
+                const size_t o2 = (size_t)i * np + hcol[q];
+                hs[o2] = h0;
+                hs[plane + o2] = h1;
+                hs[2 * plane + o2] = h2;
+            }
+        CREATE_CUDA(cudaMalloc(&ctx->d_hsplit, 3 * plane * sizeof(__nv_bfloat16)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_hsplit, hs.data(), 3 * plane * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_dsplit, 18 * plane * sizeof(__nv_bfloat16)));
+        CREATE_CUDA(cudaMemset(ctx->d_dsplit, 0, 18 * plane * sizeof(__nv_bfloat16)));
+        const int Ttc = np / qpr::kTileTc;
+        std::vector<int2> ptc;
+        for (int I = 0; I < Ttc; ++I)
+            for (int J = I + 1; J < Ttc; ++J) ptc.push_back(make_int2(I, J));
+        for (int I = 0; I < Ttc; ++I) ptc.push_back(make_int2(I, I));
+        npairs_tc = (int)ptc.size();
+        CREATE_CUDA(cudaMalloc(&ctx->d_pairs_tc, ptc.size() * sizeof(int2)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_pairs_tc, ptc.data(), ptc.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
     if (o.precision == QPR_MIXED) {
         CREATE_CUDA(cudaMalloc(&ctx->d_mix64, 4 * plane * sizeof(double)));
         CREATE_CUDA(cudaMemset(ctx->d_mix64, 0, 4 * plane * sizeof(double)));
@@ -680,6 +720,23 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         mw.npairs = (int)pairs.size();
         mw.tiles = T;
         mw.ctl = ctx->d_ctl;
+        mw.nstage_partials = (int)pairs.size();
+        if (tc) {
+            mw.pairs_tc = ctx->d_pairs_tc;
+            mw.npairs_tc = npairs_tc;
+            mw.nstage_partials = npairs_tc;
+            mw.splitD = ctx->d_dsplit;
+            mw.splitA = ctx->d_dsplit + 6 * plane;
+            mw.splitB = ctx->d_dsplit + 12 * plane;
+            const __nv_bfloat16 *ds[3] = {mw.splitD, mw.splitA, mw.splitB};
+            if (!qpr::make_tc_maps(ops, ctx->d_hsplit, ds, &ctx->tcmaps)) {
+                ctx->err = "cuTensorMapEncodeTiled failed";
+                g_create_error = ctx->err;
+                qpr_destroy(ctx);
+                return QPR_E_CUDA;
+            }
+            mw.maps = &ctx->tcmaps;
+        }
     }
     *out = ctx;
     return QPR_OK;

@@ -1,6 +1,8 @@
 // Internal declarations shared by the solver's translation units.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +30,8 @@ struct Ctl {
     long long resid_step;
     double resid_exact; // exact FP64 residual of the last reference refresh (mixed form)
     long long resid_exact_step;
+    int err_timeout;    // a bounded device-side wait gave up
+    int pad_;
 };
 
 // kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
@@ -71,16 +75,34 @@ struct Work {
 // with Work), the reference R = y / tr(y) of the last refresh and F = f(R).
 // FP32 (two np x np planes each): F32 = F, D = y - R, the stage deltas da/db
 // and the RK4 sum S.
+struct TcMaps;
 struct MixedWork {
     double *y, *R, *F;
     float *F32, *D, *da, *db, *S;
     float *g;             // gain of the stage delta, np
     double *g64;          // FP64 gain used by the refresh, np
     double *partials;
-    int2 *pairs;
+    int2 *pairs;          // 32 x 32 tile pairs (refresh and sparse stage kernel)
     int npairs;
     int tiles;
     Ctl *ctl;
+    int nstage_partials;  // residual partials the stage-1 kernel writes
+    // dense backend (tcgen05): 128 x 128 tile pairs and the BF16 split planes
+    // [3 levels][2 planes: Re, -Im][np][np] of the stage-1, stage-2 and
+    // stage-3 inputs (D, da, db); null for the sparse backend
+    int2 *pairs_tc;
+    int npairs_tc;
+    __nv_bfloat16 *splitD, *splitA, *splitB;
+    const TcMaps *maps;   // host pointer, used only by the launch code
+};
+
+constexpr int kTileTc = 128;
+
+// TMA descriptors of the dense mixed stage: H split planes [3][np][np] and
+// the three delta-split buffers.
+struct TcMaps {
+    CUtensorMap h;
+    CUtensorMap d[3];
 };
 
 constexpr int kTileFp64 = 32;
@@ -115,6 +137,11 @@ void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s)
 // One RK4 stage: parts & 1 launches the gain of the stage delta, parts & 2
 // the FP32 sparse stage kernel (3 = both, in that order).
 void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+// Dense backend of the mixed form (stage_mixed_tc.cu).
+cudaError_t init_mixed_tc();
+bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfloat16 *const dsplit[3],
+                  TcMaps *maps);
+void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcMaps &m, cudaStream_t s);
 // Kernel launches per RK4 step and per refresh of the mixed form.
 constexpr int kMixedLaunchesPerStep = 8;
 constexpr int kMixedLaunchesPerRefresh = 5;

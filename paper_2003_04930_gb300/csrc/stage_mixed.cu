@@ -239,7 +239,7 @@ gain_mixed_kernel(DevOps ops, MixedWork w, const float *__restrict__ din) {
     // judged again on the estimate)
     if (STAGE == 2 && blockIdx.x == 0 && ctl->resid_exact_step != ctl->step) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < w.npairs; i += blockDim.x) s += w.partials[i];
+        for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s += w.partials[i];
         s = block_sum_d(s, red);
         if (threadIdx.x == 0) {
             const double r = sqrt(s);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) refresh_trace_kernel(DevOps ops, MixedWor
     }
 }
 
-// Refresh, part 2: R = y = sigma y, D = 0.
+// Refresh, part 2: R = y = sigma y, D = 0 (and its BF16 split, dense backend).
 __global__ void refresh_normalize_kernel(DevOps ops, MixedWork w) {
     if (*(volatile int *)&w.ctl->done) return;  // set before this kernel started, uniform
     const double sig = w.ctl->scale;
@@ -318,6 +318,12 @@ __global__ void refresh_normalize_kernel(DevOps ops, MixedWork w) {
         w.y[i] = v;
         w.R[i] = v;
         w.D[i] = 0.0f;
+    }
+    if (w.splitD) {
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 3 * tot;
+             i += (size_t)gridDim.x * blockDim.x)
+            w.splitD[i] = z;
     }
 }
 
@@ -397,6 +403,10 @@ void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaSt
             case 3: gain_mixed_kernel<3><<<gb, 256, 0, s>>>(ops, w, din); break;
             default: gain_mixed_kernel<4><<<gb, 256, 0, s>>>(ops, w, din); break;
         }
+    }
+    if ((parts & 2) && w.splitD) {
+        launch_mixed_tc(stage, ops, w, *w.maps, s);
+        return;
     }
     if (parts & 2) {
         switch (stage) {

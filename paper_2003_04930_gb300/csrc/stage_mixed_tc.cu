@@ -1,0 +1,439 @@
+// Dense mixed-form RK4 stage on the 5th-generation tensor cores (tcgen05).
+//
+// X = H delta for an FP32 stage delta is formed as a 3-term split-BF16
+// product with FP32 accumulation: H = H0 + H1 + H2 and delta = d0 + d1 + d2
+// (each term the BF16 rounding of what the previous terms left), and
+//     X = sum over i + j <= 2 of H_i d_j
+// (six BF16 products, concatenated along K into one GEMM of depth 6 N; the
+// dropped terms are below 2^-24 relative). Because delta is Hermitian the
+// B operand of output tile J is K-major with rows [Re delta_J ; -Im delta_J],
+// so one MMA with M = 128 (rows of tile I) and N = 256 yields both the real
+// part (columns 0..127) and the imaginary part (128..255) of X_IJ.
+//
+// One CTA owns the tile pair (I, J), I <= J, of 128 x 128 complex tiles and
+// accumulates X_IJ and X_JI in TMEM (2 x 256 FP32 columns = all 512). Warp 0
+// (one thread) streams operand tiles with TMA (128-byte swizzle, two stages),
+// warp 1 (one thread) issues tcgen05.mma and commits to mbarriers, and all
+// eight warps run the fused epilogue: X_JI is staged in shared memory for
+// the transposed read, the Lindblad right-hand side of the delta and the RK4
+// stage update are formed as in the sparse mixed kernel, tile (I, J) and its
+// conjugate transpose are written, together with the BF16 split of the next
+// stage's delta (the B operand of the next GEMM).
+//
+// Every mbarrier wait gives up after a bounded number of polls, sets
+// ctl->err_timeout and skips the rest of the work; TMEM is always released.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "qpr_internal.cuh"
+
+namespace qpr {
+namespace {
+
+constexpr int TB = kTileTc;             // 128
+constexpr int BK = 64;                  // BF16 K per stage: one 128-byte swizzle row
+constexpr int NSTAGE = 2;
+constexpr int A_BYTES = TB * BK * 2;        // 16 KB
+constexpr int B_BYTES = 2 * TB * BK * 2;    // 32 KB (Re rows then -Im rows)
+constexpr int OFF_AI = 0, OFF_AJ = A_BYTES, OFF_BJ = 2 * A_BYTES, OFF_BI = 2 * A_BYTES + B_BYTES;
+constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // 96 KB
+constexpr int NTHREADS = 256;
+constexpr int LDS = 2 * TB + 1;         // staged X_JI row (floats)
+constexpr int SMEM_PIPE = NSTAGE * STAGE_BYTES;
+constexpr int SMEM_EPI = TB * LDS * 4;
+constexpr int SMEM_BYTES = (SMEM_PIPE > SMEM_EPI ? SMEM_PIPE : SMEM_EPI) + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long kSpinLimit = 1ll << 26;
+
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for phase `parity`; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];\n" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];\n" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
+// swizzled layout written by TMA (8 rows x 128 B atoms, 1024 B between
+// 8-row groups).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;     // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &h0, __nv_bfloat16 &h1, __nv_bfloat16 &h2) {
+    h0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h0);
+    h1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(h1);
+    h2 = __float2bfloat16_rn(r2);
+}
+
+// Write the split of one delta entry (a, b) = (re, im) into the B-operand
+// planes [level][plane][row][k] and its mirror (b, a): plane 0 holds Re delta
+// (symmetric), plane 1 holds -Im delta (whose value at (b, a) is +im).
+__device__ __forceinline__ void put_split(__nv_bfloat16 *sp, size_t plane, int ga, int gb, int np, float re,
+                                          float im, bool mirror) {
+    __nv_bfloat16 r0, r1, r2, i0, i1, i2, m0, m1, m2;
+    split3(re, r0, r1, r2);
+    split3(-im, i0, i1, i2);
+    const size_t o = (size_t)ga * np + gb;
+    sp[0 * plane + o] = r0; sp[2 * plane + o] = r1; sp[4 * plane + o] = r2;
+    sp[1 * plane + o] = i0; sp[3 * plane + o] = i1; sp[5 * plane + o] = i2;
+    if (mirror) {
+        split3(im, m0, m1, m2);
+        const size_t t = (size_t)gb * np + ga;
+        sp[0 * plane + t] = r0; sp[2 * plane + t] = r1; sp[4 * plane + t] = r2;
+        sp[1 * plane + t] = m0; sp[3 * plane + t] = m1; sp[5 * plane + t] = m2;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorMap tmH,
+                      const __grid_constant__ CUtensorMap tmIn) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], accum_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int s_done, s_fail;
+    __shared__ double red[NTHREADS / 32];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    Ctl *ctl = w.ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_done = *(volatile int *)&ctl->done;
+        s_fail = 0;
+    }
+    __syncthreads();
+    if (s_done) return;
+
+    const int I = w.pairs_tc[blockIdx.x].x, J = w.pairs_tc[blockIdx.x].y;
+    const bool diag = (I == J);
+    const int np = ops.np;
+    const size_t plane = (size_t)np * np;
+    const int kb_per_seg = np / BK;
+    const int nkb = 6 * kb_per_seg;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 32) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&accum_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t tm_ij = tmem, tm_ji = tmem + 256;
+
+    // split segments s = 0..5: A level i and B level j with i + j <= 2, in the
+    // order (0,2) (1,1) (2,0) (0,1) (1,0) (0,0), one hex digit per segment.
+    // The tensor core's FP32 accumulation does not round to nearest, so its
+    // error grows with every K-step added to a large accumulator: the small
+    // correction products go first and the dominant H0 d0 product last.
+    constexpr uint32_t kSegI = 0x010210u, kSegJ = 0x001012u;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        const uint32_t tx = diag ? (uint32_t)(A_BYTES + B_BYTES) : (uint32_t)STAGE_BYTES;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % NSTAGE;
+            if (kb >= NSTAGE && !mbar_wait(&empty_bar[st], ((kb / NSTAGE) - 1) & 1)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            const int seg = kb / kb_per_seg;
+            const int k0 = (kb - seg * kb_per_seg) * BK;
+            const int li = (int)((kSegI >> (4 * seg)) & 0xFu), lj = (int)((kSegJ >> (4 * seg)) & 0xFu);
+            uint8_t *sb = smem + st * STAGE_BYTES;
+            mbar_expect_tx(&full_bar[st], tx);
+            tma_load_3d(sb + OFF_AI, &tmH, &full_bar[st], k0, I * TB, li);
+            tma_load_4d(sb + OFF_BJ, &tmIn, &full_bar[st], k0, J * TB, 0, lj);
+            tma_load_4d(sb + OFF_BJ + B_BYTES / 2, &tmIn, &full_bar[st], k0, J * TB, 1, lj);
+            if (!diag) {
+                tma_load_3d(sb + OFF_AJ, &tmH, &full_bar[st], k0, J * TB, li);
+                tma_load_4d(sb + OFF_BI, &tmIn, &full_bar[st], k0, I * TB, 0, lj);
+                tma_load_4d(sb + OFF_BI + B_BYTES / 2, &tmIn, &full_bar[st], k0, I * TB, 1, lj);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % NSTAGE;
+            if (!mbar_wait(&full_bar[st], (kb / NSTAGE) & 1)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sb = smem_u32(smem + st * STAGE_BYTES);
+            const uint64_t dAI = sw128_desc(sb + OFF_AI), dBJ = sw128_desc(sb + OFF_BJ);
+            const uint64_t dAJ = sw128_desc(sb + OFF_AJ), dBI = sw128_desc(sb + OFF_BI);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 16 BF16 = 32 bytes along K
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                umma_bf16(tm_ij, dAI + adv, dBJ + adv, acc);
+                if (!diag) umma_bf16(tm_ji, dAJ + adv, dBI + adv, acc);
+            }
+            umma_commit(&empty_bar[st]);
+        }
+        umma_commit(&accum_bar);
+    }
+    __syncwarp();
+
+    // ---- epilogue (all warps) ----
+    const bool ok_acc = mbar_wait(&accum_bar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (!ok_acc || s_fail) {
+        if (tid == 0) atomicExch(&ctl->err_timeout, 1);
+    } else {
+        const int q = warp & 3;             // TMEM lane quarter this warp may read
+        const int h = warp >> 2;            // column half
+        const int row = q * 32 + lane;      // TMEM lane = row of the tile
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        float *sX = reinterpret_cast<float *>(smem);  // X_JI staged as [row][LDS], aliases the pipeline
+        // stage X_JI (or X_IJ on the diagonal): columns [h*128, h*128 + 128)
+        const uint32_t src = (diag ? tm_ij : tm_ji) + lane_off;
+        for (int c = 0; c < 128; c += 32) {
+            float v[32];
+            tmem_ld32(src + (uint32_t)(h * 128 + c), v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sX[row * LDS + h * 128 + c + i] = v[i];
+        }
+        __syncthreads();
+
+        const float om = (float)ops.omega, cm = 1.0f - om;
+        const double dt = ctl->dt;
+        const float dtf = (float)dt;
+        const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
+        float *dnext = (STAGE == 2) ? w.db : w.da;
+        __nv_bfloat16 *snext = (STAGE == 2) ? w.splitB : (STAGE == 4 ? w.splitD : w.splitA);
+        const int a = row, ga = I * TB + a;
+        double nrm = 0.0;
+        for (int c = 0; c < 64; c += 32) {
+            const int b0 = h * 64 + c;
+            float xa[32], xb[32];
+            tmem_ld32(tm_ij + lane_off + (uint32_t)b0, xa);
+            tmem_ld32(tm_ij + lane_off + (uint32_t)(TB + b0), xb);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int b = b0 + j, gb = J * TB + b;
+                const size_t off = (size_t)ga * np + gb;
+                const float Aab = xa[j], Bab = xb[j];
+                const float Aba = sX[b * LDS + a], Bba = sX[b * LDS + TB + a];
+                const float dr = din[off], di = din[plane + off];
+                const float hc = 0.5f * (ops.c32[ga] + ops.c32[gb]);
+                float kdr = cm * (Bab + Bba) - om * hc * dr;
+                const float kdi = -cm * (Aab - Aba) - om * hc * di;
+                if (ga == gb) kdr += om * w.g[ga];
+                const size_t moff = (size_t)gb * np + ga;
+                if (STAGE <= 3) {
+                    const float kr = kdr + w.F32[off], ki = kdi + w.F32[plane + off];
+                    if (STAGE == 1) nrm += (double)kr * kr + (double)ki * ki;
+                    const float Dr = w.D[off], Di = w.D[plane + off];
+                    float sr, si;
+                    if (STAGE == 1) { sr = kdr; si = kdi; }
+                    else { sr = w.S[off] + 2.0f * kdr; si = w.S[plane + off] + 2.0f * kdi; }
+                    const float cst = (STAGE == 3) ? dtf : 0.5f * dtf;
+                    const float nr = Dr + cst * kr, ni = Di + cst * ki;
+                    w.S[off] = sr; w.S[plane + off] = si;
+                    dnext[off] = nr; dnext[plane + off] = ni;
+                    if (!diag) {
+                        w.S[moff] = sr; w.S[plane + moff] = -si;
+                        dnext[moff] = nr; dnext[plane + moff] = -ni;
+                    }
+                    put_split(snext, plane, ga, gb, np, nr, ni, !diag);
+                } else {
+                    const double sr = (double)(w.S[off] + kdr), si = (double)(w.S[plane + off] + kdi);
+                    const double yr = w.y[off] + dt * w.F[off] + (dt / 6.0) * sr;
+                    const double yi = w.y[plane + off] + dt * w.F[plane + off] + (dt / 6.0) * si;
+                    const float Dr = (float)(yr - w.R[off]), Di = (float)(yi - w.R[plane + off]);
+                    w.y[off] = yr; w.y[plane + off] = yi;
+                    w.D[off] = Dr; w.D[plane + off] = Di;
+                    if (!diag) {
+                        w.y[moff] = yr; w.y[plane + moff] = -yi;
+                        w.D[moff] = Dr; w.D[plane + moff] = -Di;
+                    }
+                    put_split(snext, plane, ga, gb, np, Dr, Di, !diag);
+                }
+            }
+        }
+        if (STAGE == 1) {
+            nrm = warp_sum_d(nrm);
+            if (lane == 0) red[warp] = nrm;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (STAGE == 1 && tid == 0 && ok_acc && !s_fail) {
+        double s = 0.0;
+        for (int i = 0; i < NTHREADS / 32; ++i) s += red[i];
+        w.partials[blockIdx.x] = diag ? s : 2.0 * s;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+    if (STAGE == 4 && blockIdx.x == 0 && tid == 0) ctl->step += 1;
+}
+
+template <int STAGE>
+cudaError_t set_attr() {
+    return cudaFuncSetAttribute(stage_mixed_tc_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t init_mixed_tc() {
+    cudaError_t e = set_attr<1>();
+    if (e == cudaSuccess) e = set_attr<2>();
+    if (e == cudaSuccess) e = set_attr<3>();
+    if (e == cudaSuccess) e = set_attr<4>();
+    return e;
+}
+
+// Tensor maps: H planes [3][np][np] and delta-split planes [3][2][np][np],
+// BF16, boxes of 64 (K) x 128 rows, 128-byte swizzle.
+bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfloat16 *const dsplit[3],
+                  TcMaps *maps) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t np = (cuuint64_t)ops.np;
+    {
+        cuuint64_t dims[3] = {np, np, 3};
+        cuuint64_t strides[2] = {np * 2, np * np * 2};
+        cuuint32_t box[3] = {BK, TB, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&maps->h, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)hsplit, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    for (int i = 0; i < 3; ++i) {
+        cuuint64_t dims[4] = {np, np, 2, 3};
+        cuuint64_t strides[3] = {np * 2, np * np * 2, 2 * np * np * 2};
+        cuuint32_t box[4] = {BK, TB, 1, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&maps->d[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)dsplit[i], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+// Stage input split planes: stage 1 D (map 0), stage 2 da (map 1), stage 3
+// db (map 2), stage 4 da (map 1).
+void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcMaps &m, cudaStream_t s) {
+    switch (stage) {
+        case 1: stage_mixed_tc_kernel<1><<<w.npairs_tc, NTHREADS, SMEM_BYTES, s>>>(ops, w, m.h, m.d[0]); break;
+        case 2: stage_mixed_tc_kernel<2><<<w.npairs_tc, NTHREADS, SMEM_BYTES, s>>>(ops, w, m.h, m.d[1]); break;
+        case 3: stage_mixed_tc_kernel<3><<<w.npairs_tc, NTHREADS, SMEM_BYTES, s>>>(ops, w, m.h, m.d[2]); break;
+        default: stage_mixed_tc_kernel<4><<<w.npairs_tc, NTHREADS, SMEM_BYTES, s>>>(ops, w, m.h, m.d[1]); break;
+    }
+}
+
+}  // namespace qpr
