@@ -188,6 +188,38 @@ QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, in
  * ties to the lower index (the ranking of the main text's airline study). */
 QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank);
 
+/* ---- many problems in one batched run ----
+ * One problem of a batch: a weighted edge list (as in qpr_create), its own
+ * omega, and its density matrix rho (N x N complex128, host or device),
+ * read as rho0 and overwritten with the steady state. */
+typedef struct {
+    int64_t n;
+    int64_t m;
+    const int64_t *src;
+    const int64_t *dst;
+    const double *w; /* NULL: unit weights */
+    double omega;
+    void *rho;
+} qpr_problem;
+
+/* Steady states of `count` independent problems (graphs of any sizes and
+ * omegas, shared alpha, dt, tol and options), integrated together by the
+ * mixed-precision RK4 form on the sparse backend (QPR_MIXED; options
+ * h_diag, dangling, ref_refresh, device and cuda_stream apply). Each block
+ * of ref_refresh steps is one set of kernel launches over the tile pairs of
+ * every problem still running; a problem drops out as soon as its exact
+ * FP64 residual passes tol or it reaches max_steps, so problems that
+ * converge early cost nothing afterwards. Every problem's result is bitwise
+ * the one qpr_steady_state returns for it alone with QPR_MIXED and
+ * QPR_BACKEND_SPARSE. stats (nullable) receives one entry per problem
+ * (seconds and kernel_launches are those of the whole call). Returns
+ * QPR_OK when every problem converged, QPR_E_NOT_CONVERGED when some
+ * reached max_steps, QPR_E_NONFINITE, QPR_E_ARG / QPR_E_GRAPH (message of
+ * qpr_last_error(NULL) names the problem), QPR_E_OOM, QPR_E_CUDA,
+ * QPR_E_TIMEOUT. Synchronous. */
+QPR_API qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *problems, double alpha, double dt,
+                                          double tol, int64_t max_steps, const qpr_options *opt, qpr_stats *stats);
+
 /* ---- right-hand side without any allocation ----
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc: hosts that hand out all device memory from

@@ -3,6 +3,7 @@
 // g = G p of the dissipator.
 #include <math.h>
 
+#include "gain_body.cuh"
 #include "qpr_internal.cuh"
 
 namespace qpr {
@@ -10,24 +11,8 @@ namespace {
 
 constexpr int kGainThreads = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Fixed-order block sum, broadcast to every thread (blockDim.x <= 1024).
-__device__ double block_sum(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();  // red may still be read by a previous call
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int q = 0; q < nw; ++q) s += red[q];
-    return s;
-}
+using gain64::block_sum;
+using gain64::warp_sum;
 
 __global__ void import_kernel(const double *__restrict__ rho, int n, int np, double *__restrict__ out) {
     const size_t plane = (size_t)np * np;
@@ -65,93 +50,16 @@ __global__ void diag_kernel(const double *__restrict__ rho, int n, double *__res
         p[i] = rho[2 * ((size_t)i * n + i)];
 }
 
-// g = G p with G = alpha S + (1 - alpha) F (Eq. S2, Eq. S4), p_j = sig Y_jj:
-//   (S p)_i = sum_{j with out-links} A_ij / outDeg(j) p_j  +  dangling part,
-//   dangling part = (D - [i dangles] p_i) / (N - 1)  (F columns)  or  D / N,
-//   (F p)_i = (P - p_i) / (N - 1),
-// with P = sum_j p_j and D = sum over dangling j of p_j.
-// Stage 1 also fixes sig = 1 / Re tr(y) for the whole step. Stage 2 first
-// reduces the residual partials of stage 1 into ||f(y_n)||_F and takes the
-// stop decision (one CTA).
 template <int STAGE>
 __global__ void __launch_bounds__(kGainThreads)
 gain_kernel(DevOps ops, Work w, const double *__restrict__ yin) {
-    __shared__ double red[kGainThreads / 32];
     __shared__ int s_done;
-    Ctl *ctl = w.ctl;
     // CTA 0 of this very kernel may set `done` while other CTAs start: read
     // it once per CTA so that every thread of a CTA takes the same branch.
-    if (threadIdx.x == 0) s_done = *(volatile int *)&ctl->done;
+    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
     __syncthreads();
     if (s_done) return;
-    const int n = ops.n, np = ops.np;
-
-    if (STAGE == 2 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < w.npairs; i += blockDim.x) s += w.partials[i];
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) {
-            const double r = sqrt(s);
-            ctl->resid = r;
-            ctl->resid_step = ctl->step;
-            if (!isfinite(r)) {
-                ctl->status = kCtlNonFinite;
-                ctl->done = 1;
-            } else if (r < ctl->tol) {
-                ctl->status = kCtlConverged;
-                ctl->done = 1;
-            } else if (ctl->step >= ctl->max_steps) {
-                ctl->status = kCtlMaxSteps;
-                ctl->done = 1;
-            }
-        }
-    }
-
-    double P = 0.0, D = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double pj = yin[(size_t)j * np + j];
-        P += pj;
-        if (ops.dang[j]) D += pj;
-    }
-    P = block_sum(P, red);
-    D = block_sum(D, red);
-    double sig = 1.0;
-    if (STAGE == 1) {
-        sig = 1.0 / P;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->scale = sig;
-            ctl->trace = P;
-            if (!(P > 0.0) || !isfinite(P)) {
-                ctl->status = kCtlNonFinite;
-                ctl->done = 1;
-            }
-        }
-    }
-    const double Ps = sig * P, Ds = sig * D;
-    const double inv_nm1 = 1.0 / (double)(n - 1);
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < np; i += gridDim.x * wpb) {
-        double s = 0.0;
-        if (i < n) {
-            for (int q = ops.s_ptr[i] + lane; q < ops.s_ptr[i + 1]; q += 32) {
-                const int j = ops.s_col[q];
-                s += ops.s_val[q] * (sig * yin[(size_t)j * np + j]);
-            }
-        }
-        s = warp_sum(s);
-        if (lane == 0) {
-            double gi = 0.0;
-            if (i < n) {
-                const double pi = sig * yin[(size_t)i * np + i];
-                const double dterm = (ops.dangling == QPR_DANGLING_F)
-                                         ? (Ds - (ops.dang[i] ? pi : 0.0)) * inv_nm1
-                                         : Ds / (double)n;
-                gi = ops.alpha * (s + dterm) + (1.0 - ops.alpha) * (Ps - pi) * inv_nm1;
-            }
-            w.g[i] = gi;
-        }
-    }
+    gain64::gain_fp64_body<STAGE>(ops, w, yin, blockIdx.x, gridDim.x);
 }
 
 int grid_for(size_t work, int threads) {

@@ -1,0 +1,523 @@
+// Batched steady-state solver: many independent problems (graphs of uneven
+// N, each with its own omega) integrated together by the mixed-precision RK4
+// form.
+//
+// Every problem keeps its own operators, buffers and control block; a
+// device array of per-problem descriptors lets one kernel launch serve all of
+// them. Work is described by lists the host compacts after every block of
+// steps: the active problems (one CTA per problem for the gain, trace and
+// residual kernels) and the (problem, I, J) tile pairs of the active problems
+// (grid-stride persistent kernels for the stage and refresh products). A
+// problem leaves the lists as soon as its exact FP64 residual passes (or it
+// hits max_steps), so converged problems cost nothing afterwards. The
+// per-tile and per-problem arithmetic is the single-problem code (the same
+// device functions in the same order), so every problem's result is bitwise
+// the one qpr_steady_state returns for it alone with the same options.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "gain_body.cuh"
+#include "mixed_body.cuh"
+#include "qpr_internal.cuh"
+#include "sparse_body.cuh"
+
+namespace qpr {
+
+struct BatchGraph {
+    DevOps ops;
+    MixedWork mw;
+    Work w64;  // the FP64 refresh: y = R, z = F
+};
+static_assert(sizeof(BatchGraph) % 4 == 0, "descriptor copied as 32-bit words");
+
+namespace {
+
+constexpr int kStageNT = 256;  // threads of the mixed stage kernel (mixed_body.cuh)
+
+// Copy problem g's descriptor into shared memory (all threads; ends synced).
+__device__ __forceinline__ void load_graph(const BatchGraph *gs, int g, BatchGraph &sg) {
+    const int *src = reinterpret_cast<const int *>(gs + g);
+    int *dst = reinterpret_cast<int *>(&sg);
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchGraph) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+// 1 if problem `sg` has stopped; the same value for every thread of the CTA.
+__device__ __forceinline__ int graph_done(const BatchGraph &sg, int *s_flag) {
+    if (threadIdx.x == 0) *s_flag = *(volatile int *)&sg.mw.ctl->done;
+    __syncthreads();
+    return *s_flag;
+}
+
+__global__ void __launch_bounds__(256) b_trace_kernel(const BatchGraph *gs, const int *act) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    load_graph(gs, act[blockIdx.x], sg);
+    if (graph_done(sg, &s_flag)) return;
+    mixed::refresh_trace_body(sg.ops, sg.mw);
+}
+
+__global__ void __launch_bounds__(256) b_normalize_kernel(const BatchGraph *gs, const int *act) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    load_graph(gs, act[blockIdx.y], sg);
+    if (graph_done(sg, &s_flag)) return;
+    mixed::refresh_normalize_body(sg.ops, sg.mw, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                                  (size_t)gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(256) b_gain64_kernel(const BatchGraph *gs, const int *act) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    load_graph(gs, act[blockIdx.x], sg);
+    if (graph_done(sg, &s_flag)) return;
+    gain64::gain_fp64_body<0>(sg.ops, sg.w64, sg.w64.y, 0, 1);
+}
+
+__global__ void __launch_bounds__(sparse64::NTHREADS)
+b_sparse64_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 t = items[it];
+        load_graph(gs, t.x, sg);
+        if (!graph_done(sg, &s_flag)) sparse64::tile<0>(sg.ops, sg.w64, t.y, t.z, t.w, t.w == 0, smem);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const int *act) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    load_graph(gs, act[blockIdx.y], sg);
+    if (graph_done(sg, &s_flag)) return;
+    mixed::refresh_post_body(sg.ops, sg.mw, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                             (size_t)gridDim.x * blockDim.x, blockIdx.x == 0);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) b_gain_mixed_kernel(const BatchGraph *gs, const int *act) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    load_graph(gs, act[blockIdx.x], sg);
+    if (graph_done(sg, &s_flag)) return;
+    const float *din = (STAGE == 1) ? sg.mw.D : (STAGE == 3 ? sg.mw.db : sg.mw.da);
+    mixed::gain_mixed_body<STAGE>(sg.ops, sg.mw, din, 0, 1);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 t = items[it];
+        load_graph(gs, t.x, sg);
+        if (!graph_done(sg, &s_flag)) mixed::mixed_sparse_tile<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0);
+        __syncthreads();
+    }
+}
+
+struct Lists {
+    int *act;      // device, active problem indices
+    int4 *items;   // device, (problem, I, J, pair index) of the active problems
+    int nact, nitems;
+};
+
+int elem_chunks(int np) {
+    const size_t tot = 2 * (size_t)np * np;
+    size_t c = (tot + 256 * 8 - 1) / (256 * 8);
+    return (int)std::min<size_t>(std::max<size_t>(c, 1), 64);
+}
+
+void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream_t s, int64_t &launches) {
+    if (L.nact == 0) return;
+    const dim3 eg(elem_chunks(max_np), L.nact);
+    b_trace_kernel<<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_normalize_kernel<<<eg, 256, 0, s>>>(gs, L.act);
+    b_gain64_kernel<<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_sparse64_kernel<<<std::min(L.nitems, 152 * 3), sparse64::NTHREADS, sparse64::SMEM_BYTES, s>>>(gs, L.items,
+                                                                                                     L.nitems);
+    b_post_kernel<<<eg, 256, 0, s>>>(gs, L.act);
+    launches += 5;
+}
+
+void launch_step(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
+    const int grid = std::min(L.nitems, 152 * 5);
+    b_gain_mixed_kernel<1><<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_stage_mixed_kernel<1><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
+    b_gain_mixed_kernel<2><<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_stage_mixed_kernel<2><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
+    b_gain_mixed_kernel<3><<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_stage_mixed_kernel<3><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
+    b_gain_mixed_kernel<4><<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_stage_mixed_kernel<4><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
+    launches += 8;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool is_device_ptr_b(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// RAII owner of every device/pinned allocation of one batched call.
+struct BatchMem {
+    std::vector<void *> dev;
+    void *pinned = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~BatchMem() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void *p : dev) cudaFree(p);
+        if (pinned) cudaFreeHost(pinned);
+        if (ev) cudaEventDestroy(ev);
+        if (stream) cudaStreamDestroy(stream);
+        cudaGetLastError();
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            dev.push_back(q);
+            *p = (T *)q;
+        }
+        return e;
+    }
+};
+
+}  // namespace
+
+cudaError_t init_batch() {
+    return cudaFuncSetAttribute(b_sparse64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sparse64::SMEM_BYTES);
+}
+
+}  // namespace qpr
+
+using qpr::BatchGraph;
+using qpr::Ctl;
+
+extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *problems, double alpha, double dt,
+                                             double tol, int64_t max_steps, const qpr_options *opt,
+                                             qpr_stats *stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    auto err = [&](qpr_status st, const std::string &msg) {
+        qpr::set_create_error(msg);
+        return st;
+    };
+    if (count < 1 || !problems) return err(QPR_E_ARG, "count must be >= 1 and problems non-NULL");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return err(QPR_E_ARG, "alpha must lie in [0, 1]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return err(QPR_E_ARG, "dt must be positive and finite");
+    if (!(tol > 0.0)) return err(QPR_E_ARG, "tol must be positive");
+    if (max_steps < 0) return err(QPR_E_ARG, "max_steps must be non-negative");
+    qpr_options o;
+    qpr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.ref_refresh < 1 || o.ref_refresh > 4096) return err(QPR_E_ARG, "ref_refresh outside [1, 4096]");
+    if (o.h_diag != QPR_HDIAG_ZERO && o.h_diag != QPR_HDIAG_NEG_OUTDEG) return err(QPR_E_ARG, "unknown h_diag mode");
+    if (o.dangling != QPR_DANGLING_F && o.dangling != QPR_DANGLING_UNIFORM)
+        return err(QPR_E_ARG, "unknown dangling mode");
+
+    // ---- host assembly, per problem ----
+    const size_t G = (size_t)count;
+    std::vector<qpr::HostOps> H(G);
+    std::vector<int> np(G), T(G), npairs(G);
+    std::vector<double> hdt(G);
+    std::vector<int64_t> msub(G);
+    for (size_t g = 0; g < G; ++g) {
+        const qpr_problem &p = problems[g];
+        if (p.n < 2 || p.n > 65536) return err(QPR_E_ARG, "problem " + std::to_string(g) + ": n outside [2, 65536]");
+        if (!(p.omega >= 0.0 && p.omega <= 1.0))
+            return err(QPR_E_ARG, "problem " + std::to_string(g) + ": omega must lie in [0, 1]");
+        if (!p.rho) return err(QPR_E_ARG, "problem " + std::to_string(g) + ": rho is NULL");
+        if (p.m < 0 || (p.m > 0 && (!p.src || !p.dst)))
+            return err(QPR_E_ARG, "problem " + std::to_string(g) + ": edge arrays missing");
+        std::string aerr;
+        const qpr_status ast = qpr::assemble_host(p.n, p.m, p.src, p.dst, p.w, o.h_diag, H[g], aerr);
+        if (ast != QPR_OK) return err(ast, "problem " + std::to_string(g) + ": " + aerr);
+        np[g] = (int)(((p.n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
+        T[g] = np[g] / qpr::kTileFp64;
+        npairs[g] = T[g] * (T[g] + 1) / 2;
+        double cmax = 0.0;
+        qpr::column_sums_G(H[g], alpha, np[g], &cmax);
+        const double spread = qpr::estimate_spread(p.n, H[g].hptr, H[g].hcol, H[g].hval);
+        const double rate = (1.0 - p.omega) * spread + 2.0 * p.omega * cmax;
+        const double dmax = rate > 0.0 ? 2.5 / rate : INFINITY;
+        msub[g] = (dt > dmax) ? (int64_t)ceil(dt / dmax) : 1;
+        hdt[g] = dt / (double)msub[g];
+    }
+
+    // ---- arena layout (elements), every sub-array aligned to 64 elements ----
+    std::vector<size_t> od(G), of(G), oi(G), ob(G);
+    size_t nd = 0, nf = 0, ni = 0, nb = 0, max_nn = 0;
+    int max_np = 0;
+    for (size_t g = 0; g < G; ++g) {
+        const size_t p2 = 2 * (size_t)np[g] * np[g];
+        const size_t nh = H[g].hval.size(), ns = H[g].sval.size(), n = (size_t)problems[g].n;
+        od[g] = nd;
+        nd += qpr::align_up(3 * p2 + 2 * np[g] + nh + ns + npairs[g], 64);
+        of[g] = nf;
+        nf += qpr::align_up(5 * p2 + 2 * np[g] + qpr::align_up(nh, 64), 64) + 64;
+        oi[g] = ni;
+        ni += qpr::align_up(2 * (n + 1) + nh + ns, 64);
+        ob[g] = nb;
+        nb += qpr::align_up(n, 64);
+        max_nn = std::max(max_nn, n * n);
+        max_np = std::max(max_np, np[g]);
+    }
+
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return err(QPR_E_CUDA, "no CUDA device available");
+    }
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != dev) cudaSetDevice(dev);
+    struct Restore {
+        int d;
+        ~Restore() {
+            if (d >= 0) cudaSetDevice(d);
+        }
+    } restore{prev_dev != dev ? prev_dev : -1};
+
+    qpr::BatchMem mem;
+    double *dD = nullptr;
+    float *dF = nullptr;
+    int *dI = nullptr;
+    unsigned char *dB = nullptr;
+    Ctl *dCtl = nullptr;
+    BatchGraph *dG = nullptr;
+    int *dAct = nullptr;
+    int4 *dItems = nullptr;
+    double *dIO = nullptr;
+    size_t total_pairs = 0;
+    for (size_t g = 0; g < G; ++g) total_pairs += npairs[g];
+#define BCUDA(call)                                                                             \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return err(e_ == cudaErrorMemoryAllocation ? QPR_E_OOM : QPR_E_CUDA,                \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+    BCUDA(qpr::init_stage_sparse());
+    BCUDA(qpr::init_batch());
+    BCUDA(mem.alloc(&dD, nd));
+    BCUDA(mem.alloc(&dF, nf));
+    BCUDA(mem.alloc(&dI, ni));
+    BCUDA(mem.alloc(&dB, nb));
+    BCUDA(mem.alloc(&dCtl, G));
+    BCUDA(mem.alloc(&dG, G));
+    BCUDA(mem.alloc(&dAct, G));
+    BCUDA(mem.alloc(&dItems, total_pairs));
+    BCUDA(mem.alloc(&dIO, 2 * max_nn));
+    BCUDA(cudaMemset(dD, 0, nd * sizeof(double)));
+    BCUDA(cudaMemset(dF, 0, nf * sizeof(float)));
+    BCUDA(cudaStreamCreateWithFlags(&mem.stream, cudaStreamNonBlocking));
+    BCUDA(cudaEventCreateWithFlags(&mem.ev, cudaEventDisableTiming));
+    BCUDA(cudaMallocHost(&mem.pinned, G * sizeof(Ctl)));
+    cudaStream_t s = mem.stream;
+    BCUDA(cudaEventRecord(mem.ev, (cudaStream_t)o.cuda_stream));
+    BCUDA(cudaStreamWaitEvent(s, mem.ev, 0));
+
+    // ---- fill and upload the operators, build the descriptors ----
+    std::vector<double> hD(nd, 0.0);
+    std::vector<float> hF(nf, 0.0f);
+    std::vector<int> hI(ni, 0);
+    std::vector<unsigned char> hB(nb, 0);
+    std::vector<BatchGraph> desc(G);
+    Ctl *hCtl = (Ctl *)mem.pinned;
+    memset(hCtl, 0, G * sizeof(Ctl));
+    for (size_t g = 0; g < G; ++g) {
+        const qpr::HostOps &h = H[g];
+        const int n = (int)problems[g].n, p = np[g];
+        const size_t p2 = 2 * (size_t)p * p, nh = h.hval.size(), ns = h.sval.size();
+        double *bd = dD + od[g];
+        float *bf = dF + of[g];
+        int *bi = dI + oi[g];
+        // double arena: y R F | g64 c | hval sval | partials
+        double *y = bd, *R = bd + p2, *F = bd + 2 * p2, *g64 = bd + 3 * p2, *c = g64 + p;
+        double *hval = c + p, *sval = hval + nh, *part = sval + ns;
+        std::vector<double> cg = qpr::column_sums_G(h, alpha, p, nullptr);
+        std::copy(cg.begin(), cg.end(), hD.begin() + (c - dD));
+        std::copy(h.hval.begin(), h.hval.end(), hD.begin() + (hval - dD));
+        std::copy(h.sval.begin(), h.sval.end(), hD.begin() + (sval - dD));
+        // float arena: F32 D da db S | g32 c32 | hval32
+        float *F32 = bf, *Dp = bf + p2, *da = bf + 2 * p2, *db = bf + 3 * p2, *S = bf + 4 * p2;
+        float *g32 = bf + 5 * p2, *c32 = g32 + p, *hv32 = c32 + p;
+        for (int j = 0; j < p; ++j) hF[(c32 - dF) + j] = (float)cg[j];
+        for (size_t q = 0; q < nh; ++q) hF[(hv32 - dF) + q] = (float)h.hval[q];
+        // int arena: hptr hcol sptr scol
+        int *hptr = bi, *hcol = hptr + (n + 1), *sptr = hcol + nh, *scol = sptr + (n + 1);
+        for (int i = 0; i <= n; ++i) hI[(hptr - dI) + i] = (int)h.hptr[i];
+        std::copy(h.hcol.begin(), h.hcol.end(), hI.begin() + (hcol - dI));
+        std::copy(h.sptr.begin(), h.sptr.end(), hI.begin() + (sptr - dI));
+        std::copy(h.scol.begin(), h.scol.end(), hI.begin() + (scol - dI));
+        std::copy(h.dang.begin(), h.dang.end(), hB.begin() + ob[g]);
+
+        BatchGraph &d = desc[g];
+        memset(&d, 0, sizeof(d));
+        d.ops.n = n;
+        d.ops.np = p;
+        d.ops.alpha = alpha;
+        d.ops.omega = problems[g].omega;
+        d.ops.dangling = o.dangling;
+        d.ops.H = nullptr;
+        d.ops.h_ptr = hptr;
+        d.ops.h_col = hcol;
+        d.ops.h_val = hval;
+        d.ops.h_val32 = hv32;
+        d.ops.s_ptr = sptr;
+        d.ops.s_col = scol;
+        d.ops.s_val = sval;
+        d.ops.dang = dB + ob[g];
+        d.ops.c = c;
+        d.ops.c32 = c32;
+        qpr::MixedWork &mw = d.mw;
+        mw.y = y; mw.R = R; mw.F = F;
+        mw.F32 = F32; mw.D = Dp; mw.da = da; mw.db = db; mw.S = S;
+        mw.g = g32; mw.g64 = g64; mw.partials = part;
+        mw.pairs = nullptr; mw.npairs = npairs[g]; mw.tiles = T[g];
+        mw.ctl = dCtl + g;
+        mw.nstage_partials = npairs[g];
+        qpr::Work &w = d.w64;
+        w.y = R; w.z = F; w.ya = R; w.yb = R; w.g = g64; w.partials = part;
+        w.pairs = nullptr; w.npairs = npairs[g]; w.tiles = T[g]; w.ctl = dCtl + g;
+        Ctl &k = hCtl[g];
+        k.max_steps = max_steps;
+        k.tol = tol;
+        k.dt = hdt[g];
+        k.scale = 1.0;
+        k.resid_exact_step = -1;
+    }
+    BCUDA(cudaMemcpyAsync(dD, hD.data(), nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    BCUDA(cudaMemcpyAsync(dF, hF.data(), nf * sizeof(float), cudaMemcpyHostToDevice, s));
+    BCUDA(cudaMemcpyAsync(dI, hI.data(), ni * sizeof(int), cudaMemcpyHostToDevice, s));
+    BCUDA(cudaMemcpyAsync(dB, hB.data(), nb, cudaMemcpyHostToDevice, s));
+    BCUDA(cudaMemcpyAsync(dG, desc.data(), G * sizeof(BatchGraph), cudaMemcpyHostToDevice, s));
+    BCUDA(cudaMemcpyAsync(dCtl, hCtl, G * sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    int64_t launches = 0;
+    // ---- initial states ----
+    for (size_t g = 0; g < G; ++g) {
+        const int n = (int)problems[g].n;
+        const double *srcp = (const double *)problems[g].rho;
+        if (!qpr::is_device_ptr_b(problems[g].rho)) {
+            BCUDA(cudaMemcpyAsync(dIO, problems[g].rho, (size_t)n * n * 16, cudaMemcpyHostToDevice, s));
+            srcp = dIO;
+        }
+        qpr::launch_import(srcp, n, np[g], desc[g].mw.y, s);
+        ++launches;
+    }
+    BCUDA(cudaStreamSynchronize(s));  // hD, hF, ... and the staging buffer may be released / reused
+
+    // ---- blocks of (exact refresh + ref_refresh delta steps) ----
+    std::vector<int> active(G);
+    for (size_t g = 0; g < G; ++g) active[g] = (int)g;
+    std::vector<int4> items;
+    items.reserve(total_pairs);
+    auto make_lists = [&](const std::vector<int> &list, qpr::Lists &L) -> cudaError_t {
+        items.clear();
+        for (int g : list) {
+            int q = 0;
+            for (int I = 0; I < T[g]; ++I)
+                for (int J = I + 1; J < T[g]; ++J) items.push_back(make_int4(g, I, J, q++));
+            for (int I = 0; I < T[g]; ++I) items.push_back(make_int4(g, I, I, q++));
+        }
+        L.act = dAct;
+        L.items = dItems;
+        L.nact = (int)list.size();
+        L.nitems = (int)items.size();
+        cudaError_t e = cudaMemcpyAsync(dAct, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dItems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        // the host vectors are reused: wait until both copies have read them
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    };
+    bool timeout = false;
+    while (!active.empty()) {
+        qpr::Lists L{};
+        BCUDA(make_lists(active, L));
+        qpr::launch_refresh(dG, L, max_np, s, launches);
+        for (int k = 0; k < o.ref_refresh; ++k) qpr::launch_step(dG, L, s, launches);
+        BCUDA(cudaMemcpyAsync(hCtl, dCtl, G * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        BCUDA(cudaStreamSynchronize(s));
+        BCUDA(cudaGetLastError());
+        std::vector<int> keep, confirm;
+        for (int g : active) {
+            const Ctl &k = hCtl[g];
+            if (k.err_timeout) timeout = true;
+            if (!k.done) keep.push_back(g);
+            else if (k.status == qpr::kCtlNonFinite) continue;
+            else if (k.resid_exact_step == k.step) continue;  // decided by an exact refresh
+            else confirm.push_back(g);
+        }
+        if (!confirm.empty()) {
+            for (int g : confirm) {
+                hCtl[g].done = 0;
+                hCtl[g].status = qpr::kCtlRunning;
+            }
+            BCUDA(cudaMemcpyAsync(dCtl, hCtl, G * sizeof(Ctl), cudaMemcpyHostToDevice, s));
+            qpr::Lists Lc{};
+            BCUDA(make_lists(confirm, Lc));
+            qpr::launch_refresh(dG, Lc, max_np, s, launches);
+            BCUDA(cudaMemcpyAsync(hCtl, dCtl, G * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            BCUDA(cudaStreamSynchronize(s));
+            BCUDA(cudaGetLastError());
+            for (int g : confirm)
+                if (!hCtl[g].done) keep.push_back(g);
+        }
+        std::sort(keep.begin(), keep.end());
+        active.swap(keep);
+    }
+
+    // ---- results ----
+    qpr_status ret = QPR_OK;
+    for (size_t g = 0; g < G; ++g) {
+        const int n = (int)problems[g].n;
+        if (qpr::is_device_ptr_b(problems[g].rho)) {
+            qpr::launch_export(desc[g].mw.R, n, np[g], dCtl + g, 0, (double *)problems[g].rho, s);
+        } else {
+            qpr::launch_export(desc[g].mw.R, n, np[g], dCtl + g, 0, dIO, s);
+            BCUDA(cudaMemcpyAsync(problems[g].rho, dIO, (size_t)n * n * 16, cudaMemcpyDeviceToHost, s));
+        }
+        ++launches;
+        BCUDA(cudaStreamSynchronize(s));
+        const Ctl &k = hCtl[g];
+        if (k.status == qpr::kCtlNonFinite) ret = QPR_E_NONFINITE;
+        else if (k.status != qpr::kCtlConverged && ret == QPR_OK) ret = QPR_E_NOT_CONVERGED;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) {
+        for (size_t g = 0; g < G; ++g) {
+            const Ctl &k = hCtl[g];
+            qpr_stats &st = stats[g];
+            memset(&st, 0, sizeof(st));
+            st.steps = k.step;
+            st.substeps_m = msub[g];
+            st.t = (double)k.step * hdt[g];
+            st.residual = k.resid_exact;
+            st.trace_before = k.trace;
+            st.seconds = secs;
+            st.kernel_launches = launches;
+            st.converged = (k.status == qpr::kCtlConverged) ? 1 : 0;
+        }
+    }
+#undef BCUDA
+    if (timeout) return err(QPR_E_TIMEOUT, "a device-side wait gave up");
+    if (ret == QPR_E_NONFINITE) return err(ret, "a problem produced a non-finite trace or residual");
+    if (ret == QPR_E_NOT_CONVERGED) return err(ret, "some problems reached max_steps");
+    return QPR_OK;
+}

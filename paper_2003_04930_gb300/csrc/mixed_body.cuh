@@ -1,0 +1,334 @@
+// Device functions of the mixed-precision form (sparse backend and the
+// refresh), shared by the single-problem kernels and the batched kernels.
+#pragma once
+
+#include <math.h>
+
+#include "qpr_internal.cuh"
+
+namespace qpr {
+namespace mixed {
+
+constexpr int TS = 32;
+constexpr int NT = 256;           // threads per CTA
+constexpr int LDX = 2 * TS + 1;   // X tile row: real part, then imaginary part
+constexpr int LDO = TS + 1;
+
+__device__ __forceinline__ float4 f4fma(float h, float4 v, float4 acc) {
+    acc.x = fmaf(h, v.x, acc.x);
+    acc.y = fmaf(h, v.y, acc.y);
+    acc.z = fmaf(h, v.z, acc.z);
+    acc.w = fmaf(h, v.w, acc.w);
+    return acc;
+}
+__device__ __forceinline__ float4 f4xor(float4 v, int m) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+    v.z += __shfl_xor_sync(0xffffffffu, v.z, m);
+    v.w += __shfl_xor_sync(0xffffffffu, v.w, m);
+    return v;
+}
+
+// sX[a][b] = (H Re d)_ab, sX[a][TS + b] = (H Im d)_ab for rows of tile rt and
+// columns of tile ct, in FP32.
+__device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__restrict__ d, size_t plane,
+                                            int rt, int ct, float *sX) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 3, sub = lane & 7;
+    const int np = ops.np, n = ops.n;
+    const float *__restrict__ re = d + ct * TS + 4 * sub;
+    const float *__restrict__ im = d + plane + ct * TS + 4 * sub;
+    for (int a = warp; a < TS; a += NT / 32) {
+        const int ga = rt * TS + a;
+        float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
+        if (ga < n) {
+            const int q1 = ops.h_ptr[ga + 1];
+            int q = ops.h_ptr[ga] + grp;
+            for (; q + 4 < q1; q += 8) {
+                const int k0 = ops.h_col[q], k1 = ops.h_col[q + 4];
+                const float h0 = ops.h_val32[q], h1 = ops.h_val32[q + 4];
+                const float4 r0 = *reinterpret_cast<const float4 *>(re + (size_t)k0 * np);
+                const float4 i0 = *reinterpret_cast<const float4 *>(im + (size_t)k0 * np);
+                const float4 r1 = *reinterpret_cast<const float4 *>(re + (size_t)k1 * np);
+                const float4 i1 = *reinterpret_cast<const float4 *>(im + (size_t)k1 * np);
+                xr = f4fma(h0, r0, xr);
+                xi = f4fma(h0, i0, xi);
+                xr = f4fma(h1, r1, xr);
+                xi = f4fma(h1, i1, xi);
+            }
+            if (q < q1) {
+                const int k0 = ops.h_col[q];
+                const float h0 = ops.h_val32[q];
+                xr = f4fma(h0, *reinterpret_cast<const float4 *>(re + (size_t)k0 * np), xr);
+                xi = f4fma(h0, *reinterpret_cast<const float4 *>(im + (size_t)k0 * np), xi);
+            }
+        }
+        xr = f4xor(xr, 8);
+        xr = f4xor(xr, 16);
+        xi = f4xor(xi, 8);
+        xi = f4xor(xi, 16);
+        if (grp == 0) {
+            float *row = sX + a * LDX;
+            row[4 * sub + 0] = xr.x; row[4 * sub + 1] = xr.y; row[4 * sub + 2] = xr.z; row[4 * sub + 3] = xr.w;
+            row[TS + 4 * sub + 0] = xi.x; row[TS + 4 * sub + 1] = xi.y;
+            row[TS + 4 * sub + 2] = xi.z; row[TS + 4 * sub + 3] = xi.w;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One tile pair (I, J) of stage STAGE of the sparse mixed form; pidx is the
+// slot of its residual partial, first marks the pair that advances the step
+// counter. Ends with a barrier so that the caller may reuse shared memory.
+template <int STAGE>
+__device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                  bool first) {
+    __shared__ __align__(16) float sX1[TS * LDX];
+    __shared__ __align__(16) float sX2[TS * LDX];
+    // outputs of tile (I, J) kept for the mirrored write: stages 1-3 keep S and
+    // the next delta (4 FP32 planes), stage 4 the new y (2 FP64 planes) and D
+    // (2 FP32 planes); 25.3 KB either way
+    __shared__ __align__(16) double sOraw[(2 * TS * LDO * 8 + 2 * TS * LDO * 4) / 8];
+    double *sO64 = sOraw;
+    float *sO32 = (STAGE == 4) ? reinterpret_cast<float *>(sOraw + 2 * TS * LDO) : reinterpret_cast<float *>(sOraw);
+    __shared__ double red[NT / 32];
+    const bool diag = (I == J);
+    const int np = ops.np;
+    const size_t plane = (size_t)np * np;
+    const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
+    float *dnext = (STAGE == 2) ? w.db : w.da;
+
+    spmm32_tile(ops, din, plane, I, J, sX1);
+    if (!diag) spmm32_tile(ops, din, plane, J, I, sX2);
+    __syncthreads();
+    const float *X2 = diag ? sX1 : sX2;
+
+    const float om = (float)ops.omega, cm = 1.0f - om;
+    const double dt = w.ctl->dt;
+    const float dtf = (float)dt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double nrm = 0.0;
+    for (int e = tid; e < TS * TS; e += NT) {
+        const int a = e / TS, b = e - (e / TS) * TS;
+        const int ga = I * TS + a, gb = J * TS + b;
+        const size_t off = (size_t)ga * np + gb;
+        const float Aab = sX1[a * LDX + b], Bab = sX1[a * LDX + TS + b];
+        const float Aba = X2[b * LDX + a], Bba = X2[b * LDX + TS + a];
+        const float dr = din[off], di = din[plane + off];
+        // kd = f(delta) in FP32; k = F + kd. Explicit round-to-nearest
+        // intrinsics: the same rounding in every kernel inlining this code.
+        const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(ops.c32[ga], ops.c32[gb])));
+        float kdr = __fmaf_rn(-omhc, dr, __fmul_rn(cm, __fadd_rn(Bab, Bba)));
+        const float kdi = __fmaf_rn(-omhc, di, __fmul_rn(-cm, __fsub_rn(Aab, Aba)));
+        if (ga == gb) kdr = __fmaf_rn(om, w.g[ga], kdr);
+        if (STAGE <= 3) {
+            const float kr = __fadd_rn(kdr, w.F32[off]), ki = __fadd_rn(kdi, w.F32[plane + off]);
+            if (STAGE == 1) nrm = __fma_rn((double)kr, (double)kr, __fma_rn((double)ki, (double)ki, nrm));
+            const float Dr = w.D[off], Di = w.D[plane + off];
+            float sr, si;
+            if (STAGE == 1) { sr = kdr; si = kdi; }
+            else { sr = __fmaf_rn(2.0f, kdr, w.S[off]); si = __fmaf_rn(2.0f, kdi, w.S[plane + off]); }
+            const float cst = (STAGE == 3) ? dtf : __fmul_rn(0.5f, dtf);
+            const float nr = __fmaf_rn(cst, kr, Dr), ni = __fmaf_rn(cst, ki, Di);
+            w.S[off] = sr; w.S[plane + off] = si;
+            dnext[off] = nr; dnext[plane + off] = ni;
+            sO32[0 * TS * LDO + a * LDO + b] = sr;
+            sO32[1 * TS * LDO + a * LDO + b] = si;
+            sO32[2 * TS * LDO + a * LDO + b] = nr;
+            sO32[3 * TS * LDO + a * LDO + b] = ni;
+        } else {
+            const double sr = (double)__fadd_rn(w.S[off], kdr), si = (double)__fadd_rn(w.S[plane + off], kdi);
+            const double dt6 = __ddiv_rn(dt, 6.0);
+            const double yr = __fma_rn(dt6, sr, __fma_rn(dt, w.F[off], w.y[off]));
+            const double yi = __fma_rn(dt6, si, __fma_rn(dt, w.F[plane + off], w.y[plane + off]));
+            const float Dr = (float)__dsub_rn(yr, w.R[off]), Di = (float)__dsub_rn(yi, w.R[plane + off]);
+            w.y[off] = yr; w.y[plane + off] = yi;
+            w.D[off] = Dr; w.D[plane + off] = Di;
+            sO64[0 * TS * LDO + a * LDO + b] = yr;
+            sO64[1 * TS * LDO + a * LDO + b] = yi;
+            sO32[0 * TS * LDO + a * LDO + b] = Dr;
+            sO32[1 * TS * LDO + a * LDO + b] = Di;
+        }
+    }
+    if (STAGE == 1) {
+        nrm = warp_sum_d(nrm);
+        if (lane == 0) red[warp] = nrm;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < NT / 32; ++q) s += red[q];
+            w.partials[pidx] = diag ? s : 2.0 * s;
+        }
+    }
+    if (!diag) {
+        __syncthreads();
+        for (int e = tid; e < TS * TS; e += NT) {
+            const int b = e / TS, a = e - (e / TS) * TS;
+            const size_t off = (size_t)(J * TS + b) * np + I * TS + a;
+            if (STAGE <= 3) {
+                w.S[off] = sO32[0 * TS * LDO + a * LDO + b];
+                w.S[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
+                dnext[off] = sO32[2 * TS * LDO + a * LDO + b];
+                dnext[plane + off] = -sO32[3 * TS * LDO + a * LDO + b];
+            } else {
+                w.y[off] = sO64[0 * TS * LDO + a * LDO + b];
+                w.y[plane + off] = -sO64[1 * TS * LDO + a * LDO + b];
+                w.D[off] = sO32[0 * TS * LDO + a * LDO + b];
+                w.D[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
+            }
+        }
+    }
+    if (STAGE == 4 && first && tid == 0) w.ctl->step += 1;
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    return s;
+}
+
+// g = G p(delta) for an FP32 delta (the gain is linear in p; no trace
+// normalisation inside a block of delta steps). Stage 2 first takes the stop
+// decision from the stage-1 residual partials (an FP32-accurate estimate of
+// ||f(y_n)||_F; a pass is confirmed by an exact FP64 refresh on the host
+// side of the loop).
+template <int STAGE>
+__device__ __forceinline__ void gain_mixed_body(const DevOps &ops, const MixedWork &w, const float *__restrict__ din,
+                                                int blk, int nblk) {
+    __shared__ double red[32];
+    Ctl *ctl = w.ctl;
+    const int n = ops.n, np = ops.np;
+    // (a step index whose exact residual the refresh already judged is not
+    // judged again on the estimate)
+    if (STAGE == 2 && blk == 0 && ctl->resid_exact_step != ctl->step) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s += w.partials[i];
+        s = block_sum_d(s, red);
+        if (threadIdx.x == 0) {
+            const double r = sqrt(s);
+            ctl->resid = r;
+            ctl->resid_step = ctl->step;
+            if (!isfinite(r)) {
+                ctl->status = kCtlNonFinite;
+                ctl->done = 1;
+            } else if (r < ctl->tol) {
+                ctl->status = kCtlCandidate;
+                ctl->done = 1;
+            } else if (ctl->step >= ctl->max_steps) {
+                ctl->status = kCtlMaxSteps;
+                ctl->done = 1;
+            }
+        }
+    }
+    double P = 0.0, Dd = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double pj = (double)din[(size_t)j * np + j];
+        P += pj;
+        if (ops.dang[j]) Dd += pj;
+    }
+    P = block_sum_d(P, red);
+    Dd = block_sum_d(Dd, red);
+    const double inv_nm1 = __drcp_rn((double)(n - 1));
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int i = blk * wpb + (threadIdx.x >> 5); i < np; i += nblk * wpb) {
+        double s = 0.0;
+        if (i < n)
+            for (int q = ops.s_ptr[i] + lane; q < ops.s_ptr[i + 1]; q += 32) {
+                const int j = ops.s_col[q];
+                s = __fma_rn(ops.s_val[q], (double)din[(size_t)j * np + j], s);
+            }
+        s = warp_sum_d(s);
+        if (lane == 0) {
+            double gi = 0.0;
+            if (i < n) {
+                const double pi = (double)din[(size_t)i * np + i];
+                const double dterm = (ops.dangling == QPR_DANGLING_F)
+                                         ? __dmul_rn(__dsub_rn(Dd, ops.dang[i] ? pi : 0.0), inv_nm1)
+                                         : __ddiv_rn(Dd, (double)n);
+                gi = __fma_rn(ops.alpha, __dadd_rn(s, dterm),
+                              __dmul_rn(__dmul_rn(__dsub_rn(1.0, ops.alpha), __dsub_rn(P, pi)), inv_nm1));
+            }
+            w.g[i] = (float)gi;
+        }
+    }
+}
+
+// Refresh, part 1: sigma = 1 / Re tr(y) (one CTA).
+__device__ __forceinline__ void refresh_trace_body(const DevOps &ops, const MixedWork &w) {
+    __shared__ double red[32];
+    double P = 0.0;
+    for (int j = threadIdx.x; j < ops.n; j += blockDim.x) P += w.y[(size_t)j * ops.np + j];
+    P = block_sum_d(P, red);
+    if (threadIdx.x == 0) {
+        w.ctl->trace = P;
+        w.ctl->scale = 1.0 / P;
+        if (!(P > 0.0) || !isfinite(P)) {
+            w.ctl->status = kCtlNonFinite;
+            w.ctl->done = 1;
+        }
+    }
+}
+
+// Refresh, part 2: R = y = sigma y, D = 0 (and its BF16 split, dense
+// backend); elements i0, i0 + stride, ...
+__device__ __forceinline__ void refresh_normalize_body(const DevOps &ops, const MixedWork &w, size_t i0,
+                                                       size_t stride) {
+    const double sig = w.ctl->scale;
+    const size_t tot = 2 * (size_t)ops.np * ops.np;
+    for (size_t i = i0; i < tot; i += stride) {
+        const double v = sig * w.y[i];
+        w.y[i] = v;
+        w.R[i] = v;
+        w.D[i] = 0.0f;
+    }
+    if (w.splitD) {
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+        for (size_t i = i0; i < 3 * tot; i += stride) w.splitD[i] = z;
+    }
+}
+
+// Refresh, part 4 (after F = f(R) in FP64): F32 = F; the CTA with first set
+// reduces the exact residual ||F||_F and takes the stop decision.
+__device__ __forceinline__ void refresh_post_body(const DevOps &ops, const MixedWork &w, size_t i0, size_t stride,
+                                                  bool first) {
+    __shared__ double red[32];
+    Ctl *ctl = w.ctl;
+    const size_t tot = 2 * (size_t)ops.np * ops.np;
+    for (size_t i = i0; i < tot; i += stride) w.F32[i] = (float)w.F[i];
+    if (first) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < w.npairs; i += blockDim.x) s += w.partials[i];
+        s = block_sum_d(s, red);
+        if (threadIdx.x == 0) {
+            const double r = sqrt(s);
+            ctl->resid_exact = r;
+            ctl->resid_exact_step = ctl->step;
+            ctl->resid = r;
+            ctl->resid_step = ctl->step;
+            if (!isfinite(r)) {
+                ctl->status = kCtlNonFinite;
+                ctl->done = 1;
+            } else if (r < ctl->tol) {
+                ctl->status = kCtlConverged;
+                ctl->done = 1;
+            } else if (ctl->step >= ctl->max_steps) {
+                ctl->status = kCtlMaxSteps;
+                ctl->done = 1;
+            }
+        }
+    }
+}
+
+}  // namespace mixed
+}  // namespace qpr

@@ -15,6 +15,7 @@
 #include "qpr_internal.cuh"
 
 using qpr::Ctl;
+using qpr::HostOps;
 
 struct qpr_ctx {
     int device = 0;
@@ -107,49 +108,6 @@ bool is_device_ptr(const void *p) {
         return false;
     }
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-}
-
-// Power iteration for the extreme eigenvalues of the symmetric CSR matrix
-// H; returns an estimate of lambda_max - lambda_min (with a 2% margin, and
-// never above the Gershgorin bound).
-double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
-                       const std::vector<double> &val) {
-    if (val.empty()) return 0.0;
-    auto matvec = [&](const std::vector<double> &x, std::vector<double> &y, double shift) {
-        for (int64_t i = 0; i < n; ++i) {
-            double s = -shift * x[i];
-            for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
-            y[i] = s;
-        }
-    };
-    auto dominant = [&](double shift) {
-        std::vector<double> x(n), y(n);
-        for (int64_t i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * sin(0.7 * (double)i + 0.1);
-        double lam = 0.0;
-        for (int it = 0; it < 400; ++it) {
-            double nx = 0.0;
-            for (double v : x) nx += v * v;
-            nx = sqrt(nx);
-            if (nx == 0.0) return 0.0;
-            for (double &v : x) v /= nx;
-            matvec(x, y, shift);
-            double rq = 0.0;
-            for (int64_t i = 0; i < n; ++i) rq += x[i] * y[i];
-            lam = rq;
-            x.swap(y);
-        }
-        return lam;
-    };
-    double gersh = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        double r = 0.0;
-        for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) r += fabs(val[q]);
-        gersh = std::max(gersh, r);
-    }
-    const double l1 = dominant(0.0);
-    const double l2 = dominant(l1);  // eigenvalue of H - l1 I farthest from 0
-    double spread = fabs(l2) * 1.02 + 1e-12;
-    return std::min(spread, 2.0 * gersh);
 }
 
 qpr_status sync_ctx(qpr_ctx *ctx) {
@@ -327,6 +285,174 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
 
 }  // namespace
 
+namespace qpr {
+
+// Power iteration for the extreme eigenvalues of the symmetric CSR matrix
+// H; returns an estimate of lambda_max - lambda_min (with a 2% margin, and
+// never above the Gershgorin bound).
+double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
+                       const std::vector<double> &val) {
+    if (val.empty()) return 0.0;
+    auto matvec = [&](const std::vector<double> &x, std::vector<double> &y, double shift) {
+        for (int64_t i = 0; i < n; ++i) {
+            double s = -shift * x[i];
+            for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
+            y[i] = s;
+        }
+    };
+    auto dominant = [&](double shift) {
+        std::vector<double> x(n), y(n);
+        for (int64_t i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * sin(0.7 * (double)i + 0.1);
+        double lam = 0.0;
+        for (int it = 0; it < 400; ++it) {
+            double nx = 0.0;
+            for (double v : x) nx += v * v;
+            nx = sqrt(nx);
+            if (nx == 0.0) return 0.0;
+            for (double &v : x) v /= nx;
+            matvec(x, y, shift);
+            double rq = 0.0;
+            for (int64_t i = 0; i < n; ++i) rq += x[i] * y[i];
+            lam = rq;
+            x.swap(y);
+        }
+        return lam;
+    };
+    double gersh = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) r += fabs(val[q]);
+        gersh = std::max(gersh, r);
+    }
+    const double l1 = dominant(0.0);
+    const double l2 = dominant(l1);  // eigenvalue of H - l1 I farthest from 0
+    double spread = fabs(l2) * 1.02 + 1e-12;
+    return std::min(spread, 2.0 * gersh);
+}
+
+void set_create_error(const std::string &msg) { g_create_error = msg; }
+
+// Operators of Supplementary Note 1 on the host: adjacency (A_ij = w for the
+// link j -> i, duplicates summed, self-loops and zero weights dropped),
+// out-degrees, CSR of H (Eq. S6) and of S (column-normalised adjacency
+// restricted to columns with out-links), dangling flags.
+qpr_status assemble_host(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w, int h_diag,
+                         HostOps &out, std::string &err) {
+    out.n = n;
+    for (int64_t e = 0; e < m; ++e) {
+        const double we = w ? w[e] : 1.0;
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+            { err = "edge " + std::to_string(e) + " has a node index outside [0, n)"; return QPR_E_GRAPH; }
+        if (!std::isfinite(we) || we < 0.0)
+            { err = "edge " + std::to_string(e) + " has a negative or non-finite weight"; return QPR_E_GRAPH; }
+    }
+
+    // ---- adjacency: A_ij = w for the link j -> i; duplicates sum ----
+    struct Ent { int64_t i, j; double a; };
+    std::vector<Ent> ents;
+    ents.reserve((size_t)m);
+    for (int64_t e = 0; e < m; ++e) {
+        const double we = w ? w[e] : 1.0;
+        if (src[e] == dst[e] || we == 0.0) continue;
+        ents.push_back({dst[e], src[e], we});
+    }
+    std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) {
+        return x.i != y.i ? x.i < y.i : x.j < y.j;
+    });
+    std::vector<Ent> A;
+    for (const Ent &x : ents) {
+        if (!A.empty() && A.back().i == x.i && A.back().j == x.j) A.back().a += x.a;
+        else A.push_back(x);
+    }
+    std::vector<double> &outdeg = out.outdeg;
+    outdeg.assign(n, 0.0);
+    for (const Ent &x : A) outdeg[x.j] += x.a;
+
+    // ---- H (Eq. S6): H_ij = -max(A_ij, A_ji) off the diagonal ----
+    std::vector<Ent> Hs;
+    Hs.reserve(A.size() * 2);
+    for (const Ent &x : A) {
+        Hs.push_back({x.i, x.j, x.a});
+        Hs.push_back({x.j, x.i, x.a});
+    }
+    std::sort(Hs.begin(), Hs.end(), [](const Ent &x, const Ent &y) {
+        return x.i != y.i ? x.i < y.i : x.j < y.j;
+    });
+    std::vector<Ent> Hu;  // unique (i, j) with -max
+    for (const Ent &x : Hs) {
+        if (!Hu.empty() && Hu.back().i == x.i && Hu.back().j == x.j) Hu.back().a = std::max(Hu.back().a, x.a);
+        else Hu.push_back(x);
+    }
+    std::vector<int64_t> &hptr = out.hptr;
+    std::vector<int> &hcol = out.hcol;
+    std::vector<double> &hval = out.hval;
+    hptr.assign(n + 1, 0);
+    {
+        size_t q = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            hptr[i] = (int64_t)hcol.size();
+            bool diag_done = false;
+            const double hd = (h_diag == QPR_HDIAG_NEG_OUTDEG) ? -outdeg[i] : 0.0;
+            while (q < Hu.size() && Hu[q].i == i) {
+                if (!diag_done && Hu[q].j > i) {
+                    if (hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
+                    diag_done = true;
+                }
+                hcol.push_back((int)Hu[q].j);
+                hval.push_back(-Hu[q].a);
+                ++q;
+            }
+            if (!diag_done && hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
+        }
+        hptr[n] = (int64_t)hcol.size();
+    }
+
+    // ---- S restricted to columns with out-links, CSR by rows ----
+    std::vector<int> &sptr = out.sptr, &scol = out.scol;
+    std::vector<double> &sval = out.sval;
+    sptr.assign(n + 1, 0);
+    scol.reserve(A.size());
+    sval.reserve(A.size());
+    {
+        size_t q = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            sptr[i] = (int)scol.size();
+            while (q < A.size() && A[q].i == i) {
+                scol.push_back((int)A[q].j);
+                sval.push_back(A[q].a / outdeg[A[q].j]);
+                ++q;
+            }
+        }
+        sptr[n] = (int)scol.size();
+    }
+    std::vector<unsigned char> &dang = out.dang;
+    dang.assign(n, 0);
+    for (int64_t j = 0; j < n; ++j) dang[j] = (outdeg[j] > 0.0) ? 0 : 1;
+    return QPR_OK;
+}
+
+// c_j = sum_i G_ij = alpha (column sum of S) + (1 - alpha) (column sum of F),
+// padded with zeros to np; *cmax receives the largest.
+std::vector<double> column_sums_G(const HostOps &h, double alpha, int np, double *cmax) {
+    std::vector<double> c(np, 0.0), scs(h.n, 0.0);
+    for (size_t q = 0; q < h.sval.size(); ++q) scs[h.scol[q]] += h.sval[q];
+    const double fcol = (double)(h.n - 1) / (double)(h.n - 1);
+    double mx = 0.0;
+    for (int64_t j = 0; j < h.n; ++j) {
+        const double sj = h.dang[j] ? 1.0 : scs[j];
+        c[j] = alpha * sj + (1.0 - alpha) * fcol;
+        mx = std::max(mx, c[j]);
+    }
+    if (cmax) *cmax = mx;
+    return c;
+}
+
+}  // namespace qpr
+
+namespace {
+
+}  // namespace
+
 extern "C" {
 
 qpr_status qpr_default_options(qpr_options *opt) {
@@ -428,91 +554,18 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
     if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
-    for (int64_t e = 0; e < m; ++e) {
-        const double we = w ? w[e] : 1.0;
-        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
-            return arg_err(QPR_E_GRAPH, "edge " + std::to_string(e) + " has a node index outside [0, n)");
-        if (!std::isfinite(we) || we < 0.0)
-            return arg_err(QPR_E_GRAPH, "edge " + std::to_string(e) + " has a negative or non-finite weight");
-    }
-
-    // ---- adjacency: A_ij = w for the link j -> i; duplicates sum ----
-    struct Ent { int64_t i, j; double a; };
-    std::vector<Ent> ents;
-    ents.reserve((size_t)m);
-    for (int64_t e = 0; e < m; ++e) {
-        const double we = w ? w[e] : 1.0;
-        if (src[e] == dst[e] || we == 0.0) continue;
-        ents.push_back({dst[e], src[e], we});
-    }
-    std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) {
-        return x.i != y.i ? x.i < y.i : x.j < y.j;
-    });
-    std::vector<Ent> A;
-    for (const Ent &x : ents) {
-        if (!A.empty() && A.back().i == x.i && A.back().j == x.j) A.back().a += x.a;
-        else A.push_back(x);
-    }
-    std::vector<double> outdeg(n, 0.0);
-    for (const Ent &x : A) outdeg[x.j] += x.a;
-
-    // ---- H (Eq. S6): H_ij = -max(A_ij, A_ji) off the diagonal ----
-    std::vector<Ent> Hs;
-    Hs.reserve(A.size() * 2);
-    for (const Ent &x : A) {
-        Hs.push_back({x.i, x.j, x.a});
-        Hs.push_back({x.j, x.i, x.a});
-    }
-    std::sort(Hs.begin(), Hs.end(), [](const Ent &x, const Ent &y) {
-        return x.i != y.i ? x.i < y.i : x.j < y.j;
-    });
-    std::vector<Ent> Hu;  // unique (i, j) with -max
-    for (const Ent &x : Hs) {
-        if (!Hu.empty() && Hu.back().i == x.i && Hu.back().j == x.j) Hu.back().a = std::max(Hu.back().a, x.a);
-        else Hu.push_back(x);
-    }
-    std::vector<int64_t> hptr(n + 1, 0);
-    std::vector<int> hcol;
-    std::vector<double> hval;
+    HostOps hops;
     {
-        size_t q = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            hptr[i] = (int64_t)hcol.size();
-            bool diag_done = false;
-            const double hd = (o.h_diag == QPR_HDIAG_NEG_OUTDEG) ? -outdeg[i] : 0.0;
-            while (q < Hu.size() && Hu[q].i == i) {
-                if (!diag_done && Hu[q].j > i) {
-                    if (hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
-                    diag_done = true;
-                }
-                hcol.push_back((int)Hu[q].j);
-                hval.push_back(-Hu[q].a);
-                ++q;
-            }
-            if (!diag_done && hd != 0.0) { hcol.push_back((int)i); hval.push_back(hd); }
-        }
-        hptr[n] = (int64_t)hcol.size();
+        std::string aerr;
+        const qpr_status ast = assemble_host(n, m, src, dst, w, o.h_diag, hops, aerr);
+        if (ast != QPR_OK) return arg_err(ast, aerr);
     }
-
-    // ---- S restricted to columns with out-links, CSR by rows ----
-    std::vector<int> sptr(n + 1, 0), scol;
-    std::vector<double> sval;
-    scol.reserve(A.size());
-    sval.reserve(A.size());
-    {
-        size_t q = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            sptr[i] = (int)scol.size();
-            while (q < A.size() && A[q].i == i) {
-                scol.push_back((int)A[q].j);
-                sval.push_back(A[q].a / outdeg[A[q].j]);
-                ++q;
-            }
-        }
-        sptr[n] = (int)scol.size();
-    }
-    std::vector<unsigned char> dang(n);
-    for (int64_t j = 0; j < n; ++j) dang[j] = (outdeg[j] > 0.0) ? 0 : 1;
+    const std::vector<int64_t> &hptr = hops.hptr;
+    const std::vector<int> &hcol = hops.hcol;
+    const std::vector<double> &hval = hops.hval;
+    const std::vector<int> &sptr = hops.sptr, &scol = hops.scol;
+    const std::vector<double> &sval = hops.sval;
+    const std::vector<unsigned char> &dang = hops.dang;
 
     qpr_ctx *ctx = new (std::nothrow) qpr_ctx();
     if (!ctx) return arg_err(QPR_E_OOM, "host allocation failed");
@@ -525,25 +578,12 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
                     (o.backend == QPR_BACKEND_DENSE ||
                      (o.backend == QPR_BACKEND_AUTO && (double)hval.size() >= (double)n * (double)n / 8.0));
     if (tc) ctx->np = (int)(((n + qpr::kTileTc - 1) / qpr::kTileTc) * qpr::kTileTc);
-    ctx->spread = estimate_spread(n, hptr, hcol, hval);
+    ctx->spread = qpr::estimate_spread(n, hptr, hcol, hval);
     if (o.backend == QPR_BACKEND_AUTO)
         ctx->backend = ((double)hval.size() < (double)n * (double)n / 8.0) ? QPR_BACKEND_SPARSE : QPR_BACKEND_DENSE;
     else
         ctx->backend = o.backend;
-    // column sums of G: alpha * (column sum of S) + (1 - alpha) * 1
-    std::vector<double> c(ctx->np, 0.0);
-    {
-        std::vector<double> scs(n, 0.0);
-        for (size_t q = 0; q < sval.size(); ++q) scs[scol[q]] += sval[q];
-        const double fcol = (double)(n - 1) / (double)(n - 1);
-        double cmax = 0.0;
-        for (int64_t j = 0; j < n; ++j) {
-            double sj = dang[j] ? 1.0 : scs[j];
-            c[j] = alpha * sj + (1.0 - alpha) * fcol;
-            cmax = std::max(cmax, c[j]);
-        }
-        ctx->cmax = cmax;
-    }
+    std::vector<double> c = qpr::column_sums_G(hops, alpha, ctx->np, &ctx->cmax);
 
     if (o.device < 0) {
         if (cudaGetDevice(&ctx->device) != cudaSuccess) {

@@ -146,4 +146,25 @@ void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcM
 constexpr int kMixedLaunchesPerStep = 8;
 constexpr int kMixedLaunchesPerRefresh = 5;
 
+// ---- host assembly (qpr_api.cu) ----
+struct HostOps {
+    int64_t n = 0;
+    std::vector<double> outdeg;
+    std::vector<int64_t> hptr;
+    std::vector<int> hcol;
+    std::vector<double> hval;
+    std::vector<int> sptr, scol;
+    std::vector<double> sval;
+    std::vector<unsigned char> dang;
+};
+qpr_status assemble_host(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w, int h_diag,
+                         HostOps &out, std::string &err);
+std::vector<double> column_sums_G(const HostOps &h, double alpha, int np, double *cmax);
+// Message returned by qpr_last_error(NULL) on this thread.
+void set_create_error(const std::string &msg);
+// Opt in to the dynamic shared memory of the batched kernels (batch.cu).
+cudaError_t init_batch();
+double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
+                       const std::vector<double> &val);
+
 }  // namespace qpr

@@ -32,10 +32,12 @@ __device__ __forceinline__ double epi_warp_sum(double v) {
 // sO: 4 * 32 * kEpiLDO doubles of shared memory, disjoint from sX1/sX2.
 // Must be called by all kEpiThreads threads of the CTA after the X tiles
 // are complete and visible (__syncthreads()).
+// pidx: slot of this tile pair's residual partial; first: the tile pair
+// that advances the step counter at stage 4.
 template <int STAGE>
 __device__ __forceinline__ void stage_epilogue(const DevOps &ops, const Work &w, int I, int J, bool diag,
                                                const double *sX1, const double *sX2, int ldx,
-                                               double *sO, double *red) {
+                                               double *sO, double *red, int pidx, bool first) {
     constexpr int TS = kEpiTS, LDO = kEpiLDO;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int np = ops.np;
@@ -49,20 +51,25 @@ __device__ __forceinline__ void stage_epilogue(const DevOps &ops, const Work &w,
     const double gsig = (STAGE == 1) ? scale : 1.0;                 // stage-1 input is unnormalised y
     const double ysig = (STAGE >= 1 && STAGE <= 3) ? scale : 1.0;  // Y1 = y / tr(y)
     const double dt = ctl->dt;
+    const double dt6 = __ddiv_rn(dt, 6.0), dt3 = __ddiv_rn(dt, 3.0);
+    const double cg = __dmul_rn(cm, gsig);
     double nrm = 0.0;
 
+    // Every operation below is an explicit round-to-nearest intrinsic, so the
+    // result does not depend on how a compiler contracts it in the kernel that
+    // inlines this function (single-problem and batched kernels agree bitwise).
     for (int e = tid; e < TS * TS; e += kEpiThreads) {
         const int a = e / TS, b = e - (e / TS) * TS;
         const int ga = I * TS + a, gb = J * TS + b;
         const size_t off = (size_t)ga * np + gb;
         const double Aab = sX1[a * ldx + b], Bab = -sX1[a * ldx + TS + b];
         const double Aba = X2[b * ldx + a], Bba = -X2[b * ldx + TS + a];
-        const double ysr = gsig * yin[off], ysi = gsig * yin[plane + off];
-        const double hc = 0.5 * (ops.c[ga] + ops.c[gb]);
-        double kr = cm * gsig * (Bab + Bba) - om * hc * ysr;
-        const double ki = -cm * gsig * (Aab - Aba) - om * hc * ysi;
-        if (ga == gb) kr += om * w.g[ga];
-        if (STAGE <= 1) nrm += kr * kr + ki * ki;
+        const double ysr = __dmul_rn(gsig, yin[off]), ysi = __dmul_rn(gsig, yin[plane + off]);
+        const double omhc = __dmul_rn(om, __dmul_rn(0.5, __dadd_rn(ops.c[ga], ops.c[gb])));
+        double kr = __fma_rn(-omhc, ysr, __dmul_rn(cg, __dadd_rn(Bab, Bba)));
+        const double ki = __fma_rn(-omhc, ysi, __dmul_rn(-cg, __dsub_rn(Aab, Aba)));
+        if (ga == gb) kr = __fma_rn(om, w.g[ga], kr);
+        if (STAGE <= 1) nrm = __fma_rn(kr, kr, __fma_rn(ki, ki, nrm));
 
         double o0, o1, o2 = 0.0, o3 = 0.0;
         if (STAGE == 0) {
@@ -71,25 +78,25 @@ __device__ __forceinline__ void stage_epilogue(const DevOps &ops, const Work &w,
             w.z[off] = o0;
             w.z[plane + off] = o1;
         } else if (STAGE <= 3) {
-            const double y1r = ysig * w.y[off], y1i = ysig * w.y[plane + off];
+            const double y1r = __dmul_rn(ysig, w.y[off]), y1i = __dmul_rn(ysig, w.y[plane + off]);
             if (STAGE == 1) {
-                o0 = y1r + (dt / 6.0) * kr;
-                o1 = y1i + (dt / 6.0) * ki;
+                o0 = __fma_rn(dt6, kr, y1r);
+                o1 = __fma_rn(dt6, ki, y1i);
             } else {
-                o0 = w.z[off] + (dt / 3.0) * kr;
-                o1 = w.z[plane + off] + (dt / 3.0) * ki;
+                o0 = __fma_rn(dt3, kr, w.z[off]);
+                o1 = __fma_rn(dt3, ki, w.z[plane + off]);
             }
-            const double cst = (STAGE == 3) ? dt : 0.5 * dt;
-            o2 = y1r + cst * kr;
-            o3 = y1i + cst * ki;
+            const double cst = (STAGE == 3) ? dt : __dmul_rn(0.5, dt);
+            o2 = __fma_rn(cst, kr, y1r);
+            o3 = __fma_rn(cst, ki, y1i);
             double *yn = (STAGE == 2) ? w.yb : w.ya;
             w.z[off] = o0;
             w.z[plane + off] = o1;
             yn[off] = o2;
             yn[plane + off] = o3;
         } else {
-            o0 = w.z[off] + (dt / 6.0) * kr;
-            o1 = w.z[plane + off] + (dt / 6.0) * ki;
+            o0 = __fma_rn(dt6, kr, w.z[off]);
+            o1 = __fma_rn(dt6, ki, w.z[plane + off]);
             w.y[off] = o0;
             w.y[plane + off] = o1;
         }
@@ -108,7 +115,7 @@ __device__ __forceinline__ void stage_epilogue(const DevOps &ops, const Work &w,
         if (tid == 0) {
             double s = 0.0;
             for (int q = 0; q < kEpiThreads / 32; ++q) s += red[q];
-            w.partials[blockIdx.x] = diag ? s : 2.0 * s;
+            w.partials[pidx] = diag ? s : 2.0 * s;
         }
     }
 
@@ -141,7 +148,7 @@ __device__ __forceinline__ void stage_epilogue(const DevOps &ops, const Work &w,
         }
     }
 
-    if (STAGE == 4 && blockIdx.x == 0 && tid == 0) w.ctl->step += 1;
+    if (STAGE == 4 && first && tid == 0) w.ctl->step += 1;
 }
 
 }  // namespace qpr

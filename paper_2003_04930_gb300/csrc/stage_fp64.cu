@@ -170,7 +170,7 @@ stage_fp64_kernel(DevOps ops, Work w) {
             }
     __syncthreads();
     __shared__ double red[NTHREADS / 32];
-    stage_epilogue<STAGE>(ops, w, I, J, diag, sX1, sX2, LDX, sO, red);
+    stage_epilogue<STAGE>(ops, w, I, J, diag, sX1, sX2, LDX, sO, red, blockIdx.x, blockIdx.x == 0);
 }
 
 template <int STAGE>

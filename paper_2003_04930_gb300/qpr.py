@@ -27,7 +27,7 @@ QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
     "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
-    "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc",
+    "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
 )
 QPR_NOALLOC_MAX_N = 256
 
@@ -49,6 +49,11 @@ class qpr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k in
                 ("steps", "substeps_m", "t", "residual", "trace_before", "seconds", "kernel_launches",
                  "converged")}
+
+
+class qpr_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("omega", ctypes.c_double), ("rho", ctypes.c_void_p)]
 
 
 class QprError(RuntimeError):
@@ -99,6 +104,9 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_profile_step.restype = st
     lib.qpr_rhs_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, f64, f64, ctypes.c_int32, vp, vp, vp]
     lib.qpr_rhs_noalloc.restype = st
+    lib.qpr_batch_steady_state.argtypes = [i64, ctypes.POINTER(qpr_problem), f64, f64, f64, i64,
+                                           ctypes.POINTER(qpr_options), ctypes.POINTER(qpr_stats)]
+    lib.qpr_batch_steady_state.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
     _lib = lib
@@ -245,3 +253,33 @@ class Solver:
         ms = (ctypes.c_double * 3)()
         self._raise(self._lib.qpr_profile_step(self._h, _ptr(rho), float(dt), int(steps), ms))
         return {"stage_ms": ms[0], "gain_ms": ms[1], "step_ms": ms[2]}
+
+
+def batch_steady_state(problems, alpha=0.85, dt=0.01, tol=1e-8, max_steps=400000, ref_refresh=32,
+                       h_diag=QPR_HDIAG_ZERO, dangling=QPR_DANGLING_F, device=-1, check=True):
+    """Batched steady states. ``problems``: list of (EdgeList, omega, rho)
+    with rho a complex128 (n, n) torch tensor or NumPy array, overwritten in
+    place. Returns (status, list of per-problem stats dicts)."""
+    lib = load_library()
+    keep = []
+    arr = (qpr_problem * len(problems))()
+    for i, (g, omega, rho) in enumerate(problems):
+        _check_rho(rho, g.n)
+        src = np.ascontiguousarray(g.src, dtype=np.int64)
+        dst = np.ascontiguousarray(g.dst, dtype=np.int64)
+        w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float64)
+        keep += [src, dst, w]
+        arr[i].n, arr[i].m = int(g.n), int(src.shape[0])
+        arr[i].src, arr[i].dst, arr[i].w = _ptr(src), _ptr(dst), _ptr(w)
+        arr[i].omega = float(omega)
+        arr[i].rho = _ptr(rho)
+    opt = qpr_options()
+    lib.qpr_default_options(ctypes.byref(opt))
+    opt.precision = QPR_MIXED
+    opt.ref_refresh, opt.h_diag, opt.dangling, opt.device = int(ref_refresh), int(h_diag), int(dangling), int(device)
+    stats = (qpr_stats * len(problems))()
+    st = lib.qpr_batch_steady_state(len(problems), arr, float(alpha), float(dt), float(tol), int(max_steps),
+                                    ctypes.byref(opt), stats)
+    if check and st != QPR_OK:
+        raise QprError(st, lib.qpr_last_error(None).decode())
+    return st, [stats[i].as_dict() for i in range(len(problems))]

@@ -84,3 +84,18 @@ def test_null_context_calls(lib):
     assert lib.qpr_evolve(None, None, 0.01, 1) == qpr.QPR_E_ARG
     assert lib.qpr_n(None) == 0
     lib.qpr_destroy(None)
+
+
+def test_batch_rejects_invalid_problem_before_cuda(lib):
+    src = np.array([0, 5], dtype=np.int64)
+    dst = np.array([1, 0], dtype=np.int64)
+    rho = np.eye(3, dtype=np.complex128) / 3
+    arr = (qpr.qpr_problem * 1)()
+    arr[0].n, arr[0].m = 3, 2
+    arr[0].src, arr[0].dst, arr[0].w = qpr._ptr(src), qpr._ptr(dst), None
+    arr[0].omega = 0.5
+    arr[0].rho = qpr._ptr(rho)
+    st = lib.qpr_batch_steady_state(1, arr, 0.85, 0.01, 1e-8, 10, None, None)
+    assert st == qpr.QPR_E_GRAPH
+    assert b"problem 0" in lib.qpr_last_error(None)
+    assert lib.qpr_batch_steady_state(0, arr, 0.85, 0.01, 1e-8, 10, None, None) == qpr.QPR_E_ARG
