@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense-projection", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle RK4 steps per sample (0: auto)")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="batch: qpr_batch_steady_state over --batch-count graphs (N ~ U[32,1024], "
+                         "omega ~ U[0.1,0.95], seeds 1000+g)")
+    ap.add_argument("--batch-count", type=int, default=512)
     return ap.parse_args()
 
 
@@ -374,10 +378,62 @@ def run_ours(a):
     return 0
 
 
+def run_batch(a):
+    """One step = one qpr_batch_steady_state call over the whole batch."""
+    import numpy as np
+    import torch
+
+    from paper_2003_04930_gb300 import graphs, qpr
+    from paper_2003_04930_gb300.build import build_library
+    build_library()
+    specs = graphs.batch_specs(a.batch_count)
+    gs = [graphs.heavy_tailed(n, seed) for n, om, seed in specs]
+    rho0 = [torch.from_numpy(graphs.maximally_mixed(g.n)).cuda() for g in gs]
+    rho = [r.clone() for r in rho0]
+    probs = [(g, om, r) for g, (n, om, seed), r in zip(gs, specs, rho)]
+
+    def solve():
+        for r, r0 in zip(rho, rho0):
+            r.copy_(r0)
+        return qpr.batch_steady_state(probs, dt=a.dt, tol=a.tol, max_steps=a.max_steps, ref_refresh=a.ref_refresh)
+
+    for _ in range(a.warmup):
+        solve()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    times, stats = [], None
+    for _ in range(a.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, stats = solve()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = sampler.stop()
+    steps = [s["steps"] for s in stats]
+    value = sum(times) / a.steps
+    line = {"metric": "time-to-steady-state of the whole batch (resid 1e-8)", "value": value, "unit": "s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.batch_count} heavy-tailed graphs, N ~ U[32,1024], omega ~ U[0.1,0.95], "
+                                   f"alpha=0.85, rho0=I/N, RK4 dt={a.dt}, tol={a.tol}",
+                       "sum_n2": int(sum(g.n ** 2 for g in gs)), "ref_refresh": a.ref_refresh},
+            "rk4_steps_max": max(steps), "rk4_steps_mean": float(np.mean(steps)),
+            "converged": int(sum(s["converged"] for s in stats)), "clocks": clocks,
+            "gpu_launches": int(stats[0]["kernel_launches"])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch":
+        return run_batch(a)
     return run_ours(a)
 
 
