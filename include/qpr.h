@@ -220,6 +220,57 @@ typedef struct {
 QPR_API qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *problems, double alpha, double dt,
                                           double tol, int64_t max_steps, const qpr_options *opt, qpr_stats *stats);
 
+/* ---- learned warm start ----
+ * A 4-layer message-passing network (width 64, BF16 weights, FP32
+ * accumulation) that predicts the steady-state populations from the graph;
+ * rho0 = diag(p_hat) then starts qpr_steady_state near its fixed point,
+ * while rho0 = I/N stays the fallback. The paper has no learned component;
+ * the network serves only as an initial guess, and the stop rule of the
+ * solver decides the answer. Definition of features, layers and loss:
+ * features [1, omega, log1p(in-strength), log1p(out-strength),
+ * log1p(in-degree), log1p(out-degree), log(N pi_i), dangles] with pi the
+ * classical PageRank (the omega = 1 steady state); layers
+ * z = h Ws + (P h) Wn + b, h = relu(z) with P the row-normalised A + A^T;
+ * p_hat = softmax(h_4 wo + bo); loss -sum_i p_i log p_hat_i.
+ * Parameters: qpr_gnn_param_count() floats in the order Ws1 [8][64],
+ * Wn1 [8][64], b1 [64], then Ws, Wn [64][64] and b [64] of layers 2-4, then
+ * wo [64], bo [1]. */
+typedef struct qpr_gnn qpr_gnn;
+
+/* One training sample: a graph (as in qpr_create), its omega and the target
+ * populations p (host, n doubles, summing to 1). */
+typedef struct {
+    int64_t n;
+    int64_t m;
+    const int64_t *src;
+    const int64_t *dst;
+    const double *w;
+    double omega;
+    const double *p;
+} qpr_gnn_sample;
+
+QPR_API int64_t qpr_gnn_param_count(void);
+/* Glorot-uniform weights from `seed`, zero biases; device < 0: current. */
+QPR_API qpr_status qpr_gnn_create(qpr_gnn **out, uint64_t seed, int32_t device);
+QPR_API void qpr_gnn_destroy(qpr_gnn *g);
+/* Copy the FP32 master parameters out of / into the network (host arrays of
+ * qpr_gnn_param_count() floats); setting resets the Adam state. */
+QPR_API qpr_status qpr_gnn_get_params(qpr_gnn *g, float *host_params);
+QPR_API qpr_status qpr_gnn_set_params(qpr_gnn *g, const float *host_params);
+/* p_hat (n doubles, host or device) for a graph and omega. */
+QPR_API qpr_status qpr_gnn_predict(qpr_gnn *g, int64_t n, int64_t m, const int64_t *src, const int64_t *dst,
+                                   const double *w, double alpha, double omega, double *p_hat);
+/* Loss of one sample and its gradient with respect to the parameters
+ * (host outputs; grad: qpr_gnn_param_count() floats, nullable). */
+QPR_API qpr_status qpr_gnn_loss_grad(qpr_gnn *g, const qpr_gnn_sample *sample, double alpha, double *loss,
+                                     float *grad);
+/* Adam (beta 0.9 / 0.999, eps 1e-8) on the mean gradient of minibatches of
+ * `batch` samples, `epochs` passes in an order shuffled from `seed`;
+ * epoch_loss (nullable, `epochs` doubles) receives the mean loss of each
+ * pass. */
+QPR_API qpr_status qpr_gnn_train(qpr_gnn *g, int64_t count, const qpr_gnn_sample *samples, double alpha,
+                                 int32_t epochs, int32_t batch, double lr, uint64_t seed, double *epoch_loss);
+
 /* ---- right-hand side without any allocation ----
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc: hosts that hand out all device memory from

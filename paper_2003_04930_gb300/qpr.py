@@ -28,6 +28,8 @@ EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
     "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
+    "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
+    "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train",
 )
 QPR_NOALLOC_MAX_N = 256
 
@@ -54,6 +56,11 @@ class qpr_stats(ctypes.Structure):
 class qpr_problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("w", ctypes.c_void_p), ("omega", ctypes.c_double), ("rho", ctypes.c_void_p)]
+
+
+class qpr_gnn_sample(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("omega", ctypes.c_double), ("p", ctypes.c_void_p)]
 
 
 class QprError(RuntimeError):
@@ -107,6 +114,23 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_batch_steady_state.argtypes = [i64, ctypes.POINTER(qpr_problem), f64, f64, f64, i64,
                                            ctypes.POINTER(qpr_options), ctypes.POINTER(qpr_stats)]
     lib.qpr_batch_steady_state.restype = st
+    lib.qpr_gnn_param_count.argtypes = []
+    lib.qpr_gnn_param_count.restype = i64
+    lib.qpr_gnn_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint64, ctypes.c_int32]
+    lib.qpr_gnn_create.restype = st
+    lib.qpr_gnn_destroy.argtypes = [vp]
+    lib.qpr_gnn_destroy.restype = None
+    lib.qpr_gnn_get_params.argtypes = [vp, vp]
+    lib.qpr_gnn_get_params.restype = st
+    lib.qpr_gnn_set_params.argtypes = [vp, vp]
+    lib.qpr_gnn_set_params.restype = st
+    lib.qpr_gnn_predict.argtypes = [vp, i64, i64, vp, vp, vp, f64, f64, vp]
+    lib.qpr_gnn_predict.restype = st
+    lib.qpr_gnn_loss_grad.argtypes = [vp, ctypes.POINTER(qpr_gnn_sample), f64, ctypes.POINTER(f64), vp]
+    lib.qpr_gnn_loss_grad.restype = st
+    lib.qpr_gnn_train.argtypes = [vp, i64, ctypes.POINTER(qpr_gnn_sample), f64, ctypes.c_int32, ctypes.c_int32, f64,
+                                  ctypes.c_uint64, vp]
+    lib.qpr_gnn_train.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
     _lib = lib
@@ -283,3 +307,82 @@ def batch_steady_state(problems, alpha=0.85, dt=0.01, tol=1e-8, max_steps=400000
     if check and st != QPR_OK:
         raise QprError(st, lib.qpr_last_error(None).decode())
     return st, [stats[i].as_dict() for i in range(len(problems))]
+
+
+class Gnn:
+    """The warm-start network of the C ABI (qpr_gnn_*)."""
+
+    def __init__(self, seed: int = 0, device: int = -1):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        st = self._lib.qpr_gnn_create(ctypes.byref(h), int(seed), int(device))
+        if st != QPR_OK:
+            raise QprError(st, self._lib.qpr_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qpr_gnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        if st != QPR_OK:
+            raise QprError(st, self._lib.qpr_last_error(None).decode())
+
+    @property
+    def param_count(self) -> int:
+        return int(self._lib.qpr_gnn_param_count())
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count, dtype=np.float32)
+        self._raise(self._lib.qpr_gnn_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, params) -> None:
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        assert arr.shape == (self.param_count,)
+        self._raise(self._lib.qpr_gnn_set_params(self._h, _ptr(arr)))
+
+    def predict(self, g, omega: float, alpha: float = 0.85) -> np.ndarray:
+        src = np.ascontiguousarray(g.src, dtype=np.int64)
+        dst = np.ascontiguousarray(g.dst, dtype=np.int64)
+        w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float64)
+        out = np.zeros(g.n)
+        self._raise(self._lib.qpr_gnn_predict(self._h, int(g.n), int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w),
+                                              float(alpha), float(omega), _ptr(out)))
+        return out
+
+    @staticmethod
+    def _samples(samples):
+        keep = []
+        arr = (qpr_gnn_sample * len(samples))()
+        for i, (g, omega, p) in enumerate(samples):
+            src = np.ascontiguousarray(g.src, dtype=np.int64)
+            dst = np.ascontiguousarray(g.dst, dtype=np.int64)
+            w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float64)
+            pp = np.ascontiguousarray(p, dtype=np.float64)
+            keep += [src, dst, w, pp]
+            arr[i].n, arr[i].m = int(g.n), int(src.shape[0])
+            arr[i].src, arr[i].dst, arr[i].w, arr[i].p = _ptr(src), _ptr(dst), _ptr(w), _ptr(pp)
+            arr[i].omega = float(omega)
+        return arr, keep
+
+    def loss_grad(self, g, omega, p, alpha=0.85):
+        arr, keep = self._samples([(g, omega, p)])
+        loss = ctypes.c_double(0.0)
+        grad = np.zeros(self.param_count, dtype=np.float32)
+        self._raise(self._lib.qpr_gnn_loss_grad(self._h, arr, float(alpha), ctypes.byref(loss), _ptr(grad)))
+        return float(loss.value), grad
+
+    def train(self, samples, epochs=20, batch=8, lr=1e-3, seed=0, alpha=0.85):
+        arr, keep = self._samples(samples)
+        losses = np.zeros(int(epochs))
+        self._raise(self._lib.qpr_gnn_train(self._h, len(samples), arr, float(alpha), int(epochs), int(batch),
+                                            float(lr), int(seed), _ptr(losses)))
+        return losses
