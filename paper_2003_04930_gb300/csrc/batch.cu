@@ -102,16 +102,6 @@ __global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(256) b_gain_mixed_kernel(const BatchGraph *gs, const int *act) {
-    __shared__ BatchGraph sg;
-    __shared__ int s_flag;
-    load_graph(gs, act[blockIdx.x], sg);
-    if (graph_done(sg, &s_flag)) return;
-    const float *din = (STAGE == 1) ? sg.mw.D : (STAGE == 3 ? sg.mw.db : sg.mw.da);
-    mixed::gain_mixed_body<STAGE>(sg.ops, sg.mw, din, 0, 1);
-}
-
-template <int STAGE>
 __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
@@ -149,15 +139,11 @@ void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream
 
 void launch_step(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
     const int grid = std::min(L.nitems, 152 * 5);
-    b_gain_mixed_kernel<1><<<L.nact, 256, 0, s>>>(gs, L.act);
     b_stage_mixed_kernel<1><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_gain_mixed_kernel<2><<<L.nact, 256, 0, s>>>(gs, L.act);
     b_stage_mixed_kernel<2><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_gain_mixed_kernel<3><<<L.nact, 256, 0, s>>>(gs, L.act);
     b_stage_mixed_kernel<3><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_gain_mixed_kernel<4><<<L.nact, 256, 0, s>>>(gs, L.act);
     b_stage_mixed_kernel<4><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    launches += 8;
+    launches += 4;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -234,6 +220,8 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     const size_t G = (size_t)count;
     std::vector<qpr::HostOps> H(G);
     std::vector<int> np(G), T(G), npairs(G);
+    std::vector<std::vector<int>> rowseg(G);
+    std::vector<std::vector<int2>> segs(G);
     std::vector<double> hdt(G);
     std::vector<int64_t> msub(G);
     for (size_t g = 0; g < G; ++g) {
@@ -248,6 +236,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         const qpr_status ast = qpr::assemble_host(p.n, p.m, p.src, p.dst, p.w, o.h_diag, H[g], aerr);
         if (ast != QPR_OK) return err(ast, "problem " + std::to_string(g) + ": " + aerr);
         np[g] = (int)(((p.n + qpr::kPadFp64 - 1) / qpr::kPadFp64) * qpr::kPadFp64);
+        qpr::row_segments(H[g], np[g], 32, rowseg[g], segs[g]);
         T[g] = np[g] / qpr::kTileFp64;
         npairs[g] = T[g] * (T[g] + 1) / 2;
         double cmax = 0.0;
@@ -271,7 +260,8 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         of[g] = nf;
         nf += qpr::align_up(5 * p2 + 2 * np[g] + qpr::align_up(nh, 64), 64) + 64;
         oi[g] = ni;
-        ni += qpr::align_up(2 * (n + 1) + nh + ns, 64);
+        ni += qpr::align_up(2 * (n + 1) + nh + ns, 64) + qpr::align_up((size_t)np[g] + 1, 64) + 2 * segs[g].size();
+        ni = qpr::align_up(ni, 64);
         ob[g] = nb;
         nb += qpr::align_up(n, 64);
         max_nn = std::max(max_nn, n * n);
@@ -359,8 +349,15 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         float *g32 = bf + 5 * p2, *c32 = g32 + p, *hv32 = c32 + p;
         for (int j = 0; j < p; ++j) hF[(c32 - dF) + j] = (float)cg[j];
         for (size_t q = 0; q < nh; ++q) hF[(hv32 - dF) + q] = (float)h.hval[q];
-        // int arena: hptr hcol sptr scol
+        // int arena: hptr hcol sptr scol | rowseg | seg (pairs of ints)
         int *hptr = bi, *hcol = hptr + (n + 1), *sptr = hcol + nh, *scol = sptr + (n + 1);
+        int *rseg = bi + qpr::align_up(2 * (size_t)(n + 1) + nh + ns, 64);
+        int *sg = rseg + qpr::align_up((size_t)p + 1, 64);
+        std::copy(rowseg[g].begin(), rowseg[g].end(), hI.begin() + (rseg - dI));
+        for (size_t q = 0; q < segs[g].size(); ++q) {
+            hI[(sg - dI) + 2 * q] = segs[g][q].x;
+            hI[(sg - dI) + 2 * q + 1] = segs[g][q].y;
+        }
         for (int i = 0; i <= n; ++i) hI[(hptr - dI) + i] = (int)h.hptr[i];
         std::copy(h.hcol.begin(), h.hcol.end(), hI.begin() + (hcol - dI));
         std::copy(h.sptr.begin(), h.sptr.end(), hI.begin() + (sptr - dI));
@@ -379,6 +376,8 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         d.ops.h_col = hcol;
         d.ops.h_val = hval;
         d.ops.h_val32 = hv32;
+        d.ops.rowseg = rseg;
+        d.ops.seg = reinterpret_cast<const int2 *>(sg);
         d.ops.s_ptr = sptr;
         d.ops.s_col = scol;
         d.ops.s_val = sval;

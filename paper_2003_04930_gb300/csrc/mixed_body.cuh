@@ -29,57 +29,161 @@ __device__ __forceinline__ float4 f4xor(float4 v, int m) {
     return v;
 }
 
-// sX[a][b] = (H Re d)_ab, sX[a][TS + b] = (H Im d)_ab for rows of tile rt and
-// columns of tile ct, in FP32.
-__device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__restrict__ d, size_t plane,
-                                            int rt, int ct, float *sX) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane >> 3, sub = lane & 7;
-    const int np = ops.np, n = ops.n;
-    const float *__restrict__ re = d + ct * TS + 4 * sub;
-    const float *__restrict__ im = d + plane + ct * TS + 4 * sub;
-    for (int a = warp; a < TS; a += NT / 32) {
-        const int ga = rt * TS + a;
-        float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
-        if (ga < n) {
-            const int q1 = ops.h_ptr[ga + 1];
-            int q = ops.h_ptr[ga] + grp;
-            for (; q + 4 < q1; q += 8) {
-                const int k0 = ops.h_col[q], k1 = ops.h_col[q + 4];
-                const float h0 = ops.h_val32[q], h1 = ops.h_val32[q + 4];
-                const float4 r0 = *reinterpret_cast<const float4 *>(re + (size_t)k0 * np);
-                const float4 i0 = *reinterpret_cast<const float4 *>(im + (size_t)k0 * np);
-                const float4 r1 = *reinterpret_cast<const float4 *>(re + (size_t)k1 * np);
-                const float4 i1 = *reinterpret_cast<const float4 *>(im + (size_t)k1 * np);
-                xr = f4fma(h0, r0, xr);
-                xi = f4fma(h0, i0, xi);
-                xr = f4fma(h1, r1, xr);
-                xi = f4fma(h1, i1, xi);
-            }
-            if (q < q1) {
-                const int k0 = ops.h_col[q];
-                const float h0 = ops.h_val32[q];
-                xr = f4fma(h0, *reinterpret_cast<const float4 *>(re + (size_t)k0 * np), xr);
-                xi = f4fma(h0, *reinterpret_cast<const float4 *>(im + (size_t)k0 * np), xi);
-            }
-        }
-        xr = f4xor(xr, 8);
-        xr = f4xor(xr, 16);
-        xi = f4xor(xi, 8);
-        xi = f4xor(xi, 16);
-        if (grp == 0) {
-            float *row = sX + a * LDX;
-            row[4 * sub + 0] = xr.x; row[4 * sub + 1] = xr.y; row[4 * sub + 2] = xr.z; row[4 * sub + 3] = xr.w;
-            row[TS + 4 * sub + 0] = xi.x; row[TS + 4 * sub + 1] = xi.y;
-            row[TS + 4 * sub + 2] = xi.z; row[TS + 4 * sub + 3] = xi.w;
-        }
-    }
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    return s;
+}
+
+constexpr int kSegSlots = 96;      // segment partials held at once (24 KB)
+constexpr int kSegLen = 32;        // nonzeros per segment (one warp-wide load)
+
+// sX[a][b] = (H Re d)_ab, sX[a][TS + b] = (H Im d)_ab for rows of tile rt and
+// columns of tile ct, in FP32. The nonzeros of every row are cut into
+// segments of at most kSegLen (ops.seg, rows' ranges in ops.rowseg); warps
+// take segments round-robin, so a hub row no longer holds one warp while
+// the others wait. A warp loads a segment's columns and values with one
+// coalesced load, broadcasts them by shuffle and keeps all of the
+// segment's 2 x 8 float4 gathers in flight; segment partials go to shared
+// memory and are summed per row in segment order (deterministic).
+// slots: kSegSlots * 2 * TS floats of shared memory, free during the call.
+__device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__restrict__ d, size_t plane,
+                                            int rt, int ct, float *sX, float *slots) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 3, sub = lane & 7;
+    const int np = ops.np;
+    const float *__restrict__ re = d + ct * TS + 4 * sub;
+    const float *__restrict__ im = d + plane + ct * TS + 4 * sub;
+    const int s0 = ops.rowseg[rt * TS], s1 = ops.rowseg[rt * TS + TS];
+    int base = s0;
+    do {
+        const int cnt = min(kSegSlots, s1 - base);
+        for (int si = warp; si < cnt; si += NT / 32) {
+            const int2 sg = ops.seg[base + si];
+            const int len = sg.y - sg.x;
+            int myk = 0;
+            float myh = 0.f;
+            if (lane < len) {
+                myk = ops.h_col[sg.x + lane];
+                myh = ops.h_val32[sg.x + lane];
+            }
+            float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
+#pragma unroll
+            for (int it = 0; it < kSegLen / 4; ++it) {
+                const int e = it * 4 + grp;
+                const int k = __shfl_sync(0xffffffffu, myk, e);
+                const float h = __shfl_sync(0xffffffffu, myh, e);
+                if (e < len) {
+                    xr = f4fma(h, *reinterpret_cast<const float4 *>(re + (size_t)k * np), xr);
+                    xi = f4fma(h, *reinterpret_cast<const float4 *>(im + (size_t)k * np), xi);
+                }
+            }
+            xr = f4xor(xr, 8);
+            xr = f4xor(xr, 16);
+            xi = f4xor(xi, 8);
+            xi = f4xor(xi, 16);
+            if (grp == 0) {
+                float4 *slot = reinterpret_cast<float4 *>(slots + si * 2 * TS);
+                slot[sub] = xr;
+                slot[TS / 4 + sub] = xi;
+            }
+        }
+        __syncthreads();
+        // per row: sum its segments of this round in order (rows without
+        // nonzeros, and padding rows, get zeros)
+        for (int t = threadIdx.x; t < TS * 2 * TS; t += NT) {
+            const int a = t / (2 * TS), c = t - a * (2 * TS);
+            const int ga = rt * TS + a;
+            const int r0 = max(ops.rowseg[ga], base), r1 = min(ops.rowseg[ga + 1], base + cnt);
+            float acc = (base == s0) ? 0.f : sX[a * LDX + c];
+            for (int q = r0; q < r1; ++q) acc = __fadd_rn(acc, slots[(q - base) * 2 * TS + c]);
+            sX[a * LDX + c] = acc;
+        }
+        __syncthreads();
+        base += cnt;
+    } while (base < s1);
+}
+
+// g = G p(delta) for an FP32 delta (the gain is linear in p; there is no
+// trace normalisation inside a block of delta steps) for rows
+// r_begin, r_begin + r_step, ... < r_end (one warp per row), written to
+// out[i - out_base]. Every CTA computes the trace and dangling mass itself.
+__device__ __forceinline__ void gain_rows(const DevOps &ops, const float *__restrict__ din, int r_begin, int r_step,
+                                          int r_end, int out_base, float *out) {
+    __shared__ double red[32];
+    const int n = ops.n, np = ops.np;
+    double P = 0.0, Dd = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double pj = (double)din[(size_t)j * np + j];
+        P += pj;
+        if (ops.dang[j]) Dd += pj;
+    }
+    P = block_sum_d(P, red);
+    Dd = block_sum_d(Dd, red);
+    const double inv_nm1 = __drcp_rn((double)(n - 1));
+    const int lane = threadIdx.x & 31;
+    for (int i = r_begin + (threadIdx.x >> 5); i < r_end; i += r_step) {
+        double s = 0.0;
+        if (i < n)
+            for (int q = ops.s_ptr[i] + lane; q < ops.s_ptr[i + 1]; q += 32) {
+                const int j = ops.s_col[q];
+                s = __fma_rn(ops.s_val[q], (double)din[(size_t)j * np + j], s);
+            }
+        s = warp_sum_d(s);
+        if (lane == 0) {
+            double gi = 0.0;
+            if (i < n) {
+                const double pi = (double)din[(size_t)i * np + i];
+                const double dterm = (ops.dangling == QPR_DANGLING_F)
+                                         ? __dmul_rn(__dsub_rn(Dd, ops.dang[i] ? pi : 0.0), inv_nm1)
+                                         : __ddiv_rn(Dd, (double)n);
+                gi = __fma_rn(ops.alpha, __dadd_rn(s, dterm),
+                              __dmul_rn(__dmul_rn(__dsub_rn(1.0, ops.alpha), __dsub_rn(P, pi)), inv_nm1));
+            }
+            out[i - out_base] = (float)gi;
+        }
+    }
+}
+
+// Stop decision of stage 2 from the stage-1 residual partials (an
+// FP32-accurate estimate of ||f(y_n)||_F; a pass is confirmed by an exact
+// FP64 refresh on the host side of the loop). Every CTA computes the same
+// decision; the one with `first` records it. A step index whose exact
+// residual a refresh already judged is not judged again. Returns true when
+// the run stops (uniform over the CTA).
+__device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
+    __shared__ double red[32];
+    Ctl *ctl = w.ctl;
+    if (ctl->resid_exact_step == ctl->step) return false;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s += w.partials[i];
+    s = block_sum_d(s, red);
+    const double r = sqrt(s);
+    int status = kCtlRunning;
+    if (!isfinite(r)) status = kCtlNonFinite;
+    else if (r < ctl->tol) status = kCtlCandidate;
+    else if (ctl->step >= ctl->max_steps) status = kCtlMaxSteps;
+    __syncthreads();  // every thread has read ctl before it may change
+    if (first && threadIdx.x == 0) {
+        ctl->resid = r;
+        ctl->resid_step = ctl->step;
+        if (status != kCtlRunning) {
+            ctl->status = status;
+            ctl->done = 1;
+        }
+    }
+    return status != kCtlRunning;
 }
 
 // One tile pair (I, J) of stage STAGE of the sparse mixed form; pidx is the
@@ -97,15 +201,23 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
     double *sO64 = sOraw;
     float *sO32 = (STAGE == 4) ? reinterpret_cast<float *>(sOraw + 2 * TS * LDO) : reinterpret_cast<float *>(sOraw);
     __shared__ double red[NT / 32];
+    __shared__ float sg[TS];
     const bool diag = (I == J);
+    if (STAGE == 2 && stage2_decide(w, first)) return;
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
     float *dnext = (STAGE == 2) ? w.db : w.da;
 
-    spmm32_tile(ops, din, plane, I, J, sX1);
-    if (!diag) spmm32_tile(ops, din, plane, J, I, sX2);
-    __syncthreads();
+    static_assert(kSegSlots * 2 * TS * 4 <= (int)sizeof(sOraw), "segment slots alias the output stash");
+    spmm32_tile(ops, din, plane, I, J, sX1, reinterpret_cast<float *>(sOraw));
+    if (!diag) spmm32_tile(ops, din, plane, J, I, sX2, reinterpret_cast<float *>(sOraw));
+    // only diagonal tiles add the gain g = G p(delta); they compute it for
+    // their own rows
+    if (diag) {
+        gain_rows(ops, din, I * TS, NT / 32, I * TS + TS, I * TS, sg);
+        __syncthreads();
+    }
     const float *X2 = diag ? sX1 : sX2;
 
     const float om = (float)ops.omega, cm = 1.0f - om;
@@ -113,6 +225,7 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
     const float dtf = (float)dt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double nrm = 0.0;
+#pragma unroll
     for (int e = tid; e < TS * TS; e += NT) {
         const int a = e / TS, b = e - (e / TS) * TS;
         const int ga = I * TS + a, gb = J * TS + b;
@@ -125,7 +238,7 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
         const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(ops.c32[ga], ops.c32[gb])));
         float kdr = __fmaf_rn(-omhc, dr, __fmul_rn(cm, __fadd_rn(Bab, Bba)));
         const float kdi = __fmaf_rn(-omhc, di, __fmul_rn(-cm, __fsub_rn(Aab, Aba)));
-        if (ga == gb) kdr = __fmaf_rn(om, w.g[ga], kdr);
+        if (ga == gb) kdr = __fmaf_rn(om, sg[a], kdr);
         if (STAGE <= 3) {
             const float kr = __fadd_rn(kdr, w.F32[off]), ki = __fadd_rn(kdi, w.F32[plane + off]);
             if (STAGE == 1) nrm = __fma_rn((double)kr, (double)kr, __fma_rn((double)ki, (double)ki, nrm));
@@ -187,81 +300,15 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
     __syncthreads();
 }
 
-__device__ __forceinline__ double block_sum_d(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum_d(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-    return s;
-}
 
-// g = G p(delta) for an FP32 delta (the gain is linear in p; no trace
-// normalisation inside a block of delta steps). Stage 2 first takes the stop
-// decision from the stage-1 residual partials (an FP32-accurate estimate of
-// ||f(y_n)||_F; a pass is confirmed by an exact FP64 refresh on the host
-// side of the loop).
+// The gain kernel of the dense (tensor-core) stage: stage 2 also takes the
+// stop decision (CTA blk 0).
 template <int STAGE>
 __device__ __forceinline__ void gain_mixed_body(const DevOps &ops, const MixedWork &w, const float *__restrict__ din,
                                                 int blk, int nblk) {
-    __shared__ double red[32];
-    Ctl *ctl = w.ctl;
-    const int n = ops.n, np = ops.np;
-    // (a step index whose exact residual the refresh already judged is not
-    // judged again on the estimate)
-    if (STAGE == 2 && blk == 0 && ctl->resid_exact_step != ctl->step) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s += w.partials[i];
-        s = block_sum_d(s, red);
-        if (threadIdx.x == 0) {
-            const double r = sqrt(s);
-            ctl->resid = r;
-            ctl->resid_step = ctl->step;
-            if (!isfinite(r)) {
-                ctl->status = kCtlNonFinite;
-                ctl->done = 1;
-            } else if (r < ctl->tol) {
-                ctl->status = kCtlCandidate;
-                ctl->done = 1;
-            } else if (ctl->step >= ctl->max_steps) {
-                ctl->status = kCtlMaxSteps;
-                ctl->done = 1;
-            }
-        }
-    }
-    double P = 0.0, Dd = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double pj = (double)din[(size_t)j * np + j];
-        P += pj;
-        if (ops.dang[j]) Dd += pj;
-    }
-    P = block_sum_d(P, red);
-    Dd = block_sum_d(Dd, red);
-    const double inv_nm1 = __drcp_rn((double)(n - 1));
-    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    for (int i = blk * wpb + (threadIdx.x >> 5); i < np; i += nblk * wpb) {
-        double s = 0.0;
-        if (i < n)
-            for (int q = ops.s_ptr[i] + lane; q < ops.s_ptr[i + 1]; q += 32) {
-                const int j = ops.s_col[q];
-                s = __fma_rn(ops.s_val[q], (double)din[(size_t)j * np + j], s);
-            }
-        s = warp_sum_d(s);
-        if (lane == 0) {
-            double gi = 0.0;
-            if (i < n) {
-                const double pi = (double)din[(size_t)i * np + i];
-                const double dterm = (ops.dangling == QPR_DANGLING_F)
-                                         ? __dmul_rn(__dsub_rn(Dd, ops.dang[i] ? pi : 0.0), inv_nm1)
-                                         : __ddiv_rn(Dd, (double)n);
-                gi = __fma_rn(ops.alpha, __dadd_rn(s, dterm),
-                              __dmul_rn(__dmul_rn(__dsub_rn(1.0, ops.alpha), __dsub_rn(P, pi)), inv_nm1));
-            }
-            w.g[i] = (float)gi;
-        }
-    }
+    if (STAGE == 2) stage2_decide(w, blk == 0);
+    const int wpb = blockDim.x >> 5;
+    gain_rows(ops, din, blk * wpb, nblk * wpb, ops.np, 0, w.g);
 }
 
 // Refresh, part 1: sigma = 1 / Re tr(y) (one CTA).

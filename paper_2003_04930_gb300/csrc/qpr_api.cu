@@ -29,6 +29,8 @@ struct qpr_ctx {
     double *d_H = nullptr;
     int *d_hptr = nullptr, *d_hcol = nullptr;
     double *d_hval = nullptr;
+    int *d_rowseg = nullptr;
+    int2 *d_seg = nullptr;
     int backend = QPR_BACKEND_SPARSE;
     int *d_sptr = nullptr, *d_scol = nullptr;
     double *d_sval = nullptr;
@@ -260,7 +262,8 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         } else {
             enqueue_mixed_block(ctx, block);
         }
-        ctx->launches += qpr::kMixedLaunchesPerRefresh + qpr::kMixedLaunchesPerStep * (int64_t)block;
+        ctx->launches += qpr::kMixedLaunchesPerRefresh +
+                         (ctx->mw.splitD ? 2 : 1) * qpr::kMixedLaunchesPerStep * (int64_t)block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
         if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
@@ -331,6 +334,18 @@ double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::ve
 }
 
 void set_create_error(const std::string &msg) { g_create_error = msg; }
+
+void row_segments(const HostOps &h, int np, int len, std::vector<int> &rowseg, std::vector<int2> &seg) {
+    rowseg.assign((size_t)np + 1, 0);
+    seg.clear();
+    for (int i = 0; i < np; ++i) {
+        rowseg[i] = (int)seg.size();
+        if (i < h.n)
+            for (int64_t q = h.hptr[i]; q < h.hptr[i + 1]; q += len)
+                seg.push_back(make_int2((int)q, (int)std::min<int64_t>(q + len, h.hptr[i + 1])));
+    }
+    rowseg[np] = (int)seg.size();
+}
 
 // Operators of Supplementary Note 1 on the host: adjacency (A_ij = w for the
 // link j -> i, duplicates summed, self-loops and zero weights dropped),
@@ -496,6 +511,8 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_hptr);
+    cudaFree(ctx->d_rowseg);
+    cudaFree(ctx->d_seg);
     cudaFree(ctx->d_hcol);
     cudaFree(ctx->d_hval);
     cudaFree(ctx->d_sptr);
@@ -663,6 +680,14 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         for (size_t q = 0; q < hval.size(); ++q) hv32[q] = (float)hval[q];
         std::vector<float> c32(np);
         for (int j = 0; j < np; ++j) c32[j] = (float)c[j];
+        std::vector<int> rowseg;
+        std::vector<int2> segs;
+        qpr::row_segments(hops, np, 32, rowseg, segs);
+        CREATE_CUDA(cudaMalloc(&ctx->d_rowseg, rowseg.size() * sizeof(int)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_rowseg, rowseg.data(), rowseg.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_seg, std::max<size_t>(1, segs.size()) * sizeof(int2)));
+        if (!segs.empty())
+            CREATE_CUDA(cudaMemcpy(ctx->d_seg, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice));
         CREATE_CUDA(cudaMalloc(&ctx->d_hval32, hv32.size() * sizeof(float)));
         CREATE_CUDA(cudaMemcpy(ctx->d_hval32, hv32.data(), hv32.size() * sizeof(float), cudaMemcpyHostToDevice));
         CREATE_CUDA(cudaMalloc(&ctx->d_c32, np * sizeof(float)));
@@ -732,6 +757,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ops.c = ctx->d_c;
     ops.c32 = ctx->d_c32;
     ops.h_val32 = ctx->d_hval32;
+    ops.rowseg = ctx->d_rowseg;
+    ops.seg = ctx->d_seg;
     qpr::Work &wk = ctx->work;
     wk.y = ctx->d_state;
     wk.z = ctx->d_state + 2 * plane;

@@ -49,6 +49,11 @@ struct DevOps {
     const int *h_col;
     const double *h_val;
     const float *h_val32; // the same values rounded to FP32 (mixed form)
+    // rows of H cut into segments of at most 32 nonzeros (mixed form):
+    // segments of row i are seg[rowseg[i] .. rowseg[i+1]), each {q0, q1}
+    // into h_col / h_val; rowseg has np + 1 entries (empty for padding)
+    const int *rowseg;
+    const int2 *seg;
     const int *s_ptr;     // CSR of S restricted to columns with out-links: n + 1 row pointers
     const int *s_col;
     const double *s_val;  // A_ij / outDeg(j)
@@ -143,7 +148,7 @@ bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfl
                   TcMaps *maps);
 void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcMaps &m, cudaStream_t s);
 // Kernel launches per RK4 step and per refresh of the mixed form.
-constexpr int kMixedLaunchesPerStep = 8;
+constexpr int kMixedLaunchesPerStep = 4;   // sparse backend (the dense one adds 4 gain kernels)
 constexpr int kMixedLaunchesPerRefresh = 5;
 
 // ---- host assembly (qpr_api.cu) ----
@@ -159,6 +164,9 @@ struct HostOps {
 };
 qpr_status assemble_host(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w, int h_diag,
                          HostOps &out, std::string &err);
+// Segments of at most `len` nonzeros of every row of the CSR of H, for np
+// rows (rowseg: np + 1 entries, seg: {q0, q1}).
+void row_segments(const HostOps &h, int np, int len, std::vector<int> &rowseg, std::vector<int2> &seg);
 std::vector<double> column_sums_G(const HostOps &h, double alpha, int np, double *cmax);
 // Message returned by qpr_last_error(NULL) on this thread.
 void set_create_error(const std::string &msg);

@@ -107,7 +107,8 @@ void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaSt
     const float *din = (stage == 1) ? w.D : (stage == 3 ? w.db : w.da);
     int gb = (ops.np + 7) / 8;
     if (gb > 152) gb = 152;
-    if (parts & 1) {
+    // the sparse stage kernel computes the gain and the stop decision itself
+    if ((parts & 1) && w.splitD) {
         switch (stage) {
             case 1: gain_mixed_kernel<1><<<gb, 256, 0, s>>>(ops, w, din); break;
             case 2: gain_mixed_kernel<2><<<gb, 256, 0, s>>>(ops, w, din); break;
