@@ -220,6 +220,28 @@ typedef struct {
 QPR_API qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *problems, double alpha, double dt,
                                           double tol, int64_t max_steps, const qpr_options *opt, qpr_stats *stats);
 
+/* ---- autotuner ----
+ * Chooses, for one problem and one precision, the stage-kernel family
+ * (QPR_BACKEND_SPARSE: CSR gathers; QPR_BACKEND_DENSE: DMMA for QPR_FP64,
+ * split-BF16 tcgen05 for QPR_MIXED) and, for QPR_MIXED, ref_refresh in
+ * {8, 16, 32, 64}, by timing short real runs (qpr_evolve from I/N, 4 warm-up
+ * steps, then max(16, 2 ref_refresh) timed steps) of every candidate on the
+ * device. The paper has no counterpart. With cache_path (nullable) the choice is read
+ * from / appended to a text file keyed by GPU name, precision,
+ * floor(log2 N) and floor(log2(nnz(H)/N + 1)); a cached answer sets
+ * from_cache. `base` supplies the other options (NULL: defaults). */
+typedef struct {
+    int32_t backend;
+    int32_t ref_refresh;
+    double ms_per_step;  /* measured wall time of one step of the chosen configuration */
+    int32_t from_cache;
+    int32_t reserved[3];
+} qpr_tune_result;
+
+QPR_API qpr_status qpr_autotune(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w,
+                                double alpha, double omega, double dt, const qpr_options *base,
+                                const char *cache_path, qpr_tune_result *out);
+
 /* ---- learned warm start ----
  * A 4-layer message-passing network (width 64, BF16 weights, FP32
  * accumulation) that predicts the steady-state populations from the graph;

@@ -29,7 +29,7 @@ EXPORTED = (
     "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
-    "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train",
+    "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune",
 )
 QPR_NOALLOC_MAX_N = 256
 
@@ -61,6 +61,11 @@ class qpr_problem(ctypes.Structure):
 class qpr_gnn_sample(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("w", ctypes.c_void_p), ("omega", ctypes.c_double), ("p", ctypes.c_void_p)]
+
+
+class qpr_tune_result(ctypes.Structure):
+    _fields_ = [("backend", ctypes.c_int32), ("ref_refresh", ctypes.c_int32), ("ms_per_step", ctypes.c_double),
+                ("from_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class QprError(RuntimeError):
@@ -131,6 +136,9 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_gnn_train.argtypes = [vp, i64, ctypes.POINTER(qpr_gnn_sample), f64, ctypes.c_int32, ctypes.c_int32, f64,
                                   ctypes.c_uint64, vp]
     lib.qpr_gnn_train.restype = st
+    lib.qpr_autotune.argtypes = [i64, i64, vp, vp, vp, f64, f64, f64, ctypes.POINTER(qpr_options), ctypes.c_char_p,
+                                 ctypes.POINTER(qpr_tune_result)]
+    lib.qpr_autotune.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
     _lib = lib
@@ -386,3 +394,23 @@ class Gnn:
         self._raise(self._lib.qpr_gnn_train(self._h, len(samples), arr, float(alpha), int(epochs), int(batch),
                                             float(lr), int(seed), _ptr(losses)))
         return losses
+
+
+def autotune(g, omega, alpha=0.85, dt=0.01, precision=QPR_MIXED, cache_path=None, device=-1):
+    """qpr_autotune for an EdgeList: returns dict(backend, ref_refresh,
+    ms_per_step, from_cache)."""
+    lib = load_library()
+    src = np.ascontiguousarray(g.src, dtype=np.int64)
+    dst = np.ascontiguousarray(g.dst, dtype=np.int64)
+    w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float64)
+    opt = qpr_options()
+    lib.qpr_default_options(ctypes.byref(opt))
+    opt.precision, opt.device = int(precision), int(device)
+    res = qpr_tune_result()
+    st = lib.qpr_autotune(int(g.n), int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(w), float(alpha), float(omega),
+                          float(dt), ctypes.byref(opt), None if cache_path is None else str(cache_path).encode(),
+                          ctypes.byref(res))
+    if st != QPR_OK:
+        raise QprError(st, lib.qpr_last_error(None).decode())
+    return {"backend": res.backend, "ref_refresh": res.ref_refresh, "ms_per_step": res.ms_per_step,
+            "from_cache": res.from_cache}
