@@ -103,14 +103,22 @@ __global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const
 
 template <int STAGE>
 __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 t = items[it];
         load_graph(gs, t.x, sg);
-        if (!graph_done(sg, &s_flag)) mixed::mixed_sparse_tile<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0);
+        if (!graph_done(sg, &s_flag))
+            mixed::mixed_sparse_tile<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0, dyn_smem);
         __syncthreads();
     }
+}
+
+template <int STAGE>
+cudaError_t set_b_attr() {
+    return cudaFuncSetAttribute(b_stage_mixed_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mixed::kMixedDynSmem);
 }
 
 struct Lists {
@@ -138,11 +146,12 @@ void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream
 }
 
 void launch_step(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
-    const int grid = std::min(L.nitems, 152 * 5);
-    b_stage_mixed_kernel<1><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<2><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<3><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<4><<<grid, kStageNT, 0, s>>>(gs, L.items, L.nitems);
+    const int grid = std::min(L.nitems, 152 * 3);
+    const int dsm = mixed::kMixedDynSmem;
+    b_stage_mixed_kernel<1><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
+    b_stage_mixed_kernel<2><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
+    b_stage_mixed_kernel<3><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
+    b_stage_mixed_kernel<4><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
     launches += 4;
 }
 
@@ -186,8 +195,14 @@ struct BatchMem {
 }  // namespace
 
 cudaError_t init_batch() {
-    return cudaFuncSetAttribute(b_sparse64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                sparse64::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(b_sparse64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sparse64::SMEM_BYTES);
+    if (e == cudaSuccess) e = set_b_attr<1>();
+    if (e == cudaSuccess) e = set_b_attr<2>();
+    if (e == cudaSuccess) e = set_b_attr<3>();
+    if (e == cudaSuccess) e = set_b_attr<4>();
+    if (e == cudaSuccess) e = init_stage_mixed();
+    return e;
 }
 
 }  // namespace qpr

@@ -115,6 +115,101 @@ __device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__re
     } while (base < s1);
 }
 
+constexpr int kStageEntries = 3072;  // staged CSR entries of the two row tiles (24 KB)
+// Dynamic shared memory of the sparse mixed stage: segment slots, staged
+// segment headers, staged columns and values; the epilogue's output stash
+// (25.3 KB) reuses the same bytes afterwards.
+constexpr int kMixedDynSmem = kSegSlots * 2 * TS * 4 + kSegSlots * 8 + kStageEntries * 8;
+static_assert(kMixedDynSmem >= (2 * TS * LDO * 8 + 2 * TS * LDO * 4), "output stash fits the dynamic buffer");
+
+// Both products of a tile pair, X_IJ (rows of I, columns of J, into sX1)
+// and, unless I == J, X_JI (into sX2). When the segments of both row tiles
+// fit the slots and their CSR entries fit the staging buffer, the segment
+// headers, columns and values are first copied to shared memory with
+// coalesced loads, so that each segment costs one round of gathers from
+// L2; otherwise one tile after the other without staging. The sums per row
+// are formed exactly as in spmm32_tile (segment order), so the result does
+// not depend on the path taken.
+__device__ __forceinline__ void spmm32_pair(const DevOps &ops, const float *__restrict__ d, size_t plane, int I,
+                                            int J, bool diag, float *sX1, float *sX2, uint8_t *dyn) {
+    float *slots = reinterpret_cast<float *>(dyn);
+    int2 *hdr = reinterpret_cast<int2 *>(dyn + kSegSlots * 2 * TS * 4);
+    int *scol = reinterpret_cast<int *>(hdr + kSegSlots);
+    float *sval = reinterpret_cast<float *>(scol + kStageEntries);
+    const int sI0 = ops.rowseg[I * TS], sI1 = ops.rowseg[I * TS + TS];
+    const int sJ0 = diag ? 0 : ops.rowseg[J * TS], sJ1 = diag ? 0 : ops.rowseg[J * TS + TS];
+    const int cI = sI1 - sI0, cJ = sJ1 - sJ0;
+    const int qI0 = cI ? ops.seg[sI0].x : 0, qI1 = cI ? ops.seg[sI1 - 1].y : 0;
+    const int qJ0 = cJ ? ops.seg[sJ0].x : 0, qJ1 = cJ ? ops.seg[sJ1 - 1].y : 0;
+    const int lenI = qI1 - qI0, lenJ = qJ1 - qJ0;
+    if (cI + cJ > kSegSlots || lenI + lenJ > kStageEntries) {
+        spmm32_tile(ops, d, plane, I, J, sX1, slots);
+        if (!diag) spmm32_tile(ops, d, plane, J, I, sX2, slots);
+        return;
+    }
+    for (int t = threadIdx.x; t < cI + cJ; t += NT) {
+        const bool ti = t < cI;
+        const int2 sg = ops.seg[ti ? sI0 + t : sJ0 + (t - cI)];
+        const int base = ti ? -qI0 : lenI - qJ0;
+        hdr[t] = make_int2(sg.x + base, sg.y + base);
+    }
+    for (int t = threadIdx.x; t < lenI + lenJ; t += NT) {
+        const int q = t < lenI ? qI0 + t : qJ0 + (t - lenI);
+        scol[t] = ops.h_col[q];
+        sval[t] = ops.h_val32[q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 3, sub = lane & 7;
+    const int np = ops.np;
+    for (int si = warp; si < cI + cJ; si += NT / 32) {
+        const int ct = si < cI ? J : I;
+        const float *__restrict__ re = d + ct * TS + 4 * sub;
+        const float *__restrict__ im = d + plane + ct * TS + 4 * sub;
+        const int2 sg = hdr[si];
+        const int len = sg.y - sg.x;
+        int myk = 0;
+        float myh = 0.f;
+        if (lane < len) {
+            myk = scol[sg.x + lane];
+            myh = sval[sg.x + lane];
+        }
+        float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
+#pragma unroll
+        for (int it = 0; it < kSegLen / 4; ++it) {
+            const int e = it * 4 + grp;
+            const int k = __shfl_sync(0xffffffffu, myk, e);
+            const float h = __shfl_sync(0xffffffffu, myh, e);
+            if (e < len) {
+                xr = f4fma(h, *reinterpret_cast<const float4 *>(re + (size_t)k * np), xr);
+                xi = f4fma(h, *reinterpret_cast<const float4 *>(im + (size_t)k * np), xi);
+            }
+        }
+        xr = f4xor(xr, 8);
+        xr = f4xor(xr, 16);
+        xi = f4xor(xi, 8);
+        xi = f4xor(xi, 16);
+        if (grp == 0) {
+            float4 *slot = reinterpret_cast<float4 *>(slots + si * 2 * TS);
+            slot[sub] = xr;
+            slot[TS / 4 + sub] = xi;
+        }
+    }
+    __syncthreads();
+    const int ntiles = diag ? 1 : 2;
+    for (int t = threadIdx.x; t < ntiles * TS * 2 * TS; t += NT) {
+        const int which = t / (TS * 2 * TS);  // 0: rows of I into sX1, 1: rows of J into sX2
+        const int u = t - which * (TS * 2 * TS);
+        const int a = u / (2 * TS), c = u - a * (2 * TS);
+        const int ga = (which ? J : I) * TS + a;
+        const int off = which ? cI - sJ0 : -sI0;  // slot index = segment index + off
+        float acc = 0.f;
+        for (int q = ops.rowseg[ga]; q < ops.rowseg[ga + 1]; ++q) acc = __fadd_rn(acc, slots[(q + off) * 2 * TS + c]);
+        (which ? sX2 : sX1)[a * LDX + c] = acc;
+    }
+    __syncthreads();
+}
+
 // g = G p(delta) for an FP32 delta (the gain is linear in p; there is no
 // trace normalisation inside a block of delta steps) for rows
 // r_begin, r_begin + r_step, ... < r_end (one warp per row), written to
@@ -189,15 +284,16 @@ __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
 // One tile pair (I, J) of stage STAGE of the sparse mixed form; pidx is the
 // slot of its residual partial, first marks the pair that advances the step
 // counter. Ends with a barrier so that the caller may reuse shared memory.
+// dyn: kMixedDynSmem bytes of dynamic shared memory (16-byte aligned).
 template <int STAGE>
 __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
-                                                  bool first) {
+                                                  bool first, uint8_t *dyn) {
     __shared__ __align__(16) float sX1[TS * LDX];
     __shared__ __align__(16) float sX2[TS * LDX];
     // outputs of tile (I, J) kept for the mirrored write: stages 1-3 keep S and
     // the next delta (4 FP32 planes), stage 4 the new y (2 FP64 planes) and D
-    // (2 FP32 planes); 25.3 KB either way
-    __shared__ __align__(16) double sOraw[(2 * TS * LDO * 8 + 2 * TS * LDO * 4) / 8];
+    // (2 FP32 planes); 25.3 KB either way, in the dynamic buffer
+    double *sOraw = reinterpret_cast<double *>(dyn);
     double *sO64 = sOraw;
     float *sO32 = (STAGE == 4) ? reinterpret_cast<float *>(sOraw + 2 * TS * LDO) : reinterpret_cast<float *>(sOraw);
     __shared__ double red[NT / 32];
@@ -209,9 +305,7 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
     const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
     float *dnext = (STAGE == 2) ? w.db : w.da;
 
-    static_assert(kSegSlots * 2 * TS * 4 <= (int)sizeof(sOraw), "segment slots alias the output stash");
-    spmm32_tile(ops, din, plane, I, J, sX1, reinterpret_cast<float *>(sOraw));
-    if (!diag) spmm32_tile(ops, din, plane, J, I, sX2, reinterpret_cast<float *>(sOraw));
+    spmm32_pair(ops, din, plane, I, J, diag, sX1, sX2, dyn);
     // only diagonal tiles add the gain g = G p(delta); they compute it for
     // their own rows
     if (diag) {
@@ -222,9 +316,10 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
 
     const float om = (float)ops.omega, cm = 1.0f - om;
     const double dt = w.ctl->dt;
+    const double dt6 = __ddiv_rn(dt, 6.0);  // once per tile: FP64 division is slow on this part
     const float dtf = (float)dt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double nrm = 0.0;
+    float nrm = 0.f;  // this thread's share of ||k1||^2 (an FP32-accurate estimate)
 #pragma unroll
     for (int e = tid; e < TS * TS; e += NT) {
         const int a = e / TS, b = e - (e / TS) * TS;
@@ -241,7 +336,7 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
         if (ga == gb) kdr = __fmaf_rn(om, sg[a], kdr);
         if (STAGE <= 3) {
             const float kr = __fadd_rn(kdr, w.F32[off]), ki = __fadd_rn(kdi, w.F32[plane + off]);
-            if (STAGE == 1) nrm = __fma_rn((double)kr, (double)kr, __fma_rn((double)ki, (double)ki, nrm));
+            if (STAGE == 1) nrm = __fmaf_rn(kr, kr, __fmaf_rn(ki, ki, nrm));
             const float Dr = w.D[off], Di = w.D[plane + off];
             float sr, si;
             if (STAGE == 1) { sr = kdr; si = kdi; }
@@ -256,7 +351,6 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
             sO32[3 * TS * LDO + a * LDO + b] = ni;
         } else {
             const double sr = (double)__fadd_rn(w.S[off], kdr), si = (double)__fadd_rn(w.S[plane + off], kdi);
-            const double dt6 = __ddiv_rn(dt, 6.0);
             const double yr = __fma_rn(dt6, sr, __fma_rn(dt, w.F[off], w.y[off]));
             const double yi = __fma_rn(dt6, si, __fma_rn(dt, w.F[plane + off], w.y[plane + off]));
             const float Dr = (float)__dsub_rn(yr, w.R[off]), Di = (float)__dsub_rn(yi, w.R[plane + off]);
@@ -269,8 +363,8 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
         }
     }
     if (STAGE == 1) {
-        nrm = warp_sum_d(nrm);
-        if (lane == 0) red[warp] = nrm;
+        const double nrm_d = warp_sum_d((double)nrm);
+        if (lane == 0) red[warp] = nrm_d;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;

@@ -628,6 +628,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     }
     CREATE_CUDA(qpr::init_stage_fp64());
     CREATE_CUDA(qpr::init_stage_sparse());
+    CREATE_CUDA(qpr::init_stage_mixed());
     const int np = ctx->np;
     const size_t plane = (size_t)np * np;
     // dense H, np x np with zero padding

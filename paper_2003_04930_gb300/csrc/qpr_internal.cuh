@@ -142,6 +142,8 @@ void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s)
 // One RK4 stage: parts & 1 launches the gain of the stage delta, parts & 2
 // the FP32 sparse stage kernel (3 = both, in that order).
 void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+// Opt in to the dynamic shared memory of the sparse mixed stage kernels.
+cudaError_t init_stage_mixed();
 // Dense backend of the mixed form (stage_mixed_tc.cu).
 cudaError_t init_mixed_tc();
 bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfloat16 *const dsplit[3],

@@ -35,11 +35,19 @@ using namespace mixed;
 template <int STAGE>
 __global__ void __launch_bounds__(NT)
 stage_mixed_sparse_kernel(DevOps ops, MixedWork w) {
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ int s_done;
     if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
     __syncthreads();
     if (s_done) return;
-    mixed_sparse_tile<STAGE>(ops, w, w.pairs[blockIdx.x].x, w.pairs[blockIdx.x].y, blockIdx.x, blockIdx.x == 0);
+    mixed_sparse_tile<STAGE>(ops, w, w.pairs[blockIdx.x].x, w.pairs[blockIdx.x].y, blockIdx.x, blockIdx.x == 0,
+                             dyn_smem);
+}
+
+template <int STAGE>
+cudaError_t set_mixed_attr() {
+    return cudaFuncSetAttribute(stage_mixed_sparse_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMixedDynSmem);
 }
 
 template <int STAGE>
@@ -82,6 +90,14 @@ int grid_elems(size_t work) {
 
 }  // namespace
 
+cudaError_t init_stage_mixed() {
+    cudaError_t e = set_mixed_attr<1>();
+    if (e == cudaSuccess) e = set_mixed_attr<2>();
+    if (e == cudaSuccess) e = set_mixed_attr<3>();
+    if (e == cudaSuccess) e = set_mixed_attr<4>();
+    return e;
+}
+
 void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s) {
     const size_t tot = 2 * (size_t)ops.np * ops.np;
     refresh_trace_kernel<<<1, 256, 0, s>>>(ops, w);
@@ -122,10 +138,10 @@ void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaSt
     }
     if (parts & 2) {
         switch (stage) {
-            case 1: stage_mixed_sparse_kernel<1><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            case 2: stage_mixed_sparse_kernel<2><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            case 3: stage_mixed_sparse_kernel<3><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            default: stage_mixed_sparse_kernel<4><<<w.npairs, NT, 0, s>>>(ops, w); break;
+            case 1: stage_mixed_sparse_kernel<1><<<w.npairs, NT, kMixedDynSmem, s>>>(ops, w); break;
+            case 2: stage_mixed_sparse_kernel<2><<<w.npairs, NT, kMixedDynSmem, s>>>(ops, w); break;
+            case 3: stage_mixed_sparse_kernel<3><<<w.npairs, NT, kMixedDynSmem, s>>>(ops, w); break;
+            default: stage_mixed_sparse_kernel<4><<<w.npairs, NT, kMixedDynSmem, s>>>(ops, w); break;
         }
     }
 }
