@@ -271,9 +271,9 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         const size_t p2 = 2 * (size_t)np[g] * np[g];
         const size_t nh = H[g].hval.size(), ns = H[g].sval.size(), n = (size_t)problems[g].n;
         od[g] = nd;
-        nd += qpr::align_up(3 * p2 + 2 * np[g] + nh + ns + npairs[g], 64);
+        nd += qpr::align_up(2 * p2 + 2 * np[g] + nh + ns + npairs[g], 64);
         of[g] = nf;
-        nf += qpr::align_up(5 * p2 + 2 * np[g] + qpr::align_up(nh, 64), 64) + 64;
+        nf += qpr::align_up(8 * p2 + 2 * np[g] + qpr::align_up(nh, 64) + qpr::align_up(ns, 64) + npairs[g], 64) + 64;
         oi[g] = ni;
         ni += qpr::align_up(2 * (n + 1) + nh + ns, 64) + qpr::align_up((size_t)np[g] + 1, 64) + 2 * segs[g].size();
         ni = qpr::align_up(ni, 64);
@@ -352,18 +352,22 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         double *bd = dD + od[g];
         float *bf = dF + of[g];
         int *bi = dI + oi[g];
-        // double arena: y R F | g64 c | hval sval | partials
-        double *y = bd, *R = bd + p2, *F = bd + 2 * p2, *g64 = bd + 3 * p2, *c = g64 + p;
+        // double arena: R F | g64 c | hval sval | partials
+        double *R = bd, *F = bd + p2, *g64 = bd + 2 * p2, *c = g64 + p;
         double *hval = c + p, *sval = hval + nh, *part = sval + ns;
         std::vector<double> cg = qpr::column_sums_G(h, alpha, p, nullptr);
         std::copy(cg.begin(), cg.end(), hD.begin() + (c - dD));
         std::copy(h.hval.begin(), h.hval.end(), hD.begin() + (hval - dD));
         std::copy(h.sval.begin(), h.sval.end(), hD.begin() + (sval - dD));
-        // float arena: F32 D da db S | g32 c32 | hval32
-        float *F32 = bf, *Dp = bf + p2, *da = bf + 2 * p2, *db = bf + 3 * p2, *S = bf + 4 * p2;
-        float *g32 = bf + 5 * p2, *c32 = g32 + p, *hv32 = c32 + p;
+        // float arena: F32 D Dlo da db S Ghi Glo | g32 c32 | hval32 | sval32 | partials32
+        // (uploaded from zeros, so the delta D + Dlo starts at 0)
+        float *F32 = bf, *Dp = bf + p2, *Dlo = bf + 2 * p2, *da = bf + 3 * p2, *db = bf + 4 * p2;
+        float *S = bf + 5 * p2, *Ghi = bf + 6 * p2, *Glo = bf + 7 * p2;
+        float *g32 = bf + 8 * p2, *c32 = g32 + p, *hv32 = c32 + p;
+        float *sv32 = hv32 + qpr::align_up(nh, 64), *part32 = sv32 + qpr::align_up(ns, 64);
         for (int j = 0; j < p; ++j) hF[(c32 - dF) + j] = (float)cg[j];
         for (size_t q = 0; q < nh; ++q) hF[(hv32 - dF) + q] = (float)h.hval[q];
+        for (size_t q = 0; q < ns; ++q) hF[(sv32 - dF) + q] = (float)h.sval[q];
         // int arena: hptr hcol sptr scol | rowseg | seg (pairs of ints)
         int *hptr = bi, *hcol = hptr + (n + 1), *sptr = hcol + nh, *scol = sptr + (n + 1);
         int *rseg = bi + qpr::align_up(2 * (size_t)(n + 1) + nh + ns, 64);
@@ -399,10 +403,16 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         d.ops.dang = dB + ob[g];
         d.ops.c = c;
         d.ops.c32 = c32;
+        d.ops.s_val32 = sv32;
+        d.ops.alpha32 = (float)alpha;
+        d.ops.oma32 = (float)(1.0 - alpha);
+        d.ops.omega32 = (float)problems[g].omega;
+        d.ops.inv_nm1_32 = (float)(1.0 / (double)(n - 1));
+        d.ops.inv_n32 = (float)(1.0 / (double)n);
         qpr::MixedWork &mw = d.mw;
-        mw.y = y; mw.R = R; mw.F = F;
-        mw.F32 = F32; mw.D = Dp; mw.da = da; mw.db = db; mw.S = S;
-        mw.g = g32; mw.g64 = g64; mw.partials = part;
+        mw.R = R; mw.F = F;
+        mw.F32 = F32; mw.D = Dp; mw.Dlo = Dlo; mw.da = da; mw.db = db; mw.S = S; mw.Ghi = Ghi; mw.Glo = Glo;
+        mw.g = g32; mw.g64 = g64; mw.partials = part; mw.partials32 = part32;
         mw.pairs = nullptr; mw.npairs = npairs[g]; mw.tiles = T[g];
         mw.ctl = dCtl + g;
         mw.nstage_partials = npairs[g];
@@ -431,7 +441,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
             BCUDA(cudaMemcpyAsync(dIO, problems[g].rho, (size_t)n * n * 16, cudaMemcpyHostToDevice, s));
             srcp = dIO;
         }
-        qpr::launch_import(srcp, n, np[g], desc[g].mw.y, s);
+        qpr::launch_import(srcp, n, np[g], desc[g].mw.R, s);
         ++launches;
     }
     BCUDA(cudaStreamSynchronize(s));  // hD, hF, ... and the staging buffer may be released / reused

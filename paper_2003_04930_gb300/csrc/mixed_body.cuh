@@ -35,6 +35,57 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum over the CTA in a fixed order (the same bits in every CTA and run).
+__device__ __forceinline__ float block_sum_f(float v, float *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_f(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float s = 0.f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s = __fadd_rn(s, red[q]);
+    return s;
+}
+
+// Float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2, about
+// 48 significant bits, carried by FP32 instructions only (the FP64 pipe of
+// this part runs at 1/64 of the FP32 rate). ff_add is Knuth's TwoSum of the
+// high parts with the low parts added to its error, then Dekker's
+// FastTwoSum to renormalise; ff_mul_f multiplies by an FP32 factor with the
+// FMA form of TwoProduct. Explicit round-to-nearest intrinsics: no
+// contraction may change these error-free transformations.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_add(float ah, float al, float bh, float bl) {
+    const float s = __fadd_rn(ah, bh);
+    const float v = __fsub_rn(s, ah);
+    float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(bh, v));
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_mul_f(float ah, float al, float b) {
+    const float p = __fmul_rn(ah, b);
+    const float e = __fmaf_rn(al, b, __fmaf_rn(ah, b, -p));
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// Delta update of stage 4 for one real component: delta + dt F + dt/6 s4,
+// with dt F = (gh, gl) and dt / 6 = (dt6h, dt6l) in float-float.
+__device__ __forceinline__ ff delta_update(float dh, float dl, float gh, float gl, float dt6h, float dt6l, float s4) {
+    const ff u = ff_mul_f(dt6h, dt6l, s4);
+    const ff t = ff_add(u.hi, u.lo, gh, gl);
+    return ff_add(dh, dl, t.hi, t.lo);
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum_d(v);
@@ -118,9 +169,9 @@ __device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__re
 constexpr int kStageEntries = 3072;  // staged CSR entries of the two row tiles (24 KB)
 // Dynamic shared memory of the sparse mixed stage: segment slots, staged
 // segment headers, staged columns and values; the epilogue's output stash
-// (25.3 KB) reuses the same bytes afterwards.
+// (16.9 KB) reuses the same bytes afterwards.
 constexpr int kMixedDynSmem = kSegSlots * 2 * TS * 4 + kSegSlots * 8 + kStageEntries * 8;
-static_assert(kMixedDynSmem >= (2 * TS * LDO * 8 + 2 * TS * LDO * 4), "output stash fits the dynamic buffer");
+static_assert(kMixedDynSmem >= 4 * TS * LDO * 4, "output stash fits the dynamic buffer");
 
 // Both products of a tile pair, X_IJ (rows of I, columns of J, into sX1)
 // and, unless I == J, X_JI (into sX2). When the segments of both row tiles
@@ -214,71 +265,78 @@ __device__ __forceinline__ void spmm32_pair(const DevOps &ops, const float *__re
 // trace normalisation inside a block of delta steps) for rows
 // r_begin, r_begin + r_step, ... < r_end (one warp per row), written to
 // out[i - out_base]. Every CTA computes the trace and dangling mass itself.
+// FP32 throughout, in a fixed order.
 __device__ __forceinline__ void gain_rows(const DevOps &ops, const float *__restrict__ din, int r_begin, int r_step,
                                           int r_end, int out_base, float *out) {
-    __shared__ double red[32];
+    __shared__ float red[32];
     const int n = ops.n, np = ops.np;
-    double P = 0.0, Dd = 0.0;
+    float P = 0.f, Dd = 0.f;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double pj = (double)din[(size_t)j * np + j];
-        P += pj;
-        if (ops.dang[j]) Dd += pj;
+        const float pj = din[(size_t)j * np + j];
+        P = __fadd_rn(P, pj);
+        if (ops.dang[j]) Dd = __fadd_rn(Dd, pj);
     }
-    P = block_sum_d(P, red);
-    Dd = block_sum_d(Dd, red);
-    const double inv_nm1 = __drcp_rn((double)(n - 1));
+    P = block_sum_f(P, red);
+    Dd = block_sum_f(Dd, red);
     const int lane = threadIdx.x & 31;
     for (int i = r_begin + (threadIdx.x >> 5); i < r_end; i += r_step) {
-        double s = 0.0;
-        if (i < n)
-            for (int q = ops.s_ptr[i] + lane; q < ops.s_ptr[i + 1]; q += 32) {
+        float s = 0.f;
+        if (i < n) {
+            const int q1 = ops.s_ptr[i + 1];
+#pragma unroll 4
+            for (int q = ops.s_ptr[i] + lane; q < q1; q += 32) {
                 const int j = ops.s_col[q];
-                s = __fma_rn(ops.s_val[q], (double)din[(size_t)j * np + j], s);
+                s = __fmaf_rn(ops.s_val32[q], din[(size_t)j * np + j], s);
             }
-        s = warp_sum_d(s);
+        }
+        s = warp_sum_f(s);
         if (lane == 0) {
-            double gi = 0.0;
+            float gi = 0.f;
             if (i < n) {
-                const double pi = (double)din[(size_t)i * np + i];
-                const double dterm = (ops.dangling == QPR_DANGLING_F)
-                                         ? __dmul_rn(__dsub_rn(Dd, ops.dang[i] ? pi : 0.0), inv_nm1)
-                                         : __ddiv_rn(Dd, (double)n);
-                gi = __fma_rn(ops.alpha, __dadd_rn(s, dterm),
-                              __dmul_rn(__dmul_rn(__dsub_rn(1.0, ops.alpha), __dsub_rn(P, pi)), inv_nm1));
+                const float pi = din[(size_t)i * np + i];
+                const float dterm = (ops.dangling == QPR_DANGLING_F)
+                                        ? __fmul_rn(__fsub_rn(Dd, ops.dang[i] ? pi : 0.f), ops.inv_nm1_32)
+                                        : __fmul_rn(Dd, ops.inv_n32);
+                gi = __fmaf_rn(ops.alpha32, __fadd_rn(s, dterm),
+                               __fmul_rn(__fmul_rn(ops.oma32, __fsub_rn(P, pi)), ops.inv_nm1_32));
             }
-            out[i - out_base] = (float)gi;
+            out[i - out_base] = gi;
         }
     }
 }
 
 // Stop decision of stage 2 from the stage-1 residual partials (an
 // FP32-accurate estimate of ||f(y_n)||_F; a pass is confirmed by an exact
-// FP64 refresh on the host side of the loop). Every CTA computes the same
-// decision; the one with `first` records it. A step index whose exact
-// residual a refresh already judged is not judged again. Returns true when
-// the run stops (uniform over the CTA).
+// FP64 refresh on the host side of the loop). Every CTA sums the partials in
+// the same order and reaches the same decision; the one with `first`
+// records it. A step index whose exact residual a refresh already judged is
+// not judged again. Returns true when the run stops (uniform over the CTA).
 __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
-    __shared__ double red[32];
+    __shared__ float red[32];
+    __shared__ int s_status;
     Ctl *ctl = w.ctl;
     if (ctl->resid_exact_step == ctl->step) return false;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s += w.partials[i];
-    s = block_sum_d(s, red);
-    const double r = sqrt(s);
-    int status = kCtlRunning;
-    if (!isfinite(r)) status = kCtlNonFinite;
-    else if (r < ctl->tol) status = kCtlCandidate;
-    else if (ctl->step >= ctl->max_steps) status = kCtlMaxSteps;
-    __syncthreads();  // every thread has read ctl before it may change
-    if (first && threadIdx.x == 0) {
-        ctl->resid = r;
-        ctl->resid_step = ctl->step;
-        if (status != kCtlRunning) {
-            ctl->status = status;
-            ctl->done = 1;
+    float s = 0.f;
+    for (int i = threadIdx.x; i < w.nstage_partials; i += blockDim.x) s = __fadd_rn(s, w.partials32[i]);
+    s = block_sum_f(s, red);
+    if (threadIdx.x == 0) {
+        const double r = sqrt((double)s);  // one thread: the FP64 here is negligible
+        int status = kCtlRunning;
+        if (!isfinite(r)) status = kCtlNonFinite;
+        else if (r < ctl->tol) status = kCtlCandidate;
+        else if (ctl->step >= ctl->max_steps) status = kCtlMaxSteps;
+        s_status = status;
+        if (first) {
+            ctl->resid = r;
+            ctl->resid_step = ctl->step;
+            if (status != kCtlRunning) {
+                ctl->status = status;
+                ctl->done = 1;
+            }
         }
     }
-    return status != kCtlRunning;
+    __syncthreads();
+    return s_status != kCtlRunning;
 }
 
 // One tile pair (I, J) of stage STAGE of the sparse mixed form; pidx is the
@@ -290,13 +348,11 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
                                                   bool first, uint8_t *dyn) {
     __shared__ __align__(16) float sX1[TS * LDX];
     __shared__ __align__(16) float sX2[TS * LDX];
-    // outputs of tile (I, J) kept for the mirrored write: stages 1-3 keep S and
-    // the next delta (4 FP32 planes), stage 4 the new y (2 FP64 planes) and D
-    // (2 FP32 planes); 25.3 KB either way, in the dynamic buffer
-    double *sOraw = reinterpret_cast<double *>(dyn);
-    double *sO64 = sOraw;
-    float *sO32 = (STAGE == 4) ? reinterpret_cast<float *>(sOraw + 2 * TS * LDO) : reinterpret_cast<float *>(sOraw);
-    __shared__ double red[NT / 32];
+    // outputs of tile (I, J) kept for the mirrored write, 4 FP32 planes in the
+    // dynamic buffer: stages 1-3 S and the next delta, stage 4 the new delta
+    // (high parts, then low parts)
+    float *sO32 = reinterpret_cast<float *>(dyn);
+    __shared__ float red[NT / 32];
     __shared__ float sg[TS];
     const bool diag = (I == J);
     if (STAGE == 2 && stage2_decide(w, first)) return;
@@ -314,10 +370,8 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
     }
     const float *X2 = diag ? sX1 : sX2;
 
-    const float om = (float)ops.omega, cm = 1.0f - om;
-    const double dt = w.ctl->dt;
-    const double dt6 = __ddiv_rn(dt, 6.0);  // once per tile: FP64 division is slow on this part
-    const float dtf = (float)dt;
+    const float om = ops.omega32, cm = __fsub_rn(1.0f, om);
+    const float dtf = w.ctl->dtf, dt6h = w.ctl->dt6h, dt6l = w.ctl->dt6l;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float nrm = 0.f;  // this thread's share of ||k1||^2 (an FP32-accurate estimate)
 #pragma unroll
@@ -350,26 +404,27 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
             sO32[2 * TS * LDO + a * LDO + b] = nr;
             sO32[3 * TS * LDO + a * LDO + b] = ni;
         } else {
-            const double sr = (double)__fadd_rn(w.S[off], kdr), si = (double)__fadd_rn(w.S[plane + off], kdi);
-            const double yr = __fma_rn(dt6, sr, __fma_rn(dt, w.F[off], w.y[off]));
-            const double yi = __fma_rn(dt6, si, __fma_rn(dt, w.F[plane + off], w.y[plane + off]));
-            const float Dr = (float)__dsub_rn(yr, w.R[off]), Di = (float)__dsub_rn(yi, w.R[plane + off]);
-            w.y[off] = yr; w.y[plane + off] = yi;
-            w.D[off] = Dr; w.D[plane + off] = Di;
-            sO64[0 * TS * LDO + a * LDO + b] = yr;
-            sO64[1 * TS * LDO + a * LDO + b] = yi;
-            sO32[0 * TS * LDO + a * LDO + b] = Dr;
-            sO32[1 * TS * LDO + a * LDO + b] = Di;
+            // delta += dt F + dt/6 (S + kd4) in float-float
+            const float sr = __fadd_rn(w.S[off], kdr), si = __fadd_rn(w.S[plane + off], kdi);
+            const ff vr = delta_update(w.D[off], w.Dlo[off], w.Ghi[off], w.Glo[off], dt6h, dt6l, sr);
+            const ff vi = delta_update(w.D[plane + off], w.Dlo[plane + off], w.Ghi[plane + off], w.Glo[plane + off],
+                                       dt6h, dt6l, si);
+            w.D[off] = vr.hi; w.D[plane + off] = vi.hi;
+            w.Dlo[off] = vr.lo; w.Dlo[plane + off] = vi.lo;
+            sO32[0 * TS * LDO + a * LDO + b] = vr.hi;
+            sO32[1 * TS * LDO + a * LDO + b] = vi.hi;
+            sO32[2 * TS * LDO + a * LDO + b] = vr.lo;
+            sO32[3 * TS * LDO + a * LDO + b] = vi.lo;
         }
     }
     if (STAGE == 1) {
-        const double nrm_d = warp_sum_d((double)nrm);
-        if (lane == 0) red[warp] = nrm_d;
+        const float nrm_w = warp_sum_f(nrm);
+        if (lane == 0) red[warp] = nrm_w;
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int q = 0; q < NT / 32; ++q) s += red[q];
-            w.partials[pidx] = diag ? s : 2.0 * s;
+            float s = 0.f;
+            for (int q = 0; q < NT / 32; ++q) s = __fadd_rn(s, red[q]);
+            w.partials32[pidx] = diag ? s : __fmul_rn(2.0f, s);
         }
     }
     if (!diag) {
@@ -383,10 +438,10 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
                 dnext[off] = sO32[2 * TS * LDO + a * LDO + b];
                 dnext[plane + off] = -sO32[3 * TS * LDO + a * LDO + b];
             } else {
-                w.y[off] = sO64[0 * TS * LDO + a * LDO + b];
-                w.y[plane + off] = -sO64[1 * TS * LDO + a * LDO + b];
                 w.D[off] = sO32[0 * TS * LDO + a * LDO + b];
                 w.D[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
+                w.Dlo[off] = sO32[2 * TS * LDO + a * LDO + b];
+                w.Dlo[plane + off] = -sO32[3 * TS * LDO + a * LDO + b];
             }
         }
     }
@@ -405,33 +460,43 @@ __device__ __forceinline__ void gain_mixed_body(const DevOps &ops, const MixedWo
     gain_rows(ops, din, blk * wpb, nblk * wpb, ops.np, 0, w.g);
 }
 
-// Refresh, part 1: sigma = 1 / Re tr(y) (one CTA).
+// Refresh, part 1 (one CTA): sigma = 1 / Re tr(y) for y = R + delta, in
+// FP64, and the FP32 forms of dt that the delta stages use.
+__device__ __forceinline__ double state_value(const MixedWork &w, size_t i) {
+    // (double)hi + (double)lo is exact: the pair spans at most 48 bits
+    return w.R[i] + ((double)w.D[i] + (double)w.Dlo[i]);
+}
+
 __device__ __forceinline__ void refresh_trace_body(const DevOps &ops, const MixedWork &w) {
     __shared__ double red[32];
     double P = 0.0;
-    for (int j = threadIdx.x; j < ops.n; j += blockDim.x) P += w.y[(size_t)j * ops.np + j];
+    for (int j = threadIdx.x; j < ops.n; j += blockDim.x) P += state_value(w, (size_t)j * ops.np + j);
     P = block_sum_d(P, red);
     if (threadIdx.x == 0) {
-        w.ctl->trace = P;
-        w.ctl->scale = 1.0 / P;
+        Ctl *ctl = w.ctl;
+        ctl->trace = P;
+        ctl->scale = 1.0 / P;
         if (!(P > 0.0) || !isfinite(P)) {
-            w.ctl->status = kCtlNonFinite;
-            w.ctl->done = 1;
+            ctl->status = kCtlNonFinite;
+            ctl->done = 1;
         }
+        const double dt6 = ctl->dt / 6.0;
+        ctl->dtf = (float)ctl->dt;
+        ctl->dt6h = (float)dt6;
+        ctl->dt6l = (float)(dt6 - (double)ctl->dt6h);
     }
 }
 
-// Refresh, part 2: R = y = sigma y, D = 0 (and its BF16 split, dense
-// backend); elements i0, i0 + stride, ...
+// Refresh, part 2: R = sigma (R + delta), delta = 0 (and the BF16 split of
+// D, dense backend); elements i0, i0 + stride, ...
 __device__ __forceinline__ void refresh_normalize_body(const DevOps &ops, const MixedWork &w, size_t i0,
                                                        size_t stride) {
     const double sig = w.ctl->scale;
     const size_t tot = 2 * (size_t)ops.np * ops.np;
     for (size_t i = i0; i < tot; i += stride) {
-        const double v = sig * w.y[i];
-        w.y[i] = v;
-        w.R[i] = v;
+        w.R[i] = sig * state_value(w, i);
         w.D[i] = 0.0f;
+        w.Dlo[i] = 0.0f;
     }
     if (w.splitD) {
         const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
@@ -439,14 +504,23 @@ __device__ __forceinline__ void refresh_normalize_body(const DevOps &ops, const 
     }
 }
 
-// Refresh, part 4 (after F = f(R) in FP64): F32 = F; the CTA with first set
-// reduces the exact residual ||F||_F and takes the stop decision.
+// Refresh, part 4 (after F = f(R) in FP64): F32 = fl(F) and dt F as the
+// float-float pair (Ghi, Glo); the CTA with first set reduces the exact
+// residual ||F||_F and takes the stop decision.
 __device__ __forceinline__ void refresh_post_body(const DevOps &ops, const MixedWork &w, size_t i0, size_t stride,
                                                   bool first) {
     __shared__ double red[32];
     Ctl *ctl = w.ctl;
     const size_t tot = 2 * (size_t)ops.np * ops.np;
-    for (size_t i = i0; i < tot; i += stride) w.F32[i] = (float)w.F[i];
+    const double dt = ctl->dt;
+    for (size_t i = i0; i < tot; i += stride) {
+        const double f = w.F[i];
+        const double g = dt * f;
+        const float gh = (float)g;
+        w.F32[i] = (float)f;
+        w.Ghi[i] = gh;
+        w.Glo[i] = (float)(g - (double)gh);
+    }
     if (first) {
         double s = 0.0;
         for (int i = threadIdx.x; i < w.npairs; i += blockDim.x) s += w.partials[i];

@@ -39,8 +39,8 @@ struct qpr_ctx {
     // device work
     double *d_state = nullptr;  // y, z, ya, yb: 2 planes each
     double *d_mix64 = nullptr;  // mixed form: R, F (2 planes each)
-    float *d_mix32 = nullptr;   // mixed form: F32, D, da, db, S (2 planes each)
-    float *d_g32 = nullptr, *d_hval32 = nullptr, *d_c32 = nullptr;
+    float *d_mix32 = nullptr;   // mixed form: F32, D, Dlo, da, db, S, Ghi, Glo (2 planes each)
+    float *d_g32 = nullptr, *d_hval32 = nullptr, *d_c32 = nullptr, *d_sval32 = nullptr, *d_partials32 = nullptr;
     __nv_bfloat16 *d_hsplit = nullptr;  // dense mixed form: H split into 3 BF16 planes
     __nv_bfloat16 *d_dsplit = nullptr;  // dense mixed form: 3 delta-split buffers of 6 planes
     int2 *d_pairs_tc = nullptr;
@@ -161,6 +161,17 @@ qpr_status import_rho(qpr_ctx *ctx, const void *rho, double *planes) {
     }
     qpr::launch_import(src, (int)ctx->n, ctx->np, planes, ctx->stream);
     ctx->launches += 1;
+    return QPR_OK;
+}
+
+// The solver's starting state: y (FP64 form) or R with a zero delta (mixed
+// form, whose first refresh normalises R + delta).
+qpr_status import_state(qpr_ctx *ctx, const void *rho) {
+    if (ctx->opt.precision != QPR_MIXED) return import_rho(ctx, rho, ctx->work.y);
+    qpr_status st = import_rho(ctx, rho, ctx->mw.R);
+    if (st != QPR_OK) return st;
+    const size_t plane = (size_t)ctx->np * ctx->np;
+    QPR_CUDA(ctx, cudaMemsetAsync(ctx->mw.D, 0, 4 * plane * sizeof(float), ctx->stream));
     return QPR_OK;
 }
 
@@ -524,6 +535,8 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_mix64);
     cudaFree(ctx->d_mix32);
     cudaFree(ctx->d_g32);
+    cudaFree(ctx->d_sval32);
+    cudaFree(ctx->d_partials32);
     cudaFree(ctx->d_hval32);
     cudaFree(ctx->d_c32);
     cudaFree(ctx->d_hsplit);
@@ -728,9 +741,14 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     if (o.precision == QPR_MIXED) {
         CREATE_CUDA(cudaMalloc(&ctx->d_mix64, 4 * plane * sizeof(double)));
         CREATE_CUDA(cudaMemset(ctx->d_mix64, 0, 4 * plane * sizeof(double)));
-        CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 10 * plane * sizeof(float)));
-        CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 10 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 16 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 16 * plane * sizeof(float)));
         CREATE_CUDA(cudaMalloc(&ctx->d_g32, np * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_partials32, std::max<size_t>(pairs.size(), (size_t)npairs_tc) * sizeof(float)));
+        std::vector<float> sv32(std::max<size_t>(1, sval.size()));
+        for (size_t q = 0; q < sval.size(); ++q) sv32[q] = (float)sval[q];
+        CREATE_CUDA(cudaMalloc(&ctx->d_sval32, sv32.size() * sizeof(float)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_sval32, sv32.data(), sv32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     CREATE_CUDA(cudaMalloc(&ctx->d_ctl, sizeof(Ctl)));
     CREATE_CUDA(cudaMemset(ctx->d_ctl, 0, sizeof(Ctl)));
@@ -758,6 +776,12 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     ops.c = ctx->d_c;
     ops.c32 = ctx->d_c32;
     ops.h_val32 = ctx->d_hval32;
+    ops.s_val32 = ctx->d_sval32;
+    ops.alpha32 = (float)alpha;
+    ops.oma32 = (float)(1.0 - alpha);
+    ops.omega32 = (float)omega;
+    ops.inv_nm1_32 = (float)(1.0 / (double)(n - 1));
+    ops.inv_n32 = (float)(1.0 / (double)n);
     ops.rowseg = ctx->d_rowseg;
     ops.seg = ctx->d_seg;
     qpr::Work &wk = ctx->work;
@@ -773,14 +797,17 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     wk.ctl = ctx->d_ctl;
     if (o.precision == QPR_MIXED) {
         qpr::MixedWork &mw = ctx->mw;
-        mw.y = wk.y;
         mw.R = ctx->d_mix64;
         mw.F = ctx->d_mix64 + 2 * plane;
         mw.F32 = ctx->d_mix32;
-        mw.D = ctx->d_mix32 + 2 * plane;
-        mw.da = ctx->d_mix32 + 4 * plane;
-        mw.db = ctx->d_mix32 + 6 * plane;
-        mw.S = ctx->d_mix32 + 8 * plane;
+        mw.D = ctx->d_mix32 + 2 * plane;  // D and Dlo adjacent: one memset clears the delta
+        mw.Dlo = ctx->d_mix32 + 4 * plane;
+        mw.da = ctx->d_mix32 + 6 * plane;
+        mw.db = ctx->d_mix32 + 8 * plane;
+        mw.S = ctx->d_mix32 + 10 * plane;
+        mw.Ghi = ctx->d_mix32 + 12 * plane;
+        mw.Glo = ctx->d_mix32 + 14 * plane;
+        mw.partials32 = ctx->d_partials32;
         mw.g = ctx->d_g32;
         mw.g64 = ctx->d_g;
         mw.partials = ctx->d_partials;
@@ -876,7 +903,7 @@ qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps) {
     if (dt > qpr_max_stable_dt(ctx))
         return fail(ctx, QPR_E_UNSTABLE, "dt exceeds the RK4 stability estimate " +
                                              std::to_string(qpr_max_stable_dt(ctx)));
-    st = import_rho(ctx, rho, ctx->work.y);
+    st = import_state(ctx, rho);
     if (st != QPR_OK) return st;
     const bool mixed = ctx->opt.precision == QPR_MIXED;
     st = mixed ? run_mixed(ctx, dt, 0.0, steps) : run_rk4(ctx, dt, 0.0, steps);
@@ -903,7 +930,7 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
     int64_t m = 1;
     if (dt > dmax) m = (int64_t)ceil(dt / dmax);
     const double h = dt / (double)m;
-    st = import_rho(ctx, rho, ctx->work.y);
+    st = import_state(ctx, rho);
     if (st != QPR_OK) return st;
     const bool mixed = ctx->opt.precision == QPR_MIXED;
     st = mixed ? run_mixed(ctx, h, tol, max_steps) : run_rk4(ctx, h, tol, max_steps);
@@ -938,7 +965,7 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     if (st != QPR_OK) return st;
     if (!rho || !ms_out || steps < 1) return fail(ctx, QPR_E_ARG, "rho/ms_out NULL or steps < 1");
     if (!(dt > 0.0) || dt > qpr_max_stable_dt(ctx)) return fail(ctx, QPR_E_ARG, "dt not positive or unstable");
-    st = import_rho(ctx, rho, ctx->work.y);
+    st = import_state(ctx, rho);
     if (st != QPR_OK) return st;
     Ctl *h = ctx->h_ctl;
     memset(h, 0, sizeof(Ctl));

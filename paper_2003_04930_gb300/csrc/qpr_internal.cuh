@@ -32,6 +32,9 @@ struct Ctl {
     long long resid_exact_step;
     int err_timeout;    // a bounded device-side wait gave up
     int pad_;
+    // FP32 forms of dt for the mixed form's delta stages, written by its
+    // refresh: dtf = fl(dt) and dt / 6 = dt6h + dt6l as a float-float pair
+    float dtf, dt6h, dt6l, pad2_;
 };
 
 // kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
@@ -60,6 +63,10 @@ struct DevOps {
     const unsigned char *dang;  // n flags: column j has no out-links
     const double *c;      // np column sums of G (0 on padding)
     const float *c32;     // the same in FP32 (mixed form)
+    // FP32 copies for the mixed form's delta stages (no FP64 instruction in
+    // a delta stage): S values, alpha, 1 - alpha, omega, 1 / (n - 1), 1 / n
+    const float *s_val32;
+    float alpha32, oma32, omega32, inv_nm1_32, inv_n32;
 };
 
 // RK4 work buffers. Every state buffer holds two np x np FP64 planes,
@@ -76,17 +83,20 @@ struct Work {
     Ctl *ctl;
 };
 
-// Buffers of the mixed-precision form (stage_mixed.cu). FP64: y (shared
-// with Work), the reference R = y / tr(y) of the last refresh and F = f(R).
-// FP32 (two np x np planes each): F32 = F, D = y - R, the stage deltas da/db
-// and the RK4 sum S.
+// Buffers of the mixed-precision form (stage_mixed.cu). The state is
+// y = R + delta: FP64 R = y / tr(y) at the last refresh and F = f(R); the
+// delta since that refresh as a float-float pair of FP32 planes, D (high
+// part, the FP32 delta the stages read) and Dlo (low part). FP32 (two np x np
+// planes each): F32 = fl(F), dt F = Ghi + Glo (float-float), the stage
+// deltas da/db and the RK4 sum S.
 struct TcMaps;
 struct MixedWork {
-    double *y, *R, *F;
-    float *F32, *D, *da, *db, *S;
+    double *R, *F;
+    float *F32, *D, *Dlo, *da, *db, *S, *Ghi, *Glo;
     float *g;             // gain of the stage delta, np
     double *g64;          // FP64 gain used by the refresh, np
-    double *partials;
+    double *partials;     // exact residual partials of the refresh
+    float *partials32;    // residual-estimate partials of the stage-1 kernel
     int2 *pairs;          // 32 x 32 tile pairs (refresh and sparse stage kernel)
     int npairs;
     int tiles;

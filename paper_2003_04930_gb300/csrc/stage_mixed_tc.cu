@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 #include <math.h>
 
+#include "mixed_body.cuh"
 #include "qpr_internal.cuh"
 
 namespace qpr {
@@ -161,12 +162,6 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *sp, size_t plane, int g
     }
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <int STAGE>
 __global__ void __launch_bounds__(NTHREADS, 1)
 stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorMap tmH,
@@ -175,7 +170,7 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
     __shared__ uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], accum_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int s_done, s_fail;
-    __shared__ double red[NTHREADS / 32];
+    __shared__ float red[NTHREADS / 32];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
     Ctl *ctl = w.ctl;
@@ -291,14 +286,13 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
         }
         __syncthreads();
 
-        const float om = (float)ops.omega, cm = 1.0f - om;
-        const double dt = ctl->dt;
-        const float dtf = (float)dt;
+        const float om = ops.omega32, cm = 1.0f - om;
+        const float dtf = ctl->dtf, dt6h = ctl->dt6h, dt6l = ctl->dt6l;
         const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
         float *dnext = (STAGE == 2) ? w.db : w.da;
         __nv_bfloat16 *snext = (STAGE == 2) ? w.splitB : (STAGE == 4 ? w.splitD : w.splitA);
         const int a = row, ga = I * TB + a;
-        double nrm = 0.0;
+        float nrm = 0.f;
         for (int c = 0; c < 64; c += 32) {
             const int b0 = h * 64 + c;
             float xa[32], xb[32];
@@ -318,7 +312,7 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
                 const size_t moff = (size_t)gb * np + ga;
                 if (STAGE <= 3) {
                     const float kr = kdr + w.F32[off], ki = kdi + w.F32[plane + off];
-                    if (STAGE == 1) nrm += (double)kr * kr + (double)ki * ki;
+                    if (STAGE == 1) nrm += kr * kr + ki * ki;
                     const float Dr = w.D[off], Di = w.D[plane + off];
                     float sr, si;
                     if (STAGE == 1) { sr = kdr; si = kdi; }
@@ -333,31 +327,33 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
                     }
                     put_split(snext, plane, ga, gb, np, nr, ni, !diag);
                 } else {
-                    const double sr = (double)(w.S[off] + kdr), si = (double)(w.S[plane + off] + kdi);
-                    const double yr = w.y[off] + dt * w.F[off] + (dt / 6.0) * sr;
-                    const double yi = w.y[plane + off] + dt * w.F[plane + off] + (dt / 6.0) * si;
-                    const float Dr = (float)(yr - w.R[off]), Di = (float)(yi - w.R[plane + off]);
-                    w.y[off] = yr; w.y[plane + off] = yi;
-                    w.D[off] = Dr; w.D[plane + off] = Di;
+                    // delta += dt F + dt/6 (S + kd4) in float-float
+                    const float sr = w.S[off] + kdr, si = w.S[plane + off] + kdi;
+                    const mixed::ff vr =
+                        mixed::delta_update(w.D[off], w.Dlo[off], w.Ghi[off], w.Glo[off], dt6h, dt6l, sr);
+                    const mixed::ff vi = mixed::delta_update(w.D[plane + off], w.Dlo[plane + off], w.Ghi[plane + off],
+                                                             w.Glo[plane + off], dt6h, dt6l, si);
+                    w.D[off] = vr.hi; w.D[plane + off] = vi.hi;
+                    w.Dlo[off] = vr.lo; w.Dlo[plane + off] = vi.lo;
                     if (!diag) {
-                        w.y[moff] = yr; w.y[plane + moff] = -yi;
-                        w.D[moff] = Dr; w.D[plane + moff] = -Di;
+                        w.D[moff] = vr.hi; w.D[plane + moff] = -vi.hi;
+                        w.Dlo[moff] = vr.lo; w.Dlo[plane + moff] = -vi.lo;
                     }
-                    put_split(snext, plane, ga, gb, np, Dr, Di, !diag);
+                    put_split(snext, plane, ga, gb, np, vr.hi, vi.hi, !diag);
                 }
             }
         }
         if (STAGE == 1) {
-            nrm = warp_sum_d(nrm);
+            nrm = mixed::warp_sum_f(nrm);
             if (lane == 0) red[warp] = nrm;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (STAGE == 1 && tid == 0 && ok_acc && !s_fail) {
-        double s = 0.0;
+        float s = 0.f;
         for (int i = 0; i < NTHREADS / 32; ++i) s += red[i];
-        w.partials[blockIdx.x] = diag ? s : 2.0 * s;
+        w.partials32[blockIdx.x] = diag ? s : 2.0f * s;
     }
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
