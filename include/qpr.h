@@ -68,8 +68,10 @@ typedef enum {
  *   ref_refresh steps the state is renormalised, R = y / tr(y), and F = f(R)
  *   is evaluated exactly in FP64, which also gives the exact residual ||F||_F.
  *   In between, each stage evaluates only f(Y_s - R) (f is linear) in FP32
- *   (or split BF16 on tensor cores for the dense backend), and FP64 is kept
- *   for the RK accumulation into rho. A residual that passes the FP32-accurate
+ *   (or split BF16 on tensor cores for the dense backend), and the RK
+ *   accumulation of the delta y - R is carried in float-float (two FP32
+ *   planes, about 48 bits); y = R + delta is formed in FP64 at each refresh.
+ *   A residual that passes the FP32-accurate
  *   per-step estimate is confirmed by an exact FP64 refresh before the solve
  *   stops, so the returned state satisfies the FP64 stop rule. */
 enum { QPR_FP64 = 0, QPR_MIXED = 1 };
@@ -87,6 +89,15 @@ enum { QPR_DANGLING_F = 0, QPR_DANGLING_UNIFORM = 1 };
  * N^2 / 8 nonzeros. Both produce the same FP64 right-hand side up to
  * summation order. */
 enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
+/* Form of the FP32 stage of QPR_MIXED with the sparse backend.
+ * COLUMNS: per stage a column-block product X = H (Y_s - R), each CTA
+ *   staging 8 complex columns of the delta in shared memory with TMA, then a
+ *   tile-pair epilogue (2 launches per stage); for N padded to 32 <= 1536.
+ * TILES: one launch per stage; each 32 x 32 tile pair gathers, from L2, the
+ *   row slices of the delta that its rows' nonzeros select.
+ * AUTO (default): COLUMNS where it applies, else TILES. The two forms differ
+ * only in FP32 summation order. */
+enum { QPR_SPARSE_FORM_AUTO = 0, QPR_SPARSE_FORM_COLUMNS = 1, QPR_SPARSE_FORM_TILES = 2 };
 
 typedef struct {
     int32_t precision;   /* QPR_FP64 (default) or QPR_MIXED */
@@ -97,7 +108,8 @@ typedef struct {
     int32_t device;      /* CUDA device ordinal (default -1: the current device) */
     int32_t backend;     /* QPR_BACKEND_AUTO (default), QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE */
     int32_t ref_refresh; /* QPR_MIXED: steps between exact FP64 reference refreshes (default 32) */
-    int32_t reserved[5];
+    int32_t sparse_form; /* QPR_MIXED, sparse backend: QPR_SPARSE_FORM_* (default AUTO) */
+    int32_t reserved[4];
 } qpr_options;
 
 typedef struct {

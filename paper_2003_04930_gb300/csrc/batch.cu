@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "cols_body.cuh"
 #include "gain_body.cuh"
 #include "mixed_body.cuh"
 #include "qpr_internal.cuh"
@@ -115,6 +116,72 @@ __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGrap
     }
 }
 
+// Column-block form: the SpMM over (problem, J, split) items. The column
+// block, the split's CSR entries and bundles are staged with plain loads
+// (each problem has its own layout); the arithmetic is the single-problem
+// form's (warp_bundles, cta_gain), so the results are bitwise the same.
+template <int STAGE>
+__global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
+                                                                 int nitems) {
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 t = items[it];
+        load_graph(gs, t.x, sg);
+        if (!graph_done(sg, &s_flag)) {
+            const DevOps &ops = sg.ops;
+            const int J = t.y, r = t.z, np = ops.np;
+            const size_t plane = (size_t)np * np;
+            float *sD = reinterpret_cast<float *>(dyn_smem);
+            int2 *sKH = reinterpret_cast<int2 *>(dyn_smem + (size_t)np * cols::kRowFloats * 4);
+            int4 *sP = reinterpret_cast<int4 *>(dyn_smem + ops.col_p_off);
+            const float *din = cols::stage_input<STAGE>(sg.mw);
+            const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
+            const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
+            for (int u = threadIdx.x; u < np * 8; u += blockDim.x) {
+                const int k = u >> 3, part = u & 7;  // parts 0..3: real quads, 4..7: imaginary quads
+                const float4 v = *reinterpret_cast<const float4 *>(din + (part < 4 ? 0 : plane) + (size_t)k * np +
+                                                                   J * cols::kCW + 4 * (part & 3));
+                *reinterpret_cast<float4 *>(sD + k * cols::kRowFloats + 4 * part) = v;
+            }
+            for (int u = threadIdx.x; u < q_end - q_base; u += blockDim.x) sKH[u] = ops.col_kh[q_base + u];
+            for (int u = threadIdx.x; u < 4 * (p_end - p_base); u += blockDim.x)
+                sP[u] = ops.col_pieces[4 * (size_t)p_base + u];
+            const int ncb = np / cols::kCW;
+            cols::cta_gain(ops, sg.mw, din, r * ncb + J, ncb * ops.col_splits);
+            __syncthreads();
+            const int warp = threadIdx.x >> 5;
+            cols::warp_bundles(sD, sKH, sP, q_base, p_base, ops.col_wb[r * cols::kAWarps + warp],
+                               ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X);
+        }
+        __syncthreads();
+    }
+}
+
+// Column-block form: the epilogue over (problem, I, J, pair) items.
+template <int STAGE>
+__global__ void __launch_bounds__(mixed::NT) b_cols_epi_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+    __shared__ __align__(16) float sX1[mixed::TS * mixed::LDX];
+    __shared__ __align__(16) float sX2[mixed::TS * mixed::LDX];
+    __shared__ __align__(16) float sO[4 * mixed::TS * mixed::LDO];
+    __shared__ float sg32[mixed::TS];
+    __shared__ BatchGraph sg;
+    __shared__ int s_flag;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 t = items[it];
+        load_graph(gs, t.x, sg);
+        if (!graph_done(sg, &s_flag))
+            cols::epilogue_pair<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0, sg.mw.npairs, sX1, sX2, sg32, sO);
+        __syncthreads();
+    }
+}
+
+template <int STAGE>
+cudaError_t set_bcols_attr(int bytes) {
+    return cudaFuncSetAttribute(b_cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 template <int STAGE>
 cudaError_t set_b_attr() {
     return cudaFuncSetAttribute(b_stage_mixed_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -125,6 +192,11 @@ struct Lists {
     int *act;      // device, active problem indices
     int4 *items;   // device, (problem, I, J, pair index) of the active problems
     int nact, nitems;
+    // per stage: column-block SpMM items (problem, J, split), the pairs of
+    // the column-form problems and the pairs of the tile-form problems
+    int4 *items_a, *items_b, *items_t;
+    int na, nb, nt;
+    int smem_a;    // dynamic shared memory of the SpMM kernel
 };
 
 int elem_chunks(int np) {
@@ -145,14 +217,25 @@ void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream
     launches += 5;
 }
 
+template <int STAGE>
+void launch_stage_b(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
+    if (L.na) {
+        b_cols_spmm_kernel<STAGE><<<std::min(L.na, 152 * 2), cols::kANT, L.smem_a, s>>>(gs, L.items_a, L.na);
+        b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 6), mixed::NT, 0, s>>>(gs, L.items_b, L.nb);
+        launches += 2;
+    }
+    if (L.nt) {
+        b_stage_mixed_kernel<STAGE><<<std::min(L.nt, 152 * 3), kStageNT, mixed::kMixedDynSmem, s>>>(gs, L.items_t,
+                                                                                                 L.nt);
+        launches += 1;
+    }
+}
+
 void launch_step(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
-    const int grid = std::min(L.nitems, 152 * 3);
-    const int dsm = mixed::kMixedDynSmem;
-    b_stage_mixed_kernel<1><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<2><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<3><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
-    b_stage_mixed_kernel<4><<<grid, kStageNT, dsm, s>>>(gs, L.items, L.nitems);
-    launches += 4;
+    launch_stage_b<1>(gs, L, s, launches);
+    launch_stage_b<2>(gs, L, s, launches);
+    launch_stage_b<3>(gs, L, s, launches);
+    launch_stage_b<4>(gs, L, s, launches);
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -202,6 +285,14 @@ cudaError_t init_batch() {
     if (e == cudaSuccess) e = set_b_attr<3>();
     if (e == cudaSuccess) e = set_b_attr<4>();
     if (e == cudaSuccess) e = init_stage_mixed();
+    return e;
+}
+
+cudaError_t set_bcols_smem(int bytes) {
+    cudaError_t e = set_bcols_attr<1>(bytes);
+    if (e == cudaSuccess) e = set_bcols_attr<2>(bytes);
+    if (e == cudaSuccess) e = set_bcols_attr<3>(bytes);
+    if (e == cudaSuccess) e = set_bcols_attr<4>(bytes);
     return e;
 }
 
@@ -298,6 +389,33 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         }
     } restore{prev_dev != dev ? prev_dev : -1};
 
+    // ---- column-block plans: the same decision as a single-problem solve ----
+    std::vector<qpr::ColPlan> plans(G);
+    std::vector<char> colg(G, 0);
+    std::vector<size_t> okh(G), oci(G), opc(G), oxc(G);
+    size_t nkh = 0, nci = 0, npc = 0, nxc = 0, na_max = 0;
+    int smem_a = 0;
+    for (size_t g = 0; g < G; ++g) {
+        if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g])) {
+            if (o.sparse_form == QPR_SPARSE_FORM_COLUMNS)
+                return err(QPR_E_ARG, "problem " + std::to_string(g) +
+                                          ": sparse_form COLUMNS does not fit one CTA's shared memory");
+            continue;
+        }
+        const qpr::ColPlan &pl = plans[g];
+        colg[g] = 1;
+        okh[g] = nkh;
+        nkh += pl.kh.size();
+        oci[g] = nci;
+        nci += pl.q.size() + pl.sb.size() + pl.wb.size();
+        opc[g] = npc;
+        npc += pl.pieces.size();
+        oxc[g] = nxc;
+        nxc += qpr::align_up(2 * (size_t)np[g] * np[g], 64);
+        na_max += (size_t)(np[g] / qpr::cols::kCW) * pl.splits;
+        smem_a = std::max(smem_a, pl.smem);
+    }
+
     qpr::BatchMem mem;
     double *dD = nullptr;
     float *dF = nullptr;
@@ -328,6 +446,32 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     BCUDA(mem.alloc(&dAct, G));
     BCUDA(mem.alloc(&dItems, total_pairs));
     BCUDA(mem.alloc(&dIO, 2 * max_nn));
+    int2 *dKH = nullptr;
+    int *dCI = nullptr;
+    int4 *dPC = nullptr, *dItemsA = nullptr, *dItemsB = nullptr, *dItemsT = nullptr;
+    float *dXC = nullptr;
+    BCUDA(mem.alloc(&dKH, nkh));
+    BCUDA(mem.alloc(&dCI, nci));
+    BCUDA(mem.alloc(&dPC, npc));
+    BCUDA(mem.alloc(&dXC, nxc));
+    BCUDA(mem.alloc(&dItemsA, na_max));
+    BCUDA(mem.alloc(&dItemsB, total_pairs));
+    BCUDA(mem.alloc(&dItemsT, total_pairs));
+    if (nxc) BCUDA(cudaMemset(dXC, 0, nxc * sizeof(float)));
+    if (smem_a > 0) {
+        BCUDA(qpr::set_bcols_smem(smem_a));
+    }
+    for (size_t g = 0; g < G; ++g) {
+        if (!colg[g]) continue;
+        const qpr::ColPlan &pl = plans[g];
+        std::vector<int> ints(pl.q);
+        ints.insert(ints.end(), pl.sb.begin(), pl.sb.end());
+        ints.insert(ints.end(), pl.wb.begin(), pl.wb.end());
+        BCUDA(cudaMemcpy(dKH + okh[g], pl.kh.data(), pl.kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        BCUDA(cudaMemcpy(dCI + oci[g], ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!pl.pieces.empty())
+            BCUDA(cudaMemcpy(dPC + opc[g], pl.pieces.data(), pl.pieces.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     BCUDA(cudaMemset(dD, 0, nd * sizeof(double)));
     BCUDA(cudaMemset(dF, 0, nf * sizeof(float)));
     BCUDA(cudaStreamCreateWithFlags(&mem.stream, cudaStreamNonBlocking));
@@ -403,6 +547,17 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         d.ops.dang = dB + ob[g];
         d.ops.c = c;
         d.ops.c32 = c32;
+        if (colg[g]) {
+            const qpr::ColPlan &pl = plans[g];
+            d.ops.col_kh = dKH + okh[g];
+            d.ops.col_q = dCI + oci[g];
+            d.ops.col_sb = dCI + oci[g] + pl.q.size();
+            d.ops.col_wb = dCI + oci[g] + pl.q.size() + pl.sb.size();
+            d.ops.col_pieces = dPC + opc[g];
+            d.ops.col_splits = pl.splits;
+            d.ops.col_smem = pl.smem;
+            d.ops.col_p_off = pl.p_off;
+        }
         d.ops.s_val32 = sv32;
         d.ops.alpha32 = (float)alpha;
         d.ops.oma32 = (float)(1.0 - alpha);
@@ -413,6 +568,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         mw.R = R; mw.F = F;
         mw.F32 = F32; mw.D = Dp; mw.Dlo = Dlo; mw.da = da; mw.db = db; mw.S = S; mw.Ghi = Ghi; mw.Glo = Glo;
         mw.g = g32; mw.g64 = g64; mw.partials = part; mw.partials32 = part32;
+        mw.X = colg[g] ? dXC + oxc[g] : nullptr;
         mw.pairs = nullptr; mw.npairs = npairs[g]; mw.tiles = T[g];
         mw.ctl = dCtl + g;
         mw.nstage_partials = npairs[g];
@@ -449,7 +605,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     // ---- blocks of (exact refresh + ref_refresh delta steps) ----
     std::vector<int> active(G);
     for (size_t g = 0; g < G; ++g) active[g] = (int)g;
-    std::vector<int4> items;
+    std::vector<int4> items, items_a, items_b, items_t;
     items.reserve(total_pairs);
     auto make_lists = [&](const std::vector<int> &list, qpr::Lists &L) -> cudaError_t {
         items.clear();
@@ -459,13 +615,34 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
                 for (int J = I + 1; J < T[g]; ++J) items.push_back(make_int4(g, I, J, q++));
             for (int I = 0; I < T[g]; ++I) items.push_back(make_int4(g, I, I, q++));
         }
+        items_a.clear();
+        items_b.clear();
+        items_t.clear();
+        for (const int4 &t : items) (colg[t.x] ? items_b : items_t).push_back(t);
+        for (int g : list)
+            if (colg[g])
+                for (int r = 0; r < plans[g].splits; ++r)
+                    for (int J = 0; J < np[g] / qpr::cols::kCW; ++J) items_a.push_back(make_int4(g, J, r, 0));
         L.act = dAct;
         L.items = dItems;
         L.nact = (int)list.size();
         L.nitems = (int)items.size();
+        L.items_a = dItemsA;
+        L.items_b = dItemsB;
+        L.items_t = dItemsT;
+        L.na = (int)items_a.size();
+        L.nb = (int)items_b.size();
+        L.nt = (int)items_t.size();
+        L.smem_a = smem_a;
         cudaError_t e = cudaMemcpyAsync(dAct, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dItems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !items_a.empty())
+            e = cudaMemcpyAsync(dItemsA, items_a.data(), items_a.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !items_b.empty())
+            e = cudaMemcpyAsync(dItemsB, items_b.data(), items_b.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !items_t.empty())
+            e = cudaMemcpyAsync(dItemsT, items_t.data(), items_t.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
         // the host vectors are reused: wait until both copies have read them
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e;

@@ -100,6 +100,39 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
 constexpr int kSegSlots = 96;      // segment partials held at once (24 KB)
 constexpr int kSegLen = 32;        // nonzeros per segment (one warp-wide load)
 
+// The gathers of one segment (len <= kSegLen nonzeros; lane e < len holds
+// column myk and value myh of nonzero e): 8-lane group grp takes nonzeros
+// grp, grp + 4, ..., each lane a float4 of the real and of the imaginary row
+// slice, and returns its partial sums (before the sum over the groups).
+// Batches of 16 nonzeros, branch-free inside a batch: slots past len load
+// the segment's first row with weight 0, so that the 8 loads of a batch are
+// all issued before its first FMA (one L2 round trip per batch, 32
+// registers of loads in flight).
+__device__ __forceinline__ void gather_segment(const float *__restrict__ re, const float *__restrict__ im, int np,
+                                               int myk, float myh, int len, int grp, float4 &xr, float4 &xi) {
+    constexpr int R = 4;  // rounds of 4 nonzeros per batch
+    const int k0 = __shfl_sync(0xffffffffu, myk, 0);
+    for (int e0 = 0; e0 < len; e0 += 4 * R) {  // warp-uniform
+        float4 vr[R], vi[R];
+#pragma unroll
+        for (int it = 0; it < R; ++it) {
+            const int e = e0 + it * 4 + grp;
+            int k = __shfl_sync(0xffffffffu, myk, e & 31);
+            k = (e < len) ? k : k0;
+            vr[it] = *reinterpret_cast<const float4 *>(re + (size_t)k * np);
+            vi[it] = *reinterpret_cast<const float4 *>(im + (size_t)k * np);
+        }
+#pragma unroll
+        for (int it = 0; it < R; ++it) {
+            const int e = e0 + it * 4 + grp;
+            float h = __shfl_sync(0xffffffffu, myh, e & 31);
+            h = (e < len) ? h : 0.f;
+            xr = f4fma(h, vr[it], xr);
+            xi = f4fma(h, vi[it], xi);
+        }
+    }
+}
+
 // sX[a][b] = (H Re d)_ab, sX[a][TS + b] = (H Im d)_ab for rows of tile rt and
 // columns of tile ct, in FP32. The nonzeros of every row are cut into
 // segments of at most kSegLen (ops.seg, rows' ranges in ops.rowseg); warps
@@ -130,16 +163,7 @@ __device__ __forceinline__ void spmm32_tile(const DevOps &ops, const float *__re
                 myh = ops.h_val32[sg.x + lane];
             }
             float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
-#pragma unroll
-            for (int it = 0; it < kSegLen / 4; ++it) {
-                const int e = it * 4 + grp;
-                const int k = __shfl_sync(0xffffffffu, myk, e);
-                const float h = __shfl_sync(0xffffffffu, myh, e);
-                if (e < len) {
-                    xr = f4fma(h, *reinterpret_cast<const float4 *>(re + (size_t)k * np), xr);
-                    xi = f4fma(h, *reinterpret_cast<const float4 *>(im + (size_t)k * np), xi);
-                }
-            }
+            gather_segment(re, im, np, myk, myh, len, grp, xr, xi);
             xr = f4xor(xr, 8);
             xr = f4xor(xr, 16);
             xi = f4xor(xi, 8);
@@ -226,16 +250,7 @@ __device__ __forceinline__ void spmm32_pair(const DevOps &ops, const float *__re
             myh = sval[sg.x + lane];
         }
         float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), xi = xr;
-#pragma unroll
-        for (int it = 0; it < kSegLen / 4; ++it) {
-            const int e = it * 4 + grp;
-            const int k = __shfl_sync(0xffffffffu, myk, e);
-            const float h = __shfl_sync(0xffffffffu, myh, e);
-            if (e < len) {
-                xr = f4fma(h, *reinterpret_cast<const float4 *>(re + (size_t)k * np), xr);
-                xi = f4fma(h, *reinterpret_cast<const float4 *>(im + (size_t)k * np), xi);
-            }
-        }
+        gather_segment(re, im, np, myk, myh, len, grp, xr, xi);
         xr = f4xor(xr, 8);
         xr = f4xor(xr, 16);
         xi = f4xor(xi, 8);
@@ -339,35 +354,21 @@ __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
     return s_status != kCtlRunning;
 }
 
-// One tile pair (I, J) of stage STAGE of the sparse mixed form; pidx is the
-// slot of its residual partial, first marks the pair that advances the step
-// counter. Ends with a barrier so that the caller may reuse shared memory.
-// dyn: kMixedDynSmem bytes of dynamic shared memory (16-byte aligned).
+// Epilogue of one tile pair (I, J) of stage STAGE from the products
+// sX1 = X_IJ and (unless I == J) sX2 = X_JI of X = H delta, [a][LDX] rows
+// (real part, then imaginary part), and, on a diagonal pair, the gain of
+// its rows in sg. Writes tile (I, J) and its conjugate mirror (J, I); stage
+// 1 leaves this pair's residual-estimate partial in partials32[pidx].
+// sO32: 4 * TS * LDO floats of shared memory. Ends with a barrier.
 template <int STAGE>
-__device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
-                                                  bool first, uint8_t *dyn) {
-    __shared__ __align__(16) float sX1[TS * LDX];
-    __shared__ __align__(16) float sX2[TS * LDX];
-    // outputs of tile (I, J) kept for the mirrored write, 4 FP32 planes in the
-    // dynamic buffer: stages 1-3 S and the next delta, stage 4 the new delta
-    // (high parts, then low parts)
-    float *sO32 = reinterpret_cast<float *>(dyn);
+__device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                              const float *sX1, const float *sX2, const float *sg, float *sO32) {
     __shared__ float red[NT / 32];
-    __shared__ float sg[TS];
     const bool diag = (I == J);
-    if (STAGE == 2 && stage2_decide(w, first)) return;
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
     float *dnext = (STAGE == 2) ? w.db : w.da;
-
-    spmm32_pair(ops, din, plane, I, J, diag, sX1, sX2, dyn);
-    // only diagonal tiles add the gain g = G p(delta); they compute it for
-    // their own rows
-    if (diag) {
-        gain_rows(ops, din, I * TS, NT / 32, I * TS + TS, I * TS, sg);
-        __syncthreads();
-    }
     const float *X2 = diag ? sX1 : sX2;
 
     const float om = ops.omega32, cm = __fsub_rn(1.0f, om);
@@ -445,7 +446,36 @@ __device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const Mixed
             }
         }
     }
-    if (STAGE == 4 && first && tid == 0) w.ctl->step += 1;
+    __syncthreads();
+}
+
+// One tile pair (I, J) of stage STAGE of the sparse mixed form: products
+// from the segments of H gathered from L2, the gain on a diagonal pair, the
+// epilogue. pidx is the slot of its residual partial, first marks the pair
+// that advances the step counter. dyn: kMixedDynSmem bytes of dynamic shared
+// memory (16-byte aligned). Ends with a barrier so that the caller may
+// reuse shared memory.
+template <int STAGE>
+__device__ __forceinline__ void mixed_sparse_tile(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                  bool first, uint8_t *dyn) {
+    __shared__ __align__(16) float sX1[TS * LDX];
+    __shared__ __align__(16) float sX2[TS * LDX];
+    __shared__ float sg[TS];
+    const bool diag = (I == J);
+    if (STAGE == 2 && stage2_decide(w, first)) return;
+    const int np = ops.np;
+    const size_t plane = (size_t)np * np;
+    const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
+    spmm32_pair(ops, din, plane, I, J, diag, sX1, sX2, dyn);
+    // only diagonal tiles add the gain g = G p(delta); they compute it for
+    // their own rows
+    if (diag) {
+        gain_rows(ops, din, I * TS, NT / 32, I * TS + TS, I * TS, sg);
+        __syncthreads();
+    }
+    // the output stash reuses the dynamic buffer (free after the products)
+    tile_epilogue<STAGE>(ops, w, I, J, pidx, sX1, sX2, sg, reinterpret_cast<float *>(dyn));
+    if (STAGE == 4 && first && threadIdx.x == 0) w.ctl->step += 1;
     __syncthreads();
 }
 

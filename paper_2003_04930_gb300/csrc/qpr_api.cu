@@ -45,6 +45,11 @@ struct qpr_ctx {
     __nv_bfloat16 *d_dsplit = nullptr;  // dense mixed form: 3 delta-split buffers of 6 planes
     int2 *d_pairs_tc = nullptr;
     qpr::TcMaps tcmaps{};
+    int2 *d_colkh = nullptr;    // column-block form: packed CSR, plan arrays, X = H delta
+    int *d_colint = nullptr;    // q | sb | wb
+    int4 *d_colpieces = nullptr;
+    float *d_X = nullptr;
+    qpr::ColMaps colmaps{};
     qpr::MixedWork mw{};
     double *d_g = nullptr;
     double *d_partials = nullptr;
@@ -223,6 +228,11 @@ qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     return QPR_OK;
 }
 
+int mixed_launches_per_step(const qpr_ctx *ctx) {
+    if (ctx->mw.cmaps) return qpr::kMixedLaunchesPerStepCols;
+    return (ctx->mw.splitD ? 2 : 1) * qpr::kMixedLaunchesPerStep;
+}
+
 void enqueue_mixed_block(qpr_ctx *ctx, int steps) {
     qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
     for (int k = 0; k < steps; ++k)
@@ -273,8 +283,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         } else {
             enqueue_mixed_block(ctx, block);
         }
-        ctx->launches += qpr::kMixedLaunchesPerRefresh +
-                         (ctx->mw.splitD ? 2 : 1) * qpr::kMixedLaunchesPerStep * (int64_t)block;
+        ctx->launches += qpr::kMixedLaunchesPerRefresh + mixed_launches_per_step(ctx) * (int64_t)block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
         if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
@@ -535,6 +544,10 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_mix64);
     cudaFree(ctx->d_mix32);
     cudaFree(ctx->d_g32);
+    cudaFree(ctx->d_colkh);
+    cudaFree(ctx->d_colint);
+    cudaFree(ctx->d_colpieces);
+    cudaFree(ctx->d_X);
     cudaFree(ctx->d_sval32);
     cudaFree(ctx->d_partials32);
     cudaFree(ctx->d_hval32);
@@ -584,6 +597,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
     if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
+    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_TILES)
+        return arg_err(QPR_E_ARG, "unknown sparse_form");
     HostOps hops;
     {
         std::string aerr;
@@ -750,6 +765,30 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         CREATE_CUDA(cudaMalloc(&ctx->d_sval32, sv32.size() * sizeof(float)));
         CREATE_CUDA(cudaMemcpy(ctx->d_sval32, sv32.data(), sv32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
+    qpr::ColPlan cplan;
+    const bool cols = (o.precision == QPR_MIXED) && !tc && o.sparse_form != QPR_SPARSE_FORM_TILES &&
+                      qpr::plan_columns(hops, np, ctx->device, cplan);
+    if (o.precision == QPR_MIXED && !tc && o.sparse_form == QPR_SPARSE_FORM_COLUMNS && !cols) {
+        ctx->err = "sparse_form COLUMNS: the staged operands of N = " + std::to_string(n) +
+                   " do not fit one CTA's shared memory";
+        return bail(QPR_E_ARG);
+    }
+    if (cols) {
+        CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
+        std::vector<int> ints;
+        ints.insert(ints.end(), cplan.q.begin(), cplan.q.end());
+        ints.insert(ints.end(), cplan.sb.begin(), cplan.sb.end());
+        ints.insert(ints.end(), cplan.wb.begin(), cplan.wb.end());
+        CREATE_CUDA(cudaMalloc(&ctx->d_colkh, cplan.kh.size() * sizeof(int2)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_colkh, cplan.kh.data(), cplan.kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_colint, ints.size() * sizeof(int)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_colint, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_colpieces, std::max<size_t>(1, cplan.pieces.size()) * sizeof(int4)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_colpieces, cplan.pieces.data(), cplan.pieces.size() * sizeof(int4),
+                               cudaMemcpyHostToDevice));
+        CREATE_CUDA(cudaMalloc(&ctx->d_X, 2 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMemset(ctx->d_X, 0, 2 * plane * sizeof(float)));
+    }
     CREATE_CUDA(cudaMalloc(&ctx->d_ctl, sizeof(Ctl)));
     CREATE_CUDA(cudaMemset(ctx->d_ctl, 0, sizeof(Ctl)));
     CREATE_CUDA(cudaMalloc(&ctx->d_io, (size_t)n * n * 2 * sizeof(double)));
@@ -808,6 +847,25 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         mw.Ghi = ctx->d_mix32 + 12 * plane;
         mw.Glo = ctx->d_mix32 + 14 * plane;
         mw.partials32 = ctx->d_partials32;
+        if (cols) {
+            ops.col_kh = ctx->d_colkh;
+            ops.col_q = ctx->d_colint;
+            ops.col_sb = ctx->d_colint + cplan.q.size();
+            ops.col_wb = ctx->d_colint + cplan.q.size() + cplan.sb.size();
+            ops.col_pieces = ctx->d_colpieces;
+            ops.col_splits = cplan.splits;
+            ops.col_smem = cplan.smem;
+            ops.col_p_off = cplan.p_off;
+            mw.X = ctx->d_X;
+            const float *din[3] = {mw.D, mw.da, mw.db};
+            if (!qpr::make_col_maps(ops, din, &ctx->colmaps)) {
+                ctx->err = "cuTensorMapEncodeTiled failed";
+                g_create_error = ctx->err;
+                qpr_destroy(ctx);
+                return QPR_E_CUDA;
+            }
+            mw.cmaps = &ctx->colmaps;
+        }
         mw.g = ctx->d_g32;
         mw.g64 = ctx->d_g;
         mw.partials = ctx->d_partials;

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <string>
@@ -12,6 +13,8 @@
 #include "qpr.h"
 
 namespace qpr {
+
+struct HostOps;
 
 // Device control block. The host writes tol, dt and max_steps before a
 // solve; the kernels read them (so a captured CUDA graph serves every dt)
@@ -31,7 +34,7 @@ struct Ctl {
     double resid_exact; // exact FP64 residual of the last reference refresh (mixed form)
     long long resid_exact_step;
     int err_timeout;    // a bounded device-side wait gave up
-    int pad_;
+    int ticket;         // CTAs of the current stage-1 epilogue that finished (column-block form)
     // FP32 forms of dt for the mixed form's delta stages, written by its
     // refresh: dtf = fl(dt) and dt / 6 = dt6h + dt6l as a float-float pair
     float dtf, dt6h, dt6l, pad2_;
@@ -67,6 +70,18 @@ struct DevOps {
     // a delta stage): S values, alpha, 1 - alpha, omega, 1 / (n - 1), 1 / n
     const float *s_val32;
     float alpha32, oma32, omega32, inv_nm1_32, inv_n32;
+    // column-block form of the sparse mixed stage (plan of ColPlan; 0 splits:
+    // not used): the CSR of H packed as (column, FP32 value bits); per row
+    // split its entry range {first (even), end} and bundle range; bundles of
+    // 4 row pieces {row, q0, len, flags}; per (split, warp) the first bundle
+    const int2 *col_kh;
+    const int *col_q;      // 2 per split
+    const int *col_sb;     // splits + 1: bundles of split r are [col_sb[r], col_sb[r + 1])
+    const int4 *col_pieces;
+    const int *col_wb;     // splits * 16 + 1, absolute bundle indices
+    int col_splits;
+    int col_smem;          // dynamic shared memory of the SpMM kernel
+    int col_p_off;         // byte offset of the staged bundles in it
 };
 
 // RK4 work buffers. Every state buffer holds two np x np FP64 planes,
@@ -109,6 +124,17 @@ struct MixedWork {
     int npairs_tc;
     __nv_bfloat16 *splitD, *splitA, *splitB;
     const TcMaps *maps;   // host pointer, used only by the launch code
+    // column-block form of the sparse backend: X = H delta (2 planes) and the
+    // TMA maps of the stage inputs D, da, db (host pointer; null: tile-pair
+    // kernel)
+    float *X;
+    const struct ColMaps *cmaps;
+};
+
+// TMA descriptors of the stage inputs D, da, db for the column-block SpMM:
+// each pair of planes seen as 2 np rows of np FP32, boxes of 8 x 256.
+struct ColMaps {
+    CUtensorMap d[3];
 };
 
 constexpr int kTileTc = 128;
@@ -159,8 +185,32 @@ cudaError_t init_mixed_tc();
 bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfloat16 *const dsplit[3],
                   TcMaps *maps);
 void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcMaps &m, cudaStream_t s);
+// Column-block form of the sparse mixed stage (stage_cols.cu): per stage a
+// column-block SpMM X = H delta from TMA-staged columns, then the tile-pair
+// epilogue. Used where its staged operands fit (np <= kColMaxNp and a plan).
+constexpr int kColMaxNp = 1536;
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps);
+// Host plan of the column-block SpMM (device copies go to DevOps col_*).
+struct ColPlan {
+    int splits = 0;
+    int smem = 0;                 // dynamic shared memory per CTA
+    int p_off = 0;                // byte offset of the staged bundles
+    std::vector<int2> kh;         // packed CSR, padded by 2 entries
+    std::vector<int> q;           // 2 per split
+    std::vector<int> sb;          // splits + 1
+    std::vector<int4> pieces;     // 4 per bundle
+    std::vector<int> wb;          // splits * 16 + 1
+};
+// Plans the column-block form of an np x np problem on `device`; false if
+// its staged operands do not fit one CTA's shared memory.
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan);
+// Opt in to `bytes` of dynamic shared memory for the SpMM kernels.
+cudaError_t set_cols_smem(int bytes);
+void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
 // Kernel launches per RK4 step and per refresh of the mixed form.
-constexpr int kMixedLaunchesPerStep = 4;   // sparse backend (the dense one adds 4 gain kernels)
+constexpr int kMixedLaunchesPerStep = 4;   // tile-pair sparse kernel (the dense one adds 4 gain kernels)
+constexpr int kMixedLaunchesPerStepCols = 8;  // column-block form: SpMM + epilogue per stage
 constexpr int kMixedLaunchesPerRefresh = 5;
 
 // ---- host assembly (qpr_api.cu) ----
@@ -184,6 +234,7 @@ std::vector<double> column_sums_G(const HostOps &h, double alpha, int np, double
 void set_create_error(const std::string &msg);
 // Opt in to the dynamic shared memory of the batched kernels (batch.cu).
 cudaError_t init_batch();
+cudaError_t set_bcols_smem(int bytes);
 double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
                        const std::vector<double> &val);
 

@@ -1,0 +1,272 @@
+// Column-block form of the sparse mixed stage for one problem (see
+// cols_body.cuh): the SpMM kernel stages delta[:, J] with a 3-D TMA box
+// (rows of 16 real then 16 imaginary values), its split's CSR entries and
+// its work list with bulk copies, and forms X[:, J] = H delta[:, J] for its
+// rows; the epilogue kernel applies the RK4 stage per tile pair. Each step
+// is 8 launches (SpMM + epilogue per stage).
+//
+// The SpMM reads each column block once per row split (about splits x 8 N^2
+// bytes of L2 traffic per stage) instead of gathering a row slice of delta
+// from L2 for every (nonzero, column tile) pair (nnz x 8 N bytes), and its
+// inner loop is two shared-memory reads and four FMAs per nonzero.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cols_body.cuh"
+#include "qpr_internal.cuh"
+#include "tma_util.cuh"
+
+namespace qpr {
+namespace {
+
+using namespace cols;
+
+template <int STAGE>
+__global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
+                                                         MixedWork w) {
+    extern __shared__ uint8_t dyn_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_done;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        s_done = *(volatile int *)&w.ctl->done;
+        if (!s_done) {
+            tma::mbar_init(&bar, 1);
+            tma::mbar_init_fence();
+        }
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int J = blockIdx.x, r = blockIdx.y, np = ops.np;
+    const uint32_t s0 = tma::smem_u32(dyn_raw);
+    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);  // 128-byte aligned, shared provenance kept
+    float *sD = reinterpret_cast<float *>(base);
+    int2 *sKH = reinterpret_cast<int2 *>(base + (size_t)np * kRowFloats * 4);
+    int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
+    const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
+    const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
+    if (tid == 0) {
+        const uint32_t kh_bytes = (uint32_t)(((q_end - q_base) * 8 + 15) / 16 * 16);
+        const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 64);
+        tma::mbar_expect_tx(&bar, (uint32_t)np * kRowFloats * 4 + kh_bytes + p_bytes);
+        for (int b = 0; b < np; b += kBoxRows)
+            tma::load_3d(sD + (size_t)b * kRowFloats, &tm, &bar, J * kCW, 0, b);
+        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
+        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 4 * (size_t)p_base, p_bytes, &bar);
+    }
+    // while the operands are in flight: a share of the gain
+    cta_gain(ops, w, stage_input<STAGE>(w), r * gridDim.x + J, gridDim.x * gridDim.y);
+    const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
+    const bool ok = tma::mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        // bounded wait gave up: report, give the copies one more bounded wait, return
+        if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
+        tma::mbar_wait(&bar, 0);
+        return;
+    }
+    warp_bundles(sD, sKH, sP, q_base, p_base, wb0, wb1, J, np, w.X);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(NT) cols_epi_kernel(DevOps ops, MixedWork w) {
+    __shared__ __align__(16) float sX1[TS * LDX];
+    __shared__ __align__(16) float sX2[TS * LDX];
+    __shared__ __align__(16) float sO[4 * TS * LDO];
+    __shared__ float sg[TS];
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    if (s_done) return;
+    const int2 pr = w.pairs[blockIdx.x];
+    epilogue_pair<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO);
+}
+
+int max_smem_optin(int device) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaGetLastError();
+        v = 0;
+    }
+    return v;
+}
+
+template <int STAGE>
+cudaError_t set_spmm_attr(int bytes) {
+    return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Bundles of one split's rows [r0, r1): long rows alone, the others 4 at a
+// time by decreasing length; then dealt to the warps longest first, each to
+// the least loaded warp. Appends the pieces and the warps' first bundles.
+void split_bundles(const HostOps &h, int r0, int r1, int n, std::vector<int4> &pieces, std::vector<int> &wb) {
+    struct Bundle {
+        int4 p[4];
+        long long cost;
+    };
+    std::vector<Bundle> bs;
+    std::vector<int> shortrows;
+    auto row_len = [&](int i) { return i < n ? (int)(h.hptr[i + 1] - h.hptr[i]) : 0; };
+    auto row_q0 = [&](int i) { return i < n ? (int)h.hptr[i] : (int)h.hptr[n]; };
+    const int4 empty = make_int4(-1, 0, 0, 0);
+    for (int i = r0; i < r1; ++i) {
+        const int len = row_len(i);
+        if (len > kLongRow) {
+            const int T = (len + 3) / 4;
+            Bundle b;
+            b.p[0] = make_int4(i, row_q0(i), len, kPieceLong | (T << 1));
+            b.p[1] = b.p[2] = b.p[3] = empty;
+            b.cost = T + 8;
+            bs.push_back(b);
+        } else {
+            shortrows.push_back(i);
+        }
+    }
+    std::stable_sort(shortrows.begin(), shortrows.end(), [&](int a, int b) { return row_len(a) > row_len(b); });
+    for (size_t k = 0; k < shortrows.size(); k += 4) {
+        Bundle b;
+        const int T = row_len(shortrows[k]);
+        for (int j = 0; j < 4; ++j) {
+            if (k + j < shortrows.size()) {
+                const int i = shortrows[k + j];
+                b.p[j] = make_int4(i, row_q0(i), row_len(i), 0);
+            } else {
+                b.p[j] = empty;
+            }
+        }
+        b.p[0].w = T << 1;
+        b.cost = T + 8;
+        bs.push_back(b);
+    }
+    std::stable_sort(bs.begin(), bs.end(), [](const Bundle &a, const Bundle &b) { return a.cost > b.cost; });
+    std::vector<std::vector<int>> per(kAWarps);
+    std::vector<long long> load(kAWarps, 0);
+    for (int k = 0; k < (int)bs.size(); ++k) {
+        const int wmin = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[wmin].push_back(k);
+        load[wmin] += bs[k].cost;
+    }
+    for (int wi = 0; wi < kAWarps; ++wi) {
+        wb.push_back((int)(pieces.size() / 4));
+        for (int k : per[wi])
+            for (int j = 0; j < 4; ++j) pieces.push_back(bs[k].p[j]);
+    }
+}
+
+}  // namespace
+
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan) {
+    if (np > kColMaxNp || np % kBoxRows != 0) return false;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return false;
+    }
+    const int smem_max = max_smem_optin(device);
+    const int n = (int)h.n;
+    const int ncb = np / kCW;
+    // cumulative row cost (nonzeros + a per-row overhead) for the splits
+    std::vector<double> cum(np + 1, 0.0);
+    for (int i = 0; i < np; ++i) {
+        const double nz = (i < n) ? (double)(h.hptr[i + 1] - h.hptr[i]) : 0.0;
+        cum[i + 1] = cum[i] + nz + 4.0;
+    }
+    for (int s = std::max(1, sms / ncb); s <= 16; ++s) {
+        ColPlan pl;
+        pl.splits = s;
+        std::vector<int> rows(s + 1, 0);
+        int i = 0;
+        for (int k = 1; k < s; ++k) {
+            const double target = cum[np] * (double)k / (double)s;
+            while (i < np && cum[i] < target) ++i;
+            rows[k] = std::max(rows[k - 1], i);
+        }
+        rows[s] = np;
+        size_t kh_max = 0, p_max = 0;
+        for (int k = 0; k < s; ++k) {
+            const int qs = (int)h.hptr[std::min(rows[k], n)], qe = (int)h.hptr[std::min(rows[k + 1], n)];
+            const int qs_even = qs & ~1;
+            pl.q.push_back(qs_even);
+            pl.q.push_back(qe);
+            kh_max = std::max(kh_max, (size_t)((qe - qs_even) * 8 + 15) / 16 * 16);
+            const int first = (int)(pl.pieces.size() / 4);
+            pl.sb.push_back(first);
+            split_bundles(h, rows[k], rows[k + 1], n, pl.pieces, pl.wb);
+            p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / 4) - first) * 64);
+        }
+        pl.sb.push_back((int)(pl.pieces.size() / 4));
+        pl.wb.push_back((int)(pl.pieces.size() / 4));
+        pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
+        const size_t smem = (size_t)pl.p_off + p_max + 128;
+        // 1 KB left for the static shared memory of the kernels (the batched
+        // kernel keeps its problem descriptor there)
+        if (smem_max > 1024 && smem <= (size_t)smem_max - 1024) {
+            pl.smem = (int)smem;
+            pl.kh.resize(h.hval.size() + 2);
+            for (size_t q = 0; q < h.hval.size(); ++q) {
+                const float v = (float)h.hval[q];
+                int bits;
+                memcpy(&bits, &v, 4);
+                pl.kh[q] = make_int2(h.hcol[q], bits);
+            }
+            pl.kh[h.hval.size()] = pl.kh[h.hval.size() + 1] = make_int2(0, 0);
+            plan = std::move(pl);
+            return true;
+        }
+    }
+    return false;
+}
+
+bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t np = (cuuint64_t)ops.np;
+    for (int i = 0; i < 3; ++i) {
+        // (column, plane, row): a box is kBoxRows rows of kCW real then kCW imaginary values
+        cuuint64_t dims[3] = {np, 2, np};
+        cuuint64_t strides[2] = {np * np * sizeof(float), np * sizeof(float)};
+        cuuint32_t box[3] = {kCW, 2, kBoxRows};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&maps->d[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)din[i], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+cudaError_t set_cols_smem(int bytes) {
+    cudaError_t e = set_spmm_attr<1>(bytes);
+    if (e == cudaSuccess) e = set_spmm_attr<2>(bytes);
+    if (e == cudaSuccess) e = set_spmm_attr<3>(bytes);
+    if (e == cudaSuccess) e = set_spmm_attr<4>(bytes);
+    return e;
+}
+
+// Stage inputs: stage 1 D (map 0), stage 2 da (map 1), stage 3 db (map 2),
+// stage 4 da (map 1). parts & 1: the SpMM kernel, parts & 2: the epilogue.
+void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts) {
+    const ColMaps &m = *w.cmaps;
+    const dim3 ga(ops.np / kCW, ops.col_splits);
+    const size_t sm = (size_t)ops.col_smem;
+    if (parts & 1) {
+        switch (stage) {
+            case 1: cols_spmm_kernel<1><<<ga, kANT, sm, s>>>(m.d[0], ops, w); break;
+            case 2: cols_spmm_kernel<2><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
+            case 3: cols_spmm_kernel<3><<<ga, kANT, sm, s>>>(m.d[2], ops, w); break;
+            default: cols_spmm_kernel<4><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
+        }
+    }
+    if (parts & 2) {
+        switch (stage) {
+            case 1: cols_epi_kernel<1><<<w.npairs, NT, 0, s>>>(ops, w); break;
+            case 2: cols_epi_kernel<2><<<w.npairs, NT, 0, s>>>(ops, w); break;
+            case 3: cols_epi_kernel<3><<<w.npairs, NT, 0, s>>>(ops, w); break;
+            default: cols_epi_kernel<4><<<w.npairs, NT, 0, s>>>(ops, w); break;
+        }
+    }
+}
+
+}  // namespace qpr

@@ -120,6 +120,10 @@ void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s)
 }
 
 void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts) {
+    if (w.cmaps) {  // column-block form: parts 1 = SpMM, 2 = epilogue
+        launch_cols_stage(stage, ops, w, s, parts);
+        return;
+    }
     const float *din = (stage == 1) ? w.D : (stage == 3 ? w.db : w.da);
     int gb = (ops.np + 7) / 8;
     if (gb > 152) gb = 152;

@@ -29,6 +29,7 @@
 
 #include "mixed_body.cuh"
 #include "qpr_internal.cuh"
+#include "tma_util.cuh"
 
 namespace qpr {
 namespace {
@@ -46,50 +47,15 @@ constexpr int SMEM_PIPE = NSTAGE * STAGE_BYTES;
 constexpr int SMEM_EPI = TB * LDS * 4;
 constexpr int SMEM_BYTES = (SMEM_PIPE > SMEM_EPI ? SMEM_PIPE : SMEM_EPI) + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long kSpinLimit = 1ll << 26;
 
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bounded wait for phase `parity`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];\n" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                            int c2, int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
-        "%6}], [%2];\n" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait;
+using tma::smem_u32;
+using tma::load_3d;
+using tma::load_4d;
 
 // Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
 // swizzled layout written by TMA (8 rows x 128 B atoms, 1024 B between
@@ -201,7 +167,7 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&accum_bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        tma::mbar_init_fence();
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -230,13 +196,13 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
             const int li = (int)((kSegI >> (4 * seg)) & 0xFu), lj = (int)((kSegJ >> (4 * seg)) & 0xFu);
             uint8_t *sb = smem + st * STAGE_BYTES;
             mbar_expect_tx(&full_bar[st], tx);
-            tma_load_3d(sb + OFF_AI, &tmH, &full_bar[st], k0, I * TB, li);
-            tma_load_4d(sb + OFF_BJ, &tmIn, &full_bar[st], k0, J * TB, 0, lj);
-            tma_load_4d(sb + OFF_BJ + B_BYTES / 2, &tmIn, &full_bar[st], k0, J * TB, 1, lj);
+            load_3d(sb + OFF_AI, &tmH, &full_bar[st], k0, I * TB, li);
+            load_4d(sb + OFF_BJ, &tmIn, &full_bar[st], k0, J * TB, 0, lj);
+            load_4d(sb + OFF_BJ + B_BYTES / 2, &tmIn, &full_bar[st], k0, J * TB, 1, lj);
             if (!diag) {
-                tma_load_3d(sb + OFF_AJ, &tmH, &full_bar[st], k0, J * TB, li);
-                tma_load_4d(sb + OFF_BI, &tmIn, &full_bar[st], k0, I * TB, 0, lj);
-                tma_load_4d(sb + OFF_BI + B_BYTES / 2, &tmIn, &full_bar[st], k0, I * TB, 1, lj);
+                load_3d(sb + OFF_AJ, &tmH, &full_bar[st], k0, J * TB, li);
+                load_4d(sb + OFF_BI, &tmIn, &full_bar[st], k0, I * TB, 0, lj);
+                load_4d(sb + OFF_BI + B_BYTES / 2, &tmIn, &full_bar[st], k0, I * TB, 1, lj);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -368,7 +334,7 @@ cudaError_t set_attr() {
                                 SMEM_BYTES);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_impl() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -383,6 +349,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return get_encode_impl(); }
+
 cudaError_t init_mixed_tc() {
     cudaError_t e = set_attr<1>();
     if (e == cudaSuccess) e = set_attr<2>();
@@ -395,7 +363,7 @@ cudaError_t init_mixed_tc() {
 // BF16, boxes of 64 (K) x 128 rows, 128-byte swizzle.
 bool make_tc_maps(const DevOps &ops, const __nv_bfloat16 *hsplit, const __nv_bfloat16 *const dsplit[3],
                   TcMaps *maps) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t np = (cuuint64_t)ops.np;
     {

@@ -22,6 +22,7 @@ QPR_FP64, QPR_MIXED = 0, 1
 QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
 QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
+QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES = 0, 1, 2
 
 # every entry point declared in include/qpr.h
 EXPORTED = (
@@ -38,7 +39,8 @@ class qpr_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("h_diag", ctypes.c_int32), ("dangling", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("backend", ctypes.c_int32),
-                ("ref_refresh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("ref_refresh", ctypes.c_int32), ("sparse_form", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class qpr_stats(ctypes.Structure):
@@ -179,7 +181,7 @@ class Solver:
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO, ref_refresh=32):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -193,6 +195,7 @@ class Solver:
         opt.device = int(device)
         opt.backend = int(backend)
         opt.ref_refresh = int(ref_refresh)
+        opt.sparse_form = int(sparse_form)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         h = ctypes.c_void_p()
