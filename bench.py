@@ -35,6 +35,20 @@ if ROOT not in sys.path:
 METRIC = "time-to-steady-state (resid 1e-8) N=922/4096, warm+BF16 vs plain FP64; %TC peak"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # nominal dense FP64 / dense BF16 tensor rate of GB300
+SMS = 152            # streaming multiprocessors of a GB300
+SM_MAX_GHZ = 2.07    # maximum SM clock
+
+
+def h_nonzeros(g):
+    """Nonzeros of the off-diagonal H: ordered pairs (i, j), i != j, with a
+    link i -> j or j -> i of nonzero weight."""
+    import numpy as np
+    src = np.asarray(g.src, dtype=np.int64)
+    dst = np.asarray(g.dst, dtype=np.int64)
+    w = np.ones(len(src)) if g.w is None else np.asarray(g.w, dtype=np.float64)
+    keep = (src != dst) & (w != 0)
+    a, b = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
+    return 2 * int(np.unique(a * (int(g.n) + 1) + b).size)
 
 
 def parse_args():
@@ -286,6 +300,32 @@ def run_ours(a):
                 "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "stage_mixed_tc_kernel (tcgen05)",
                 "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
                 "peak_source": f"bf16_tflops of {peak_src}"}
+    elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
+            s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
+        # column-block SpMM: every nonzero of H reads its row slice of each
+        # column block from shared memory, nnz(H) x np x 8 bytes per launch;
+        # bound by shared-memory bandwidth, peak derived from the unit counts
+        # (128 bytes per clock per SM) and the maximum SM clock
+        npad = ((n + 31) // 32) * 32
+        alg = h_nonzeros(g) * npad * 8
+        smem_peak = 128.0 * SMS * SM_MAX_GHZ  # GB/s
+        ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
+        # epilogue kernel: N x N planes read or written per stage, mean of the
+        # 4 stages: X (8), delta in (8), F32 (8), S (8 read at stages 2-4,
+        # written at 1-3), the next delta (8, stages 1-3); stage 4 adds D, Dlo
+        # (read and written) and Ghi, Glo: 56 + 64 + 64 + 80 = 264 / 4 = 66
+        epi_alg = 66 * n * n
+        roof = {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
+                "traffic": None, "kernel": "cols_spmm_kernel",
+                "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
+                "peak_source": f"derived: 128 B/clk/SM x {SMS} SMs x {SM_MAX_GHZ} GHz",
+                "epilogue": {"kernel": "cols_epi_kernel", "bound": "hbm", "launch_ms": prof["stage_ms"],
+                             "alg_bytes_per_launch": epi_alg,
+                             "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                             "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                             "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
+                "note": "launch_ms from CUDA events around each launch (includes the launch gap); the state "
+                        "is L2-resident at this N, so the epilogue's HBM fraction can exceed 1"}
     elif s.backend == qpr.QPR_BACKEND_SPARSE:
         if prec == qpr.QPR_MIXED:
             # mean over the 4 stages of the N x N planes read or written: FP32
@@ -315,8 +355,11 @@ def run_ours(a):
     form = {(qpr.QPR_FP64, 1): "fp64 dense DMMA", (qpr.QPR_FP64, 2): "fp64 sparse CSR",
             (qpr.QPR_MIXED, 1): "mixed: split-BF16 tcgen05 GEMM deltas (FP32 accumulate) + fp64 "
                                 "reference/accumulation/residual",
-            (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas + fp64 reference/accumulation/residual"}[
-        (prec, s.backend)]
+            (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas (tile pairs) + float-float delta "
+                                "accumulation + fp64 reference/residual"}[(prec, s.backend)]
+    if s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
+        form = ("mixed: fp32 column-block SpMM from TMA-staged shared memory + tile-pair epilogue, "
+                "float-float delta accumulation, fp64 reference/residual")
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",

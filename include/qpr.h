@@ -91,13 +91,23 @@ enum { QPR_DANGLING_F = 0, QPR_DANGLING_UNIFORM = 1 };
 enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
 /* Form of the FP32 stage of QPR_MIXED with the sparse backend.
  * COLUMNS: per stage a column-block product X = H (Y_s - R), each CTA
- *   staging 8 complex columns of the delta in shared memory with TMA, then a
- *   tile-pair epilogue (2 launches per stage); for N padded to 32 <= 1536.
+ *   staging 16 complex columns of the delta in shared memory with TMA, then
+ *   a tile-pair epilogue: 2 launches per stage (and the gain on a forked
+ *   branch beside the product); where the staged operands fit one CTA's
+ *   shared memory (N padded to 32 <= 1536).
+ * COLUMNS_PERSISTENT: the same arithmetic in one cooperative launch per
+ *   block of ref_refresh steps, grid barriers between the phases (needs
+ *   cooperative launch support).
  * TILES: one launch per stage; each 32 x 32 tile pair gathers, from L2, the
  *   row slices of the delta that its rows' nonzeros select.
- * AUTO (default): COLUMNS where it applies, else TILES. The two forms differ
- * only in FP32 summation order. */
-enum { QPR_SPARSE_FORM_AUTO = 0, QPR_SPARSE_FORM_COLUMNS = 1, QPR_SPARSE_FORM_TILES = 2 };
+ * AUTO (default): COLUMNS where it applies, else TILES. The column forms give
+ * bitwise the same results; TILES differs only in FP32 summation order. */
+enum {
+    QPR_SPARSE_FORM_AUTO = 0,
+    QPR_SPARSE_FORM_COLUMNS = 1,
+    QPR_SPARSE_FORM_TILES = 2,
+    QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 3
+};
 
 typedef struct {
     int32_t precision;   /* QPR_FP64 (default) or QPR_MIXED */
@@ -150,9 +160,13 @@ QPR_API const char *qpr_status_string(qpr_status s);
 
 /* Number of nodes and the estimated spectral spread lambda_max - lambda_min
  * of H used by the RK4 step-size check. qpr_backend: the backend in use
- * (QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE). */
+ * (QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE). qpr_sparse_form: the form of
+ * the FP32 sparse stage in use (QPR_SPARSE_FORM_COLUMNS,
+ * _COLUMNS_PERSISTENT or _TILES; 0 when the context is not QPR_MIXED with
+ * the sparse backend). */
 QPR_API int64_t qpr_n(const qpr_ctx *ctx);
 QPR_API int32_t qpr_backend(const qpr_ctx *ctx);
+QPR_API int32_t qpr_sparse_form(const qpr_ctx *ctx);
 QPR_API double qpr_h_spread(const qpr_ctx *ctx);
 
 /* Largest dt for which the context considers one RK4 step stable: it needs
@@ -191,7 +205,9 @@ QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double t
  * RK4 steps from rho (rho itself is not modified) without CUDA graphs,
  * bracketing every kernel launch with CUDA events, and writes the mean
  * durations in milliseconds: ms_out[0] one stage kernel (H rho plus the fused
- * epilogue), ms_out[1] one gain kernel (G p), ms_out[2] one whole step.
+ * epilogue; the epilogue kernel in the column-block form), ms_out[1] one
+ * gain kernel (G p; the SpMM kernel in the column-block form, 0 where the
+ * stage kernel computes the gain itself), ms_out[2] one whole step.
  * Meant for roofline measurements; steps >= 1. */
 QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out);
 

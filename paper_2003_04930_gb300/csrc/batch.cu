@@ -146,13 +146,14 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
                 *reinterpret_cast<float4 *>(sD + k * cols::kRowFloats + 4 * part) = v;
             }
             for (int u = threadIdx.x; u < q_end - q_base; u += blockDim.x) sKH[u] = ops.col_kh[q_base + u];
-            for (int u = threadIdx.x; u < 4 * (p_end - p_base); u += blockDim.x)
-                sP[u] = ops.col_pieces[4 * (size_t)p_base + u];
+            for (int u = threadIdx.x; u < 2 * (p_end - p_base); u += blockDim.x)
+                sP[u] = ops.col_pieces[2 * (size_t)p_base + u];
             const int ncb = np / cols::kCW;
-            cols::cta_gain(ops, sg.mw, din, r * ncb + J, ncb * ops.col_splits);
+            cols::cta_gain(ops, sg.mw, r * ncb + J, ncb * ops.col_splits,
+                           reinterpret_cast<float *>(dyn_smem + ops.col_sp_off));
             __syncthreads();
             const int warp = threadIdx.x >> 5;
-            cols::warp_bundles(sD, sKH, sP, q_base, p_base, ops.col_wb[r * cols::kAWarps + warp],
+            cols::warp_bundles(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
                                ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X);
         }
         __syncthreads();
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
 
 // Column-block form: the epilogue over (problem, I, J, pair) items.
 template <int STAGE>
-__global__ void __launch_bounds__(mixed::NT) b_cols_epi_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+__global__ void __launch_bounds__(cols::kENT, 3) b_cols_epi_kernel(const BatchGraph *gs, const int4 *items,
+                                                                 int nitems) {
     __shared__ __align__(16) float sX1[mixed::TS * mixed::LDX];
     __shared__ __align__(16) float sX2[mixed::TS * mixed::LDX];
     __shared__ __align__(16) float sO[4 * mixed::TS * mixed::LDO];
@@ -221,7 +223,7 @@ template <int STAGE>
 void launch_stage_b(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
     if (L.na) {
         b_cols_spmm_kernel<STAGE><<<std::min(L.na, 152 * 2), cols::kANT, L.smem_a, s>>>(gs, L.items_a, L.na);
-        b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 6), mixed::NT, 0, s>>>(gs, L.items_b, L.nb);
+        b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 3), cols::kENT, 0, s>>>(gs, L.items_b, L.nb);
         launches += 2;
     }
     if (L.nt) {
@@ -364,7 +366,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         od[g] = nd;
         nd += qpr::align_up(2 * p2 + 2 * np[g] + nh + ns + npairs[g], 64);
         of[g] = nf;
-        nf += qpr::align_up(8 * p2 + 2 * np[g] + qpr::align_up(nh, 64) + qpr::align_up(ns, 64) + npairs[g], 64) + 64;
+        nf += qpr::align_up(8 * p2 + 3 * np[g] + qpr::align_up(nh, 64) + qpr::align_up(ns, 64) + npairs[g], 64) + 64;
         oi[g] = ni;
         ni += qpr::align_up(2 * (n + 1) + nh + ns, 64) + qpr::align_up((size_t)np[g] + 1, 64) + 2 * segs[g].size();
         ni = qpr::align_up(ni, 64);
@@ -397,7 +399,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     int smem_a = 0;
     for (size_t g = 0; g < G; ++g) {
         if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g])) {
-            if (o.sparse_form == QPR_SPARSE_FORM_COLUMNS)
+            if (o.sparse_form == QPR_SPARSE_FORM_COLUMNS || o.sparse_form == QPR_SPARSE_FORM_COLUMNS_PERSISTENT)
                 return err(QPR_E_ARG, "problem " + std::to_string(g) +
                                           ": sparse_form COLUMNS does not fit one CTA's shared memory");
             continue;
@@ -503,11 +505,11 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         std::copy(cg.begin(), cg.end(), hD.begin() + (c - dD));
         std::copy(h.hval.begin(), h.hval.end(), hD.begin() + (hval - dD));
         std::copy(h.sval.begin(), h.sval.end(), hD.begin() + (sval - dD));
-        // float arena: F32 D Dlo da db S Ghi Glo | g32 c32 | hval32 | sval32 | partials32
+        // float arena: F32 D Dlo da db S Ghi Glo | g32 pv32 c32 | hval32 | sval32 | partials32
         // (uploaded from zeros, so the delta D + Dlo starts at 0)
         float *F32 = bf, *Dp = bf + p2, *Dlo = bf + 2 * p2, *da = bf + 3 * p2, *db = bf + 4 * p2;
         float *S = bf + 5 * p2, *Ghi = bf + 6 * p2, *Glo = bf + 7 * p2;
-        float *g32 = bf + 8 * p2, *c32 = g32 + p, *hv32 = c32 + p;
+        float *g32 = bf + 8 * p2, *pv32 = g32 + p, *c32 = pv32 + p, *hv32 = c32 + p;
         float *sv32 = hv32 + qpr::align_up(nh, 64), *part32 = sv32 + qpr::align_up(ns, 64);
         for (int j = 0; j < p; ++j) hF[(c32 - dF) + j] = (float)cg[j];
         for (size_t q = 0; q < nh; ++q) hF[(hv32 - dF) + q] = (float)h.hval[q];
@@ -557,6 +559,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
             d.ops.col_splits = pl.splits;
             d.ops.col_smem = pl.smem;
             d.ops.col_p_off = pl.p_off;
+            d.ops.col_sp_off = pl.sp_off;
         }
         d.ops.s_val32 = sv32;
         d.ops.alpha32 = (float)alpha;
@@ -567,7 +570,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         qpr::MixedWork &mw = d.mw;
         mw.R = R; mw.F = F;
         mw.F32 = F32; mw.D = Dp; mw.Dlo = Dlo; mw.da = da; mw.db = db; mw.S = S; mw.Ghi = Ghi; mw.Glo = Glo;
-        mw.g = g32; mw.g64 = g64; mw.partials = part; mw.partials32 = part32;
+        mw.g = g32; mw.pv = pv32; mw.g64 = g64; mw.partials = part; mw.partials32 = part32;
         mw.X = colg[g] ? dXC + oxc[g] : nullptr;
         mw.pairs = nullptr; mw.npairs = npairs[g]; mw.tiles = T[g];
         mw.ctl = dCtl + g;

@@ -10,12 +10,15 @@
 // applies the RK4 stage to every tile pair (I, J), I <= J, from X_IJ and
 // X_JI, as the tile-pair form does.
 //
-// Work list: the rows of a split are cut into bundles of 4 row pieces, one
-// per 8-lane group of a warp (lane p of a group holds 4 of the 32 values of
-// the row: one 16-byte read per nonzero, a whole row per group and no bank
-// conflict); a row longer than kLongRow nonzeros is a bundle of its own,
-// its nonzeros dealt to the 4 groups in turn. Bundles go to warps longest
-// first, each to the least loaded warp.
+// Work list: the rows of a split are cut into bundles, one row per 8-lane
+// group of a warp (lane p of a group holds 4 of the 32 values of a staged
+// row: one 16-byte read per nonzero, a whole row per group, no bank
+// conflict): 4 rows of similar length, or one row longer than kLongRow
+// nonzeros whose nonzeros are dealt to the 4 groups in turn. A bundle's CSR
+// entries are stored interleaved and zero-padded to its T rounds (entry t of
+// group g at 4 t + g), so the 4 groups read one contiguous 32-byte run per
+// round, without predicates. Bundles go to warps longest first, each to the
+// least loaded warp.
 #pragma once
 
 #include "mixed_body.cuh"
@@ -34,58 +37,46 @@ constexpr int kBoxRows = 32;       // rows of one TMA box
 constexpr int kANT = 512;          // threads of the SpMM kernel
 constexpr int kAWarps = kANT / 32;
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
-constexpr int kPieceLong = 1;      // flags bit 0 of piece 0: long-row bundle; flags >> 1: rounds
+constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
+constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
 
-// Shared memory of the SpMM kernel for np rows, `kh` CSR entries and
-// `bundles` bundles (+ 128 bytes of alignment slack).
-__host__ __device__ __forceinline__ size_t spmm_smem_bytes(int np, int kh, int bundles) {
-    return (size_t)np * kRowFloats * 4 + ((size_t)kh * 8 + 15) / 16 * 16 + (size_t)bundles * 64 + 128;
-}
+// A bundle descriptor is two int4: {first entry (relative to its split's
+// entries), rounds T, flags, 0} and the rows of the 4 groups (-1: none; a
+// long-row bundle has only the first).
+constexpr int kBundleInts = 8;
 
 __device__ __forceinline__ float4 f4fma(float h, float4 v, float4 acc) { return mixed::f4fma(h, v, acc); }
 
-// Bundles [b0, b1) of one warp: X[row, J] for each row piece, from the
-// staged block sD ([row][kRowFloats]), the staged CSR entries sKH (entry q
-// at sKH[q - q_base]) and the staged bundles sP (bundle b at sP[4 (b -
-// p_base)]). Sums are formed in a fixed order (per group in entry order,
-// then over the groups of a long row by xor-shuffle), so the result does
-// not depend on timing.
+// Bundles [b0, b1) of one warp: X[row, J] for each row, from the staged
+// block sD ([row][kRowFloats]), the split's staged entries sKH and the
+// staged bundles sP (bundle b at sP[2 (b - p_base)]). Sums are formed in a
+// fixed order (per group in entry order, then over the groups of a long row
+// by xor-shuffle), so the result does not depend on timing.
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
-                                             const int4 *__restrict__ sP, int q_base, int p_base, int b0, int b1,
-                                             int J, int np, float *__restrict__ X) {
+                                             const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
+                                             float *__restrict__ X) {
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
     const float *__restrict__ sDp = sD + 4 * p;
     const size_t plane = (size_t)np * np;
     const int col = J * kCW + 4 * (p & 3);
     float *__restrict__ Xp = X + (p < 4 ? 0 : plane) + col;
     for (int b = b0; b < b1; ++b) {
-        const int4 pc = sP[4 * (b - p_base) + g];
-        const int f0 = sP[4 * (b - p_base)].w;
+        const int4 d0 = sP[2 * (b - p_base)], rows = sP[2 * (b - p_base) + 1];
+        const int2 *__restrict__ kh = sKH + d0.x + g;
+        const int T = d0.y;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (f0 & kPieceLong) {
-            const int4 p0 = sP[4 * (b - p_base)];
-            const int T = f0 >> 1;
 #pragma unroll 4
-            for (int t = 0; t < T; ++t) {
-                const int e = 4 * t + g;
-                const bool v = e < p0.z;
-                const int2 kh = v ? sKH[p0.y + e - q_base] : make_int2(0, 0);
-                const float h = __int_as_float(kh.y);
-                acc = f4fma(h, *reinterpret_cast<const float4 *>(sDp + kh.x * kRowFloats), acc);
-            }
+        for (int t = 0; t < T; ++t) {
+            const int2 e = kh[4 * t];
+            acc = f4fma(__int_as_float(e.y), *reinterpret_cast<const float4 *>(sDp + e.x * kRowFloats), acc);
+        }
+        if (d0.z & kPieceLong) {
             acc = mixed::f4xor(acc, 8);
             acc = mixed::f4xor(acc, 16);
-            if (g == 0) *reinterpret_cast<float4 *>(Xp + (size_t)p0.x * np) = acc;
+            if (g == 0) *reinterpret_cast<float4 *>(Xp + (size_t)rows.x * np) = acc;
         } else {
-            const int T = f0 >> 1;  // longest piece of the bundle
-#pragma unroll 4
-            for (int t = 0; t < T; ++t) {
-                const bool v = t < pc.z;
-                const int2 kh = v ? sKH[pc.y + t - q_base] : make_int2(0, 0);
-                const float h = __int_as_float(kh.y);
-                acc = f4fma(h, *reinterpret_cast<const float4 *>(sDp + kh.x * kRowFloats), acc);
-            }
-            if (pc.x >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)pc.x * np) = acc;
+            const int row = (g == 0) ? rows.x : (g == 1) ? rows.y : (g == 2) ? rows.z : rows.w;
+            if (row >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = acc;
         }
     }
 }
@@ -96,13 +87,47 @@ __device__ __forceinline__ const float *stage_input(const MixedWork &w) {
     return (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
 }
 
-// The gain g = G p(delta): CTA b of the nb SpMM CTAs computes rows
-// [b np / nb, (b + 1) np / nb), at most a few per warp, while its operands
-// are in flight.
-__device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, const float *din, int b, int nb) {
-    const int np = ops.np;
+// The gain g = G p(delta) of rows [b np / nb, (b + 1) np / nb) (CTA b of
+// nb), from the compact diagonal p = w.pv of the stage input (written by the
+// previous epilogue): p is staged in shared memory (sp: np floats) with one
+// coalesced round trip, together with the rows' S entries. The sums are
+// those of gain_rows on the strided diagonal, in the same order.
+__device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, int b, int nb, float *sp) {
+    __shared__ float red[32];
+    const int n = ops.n, np = ops.np;
     const int r0 = (int)((long long)b * np / nb), r1 = (int)((long long)(b + 1) * np / nb);
-    mixed::gain_rows(ops, din, r0, (int)(blockDim.x >> 5), r1, 0, w.g);
+    float P = 0.f, Dd = 0.f;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const float pj = __ldcg(w.pv + j);
+        sp[j] = pj;
+        if (j < n) {
+            P = __fadd_rn(P, pj);
+            if (ops.dang[j]) Dd = __fadd_rn(Dd, pj);
+        }
+    }
+    P = mixed::block_sum_f(P, red);  // its barriers also publish sp
+    Dd = mixed::block_sum_f(Dd, red);
+    const int lane = threadIdx.x & 31;
+    for (int i = r0 + (int)(threadIdx.x >> 5); i < r1; i += (int)(blockDim.x >> 5)) {
+        float s = 0.f;
+        if (i < n) {
+            const int q1 = ops.s_ptr[i + 1];
+            for (int q = ops.s_ptr[i] + lane; q < q1; q += 32) s = __fmaf_rn(ops.s_val32[q], sp[ops.s_col[q]], s);
+        }
+        s = mixed::warp_sum_f(s);
+        if (lane == 0) {
+            float gi = 0.f;
+            if (i < n) {
+                const float pi = sp[i];
+                const float dterm = (ops.dangling == QPR_DANGLING_F)
+                                        ? __fmul_rn(__fsub_rn(Dd, ops.dang[i] ? pi : 0.f), ops.inv_nm1_32)
+                                        : __fmul_rn(Dd, ops.inv_n32);
+                gi = __fmaf_rn(ops.alpha32, __fadd_rn(s, dterm),
+                               __fmul_rn(__fmul_rn(ops.oma32, __fsub_rn(P, pi)), ops.inv_nm1_32));
+            }
+            w.g[i] = gi;
+        }
+    }
 }
 
 // Stop decision after stage 1, taken by the last epilogue CTA to finish
@@ -111,67 +136,85 @@ __device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, 
 // estimate and, when the run stops here, sets done so that the kernels of
 // stages 2..4 return at once. A step whose exact residual a refresh already
 // judged is not judged again. Called by every thread after tile_epilogue.
-__device__ __forceinline__ void stage1_last_decides(const MixedWork &w, int nparts) {
-    __shared__ int s_last;
+// Stop decision from the stage-1 partials of step `step` (every thread of
+// the CTA calls it; all CTAs that call it compute the same sum in index
+// order). Returns the status; the CTA with `record` writes it to ctl.
+__device__ __forceinline__ int stage1_decision(const MixedWork &w, int nparts, long long step, bool record) {
     __shared__ float red[32];
+    __shared__ int s_status;
     Ctl *ctl = w.ctl;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = (atomicAdd(&ctl->ticket, 1) == nparts - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
     float s = 0.f;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s = __fadd_rn(s, __ldcg(w.partials32 + i));
     s = mixed::block_sum_f(s, red);
     if (threadIdx.x == 0) {
-        ctl->ticket = 0;
-        if (ctl->resid_exact_step != ctl->step) {
+        int status = kCtlRunning;
+        if (*(volatile long long *)&ctl->resid_exact_step != step) {
             const double r = sqrt((double)s);
-            int status = kCtlRunning;
             if (!isfinite(r)) status = kCtlNonFinite;
             else if (r < ctl->tol) status = kCtlCandidate;
-            else if (ctl->step >= ctl->max_steps) status = kCtlMaxSteps;
-            ctl->resid = r;
-            ctl->resid_step = ctl->step;
-            if (status != kCtlRunning) {
-                ctl->status = status;
-                ctl->done = 1;
+            else if (step >= ctl->max_steps) status = kCtlMaxSteps;
+            if (record) {
+                ctl->resid = r;
+                ctl->resid_step = step;
+                if (status != kCtlRunning) {
+                    ctl->status = status;
+                    ctl->done = 1;
+                }
             }
         }
+        s_status = status;
     }
+    __syncthreads();
+    return s_status;
+}
+
+__device__ __forceinline__ void stage1_last_decides(const MixedWork &w, int nparts) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(&w.ctl->ticket, 1) == nparts - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) w.ctl->ticket = 0;
+    stage1_decision(w, nparts, *(volatile long long *)&w.ctl->step, true);
 }
 
 // Epilogue of tile pair (I, J) from X (global, written by the SpMM kernel)
-// and the gain w.g; stage 1 ends with the ticket of the stop decision,
-// stage 4 advances the step counter (first pair). Shared memory: sX1, sX2
-// (TS * LDX floats each), sg (TS), sO (4 * TS * LDO).
-template <int STAGE>
+// and the gain w.g (both read from L2: other CTAs wrote them); stage 1 ends
+// with the ticket of the stop decision (TICKET),
+// stage 4 advances the step counter (first pair). kENT threads. Shared
+// memory: sX1, sX2 (TS * LDX floats each), sg (TS), sO (4 * TS * LDO).
+template <int STAGE, bool TICKET = true>
 __device__ __forceinline__ void epilogue_pair(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
                                               bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO) {
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const bool diag = (I == J);
     const int ntiles = diag ? 1 : 2;
+    // the elementwise operands first, so that their loads and the X tiles'
+    // are in flight together
+    mixed::EpiIn<STAGE, kENT> in;
+    mixed::epi_load<STAGE, kENT>(ops, w, I, J, in);
     // X tiles as [a][LDX] rows (real part, then imaginary part), float4 loads
-    for (int t = threadIdx.x; t < ntiles * TS * (2 * TS / 4); t += NT) {
+    for (int t = threadIdx.x; t < ntiles * TS * (2 * TS / 4); t += kENT) {
         const int which = t / (TS * (2 * TS / 4));
         const int u = t - which * (TS * (2 * TS / 4));
         const int a = u / (2 * TS / 4), q = u - a * (2 * TS / 4);  // q: 0..7 real quads, 8..15 imaginary
         const int R = which ? J : I, C = which ? I : J;
         const size_t o = (size_t)(R * TS + a) * np + C * TS + 4 * (q & 7);
-        const float4 v = *reinterpret_cast<const float4 *>(w.X + (q < 8 ? 0 : plane) + o);
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(w.X + (q < 8 ? 0 : plane) + o));
         float *dst = (which ? sX2 : sX1) + a * LDX + 4 * q;
         dst[0] = v.x;
         dst[1] = v.y;
         dst[2] = v.z;
         dst[3] = v.w;
     }
-    if (diag && threadIdx.x < TS) sg[threadIdx.x] = w.g[I * TS + threadIdx.x];
+    if (diag && threadIdx.x < TS) sg[threadIdx.x] = __ldcg(w.g + I * TS + threadIdx.x);
     __syncthreads();
-    mixed::tile_epilogue<STAGE>(ops, w, I, J, pidx, sX1, sX2, sg, sO);
-    if (STAGE == 1) stage1_last_decides(w, nparts);
+    mixed::tile_epilogue_in<STAGE, kENT>(ops, w, I, J, pidx, sX1, sX2, sg, sO, in);
+    if (STAGE == 1 && TICKET) stage1_last_decides(w, nparts);
     if (STAGE == 4 && first && threadIdx.x == 0) w.ctl->step += 1;
 }
 

@@ -286,8 +286,10 @@ __device__ __forceinline__ void gain_rows(const DevOps &ops, const float *__rest
     __shared__ float red[32];
     const int n = ops.n, np = ops.np;
     float P = 0.f, Dd = 0.f;
+    // __ldcg: the diagonal may have been written by another CTA of the same
+    // (persistent) launch, so it is read from L2
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const float pj = din[(size_t)j * np + j];
+        const float pj = __ldcg(din + (size_t)j * np + j);
         P = __fadd_rn(P, pj);
         if (ops.dang[j]) Dd = __fadd_rn(Dd, pj);
     }
@@ -301,14 +303,14 @@ __device__ __forceinline__ void gain_rows(const DevOps &ops, const float *__rest
 #pragma unroll 4
             for (int q = ops.s_ptr[i] + lane; q < q1; q += 32) {
                 const int j = ops.s_col[q];
-                s = __fmaf_rn(ops.s_val32[q], din[(size_t)j * np + j], s);
+                s = __fmaf_rn(ops.s_val32[q], __ldcg(din + (size_t)j * np + j), s);
             }
         }
         s = warp_sum_f(s);
         if (lane == 0) {
             float gi = 0.f;
             if (i < n) {
-                const float pi = din[(size_t)i * np + i];
+                const float pi = __ldcg(din + (size_t)i * np + i);
                 const float dterm = (ops.dangling == QPR_DANGLING_F)
                                         ? __fmul_rn(__fsub_rn(Dd, ops.dang[i] ? pi : 0.f), ops.inv_nm1_32)
                                         : __fmul_rn(Dd, ops.inv_n32);
@@ -354,20 +356,72 @@ __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
     return s_status != kCtlRunning;
 }
 
-// Epilogue of one tile pair (I, J) of stage STAGE from the products
-// sX1 = X_IJ and (unless I == J) sX2 = X_JI of X = H delta, [a][LDX] rows
-// (real part, then imaginary part), and, on a diagonal pair, the gain of
-// its rows in sg. Writes tile (I, J) and its conjugate mirror (J, I); stage
-// 1 leaves this pair's residual-estimate partial in partials32[pidx].
-// sO32: 4 * TS * LDO floats of shared memory. Ends with a barrier.
-template <int STAGE>
-__device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
-                                              const float *sX1, const float *sX2, const float *sg, float *sO32) {
-    __shared__ float red[NT / 32];
-    const bool diag = (I == J);
+// Operands of one thread's elements e = tid + k NTH (k < K) of tile (I, J)
+// of stage STAGE, loaded into registers ahead of the products (one round
+// trip to memory for the whole epilogue): the stage input d; stages 1-3: F32
+// (u), D (v), S (s, stages 2-3); stage 4: S (u), D (v), Dlo (s), Ghi (g), Glo
+// (l); and c32 of the element's row (ca) and column (cb).
+template <int STAGE, int NTH>
+struct EpiIn {
+    static constexpr int K = TS * TS / NTH;
+    float dr[K], di[K], ur[K], ui[K], vr[K], vi[K], sr[K], si[K], gr[K], gi[K], lr[K], li[K], ca[K];
+    float cb;
+};
+
+template <int STAGE, int NTH>
+__device__ __forceinline__ void epi_load(const DevOps &ops, const MixedWork &w, int I, int J, EpiIn<STAGE, NTH> &in) {
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < EpiIn<STAGE, NTH>::K; ++k) {
+        const int e = tid + k * NTH;
+        const int a = e / TS, b = e - (e / TS) * TS;
+        const size_t off = (size_t)(I * TS + a) * np + J * TS + b;
+        in.dr[k] = din[off];
+        in.di[k] = din[plane + off];
+        if (STAGE <= 3) {
+            in.ur[k] = w.F32[off];
+            in.ui[k] = w.F32[plane + off];
+            in.vr[k] = w.D[off];
+            in.vi[k] = w.D[plane + off];
+            if (STAGE >= 2) {
+                in.sr[k] = w.S[off];
+                in.si[k] = w.S[plane + off];
+            }
+        } else {
+            in.ur[k] = w.S[off];
+            in.ui[k] = w.S[plane + off];
+            in.vr[k] = w.D[off];
+            in.vi[k] = w.D[plane + off];
+            in.sr[k] = w.Dlo[off];
+            in.si[k] = w.Dlo[plane + off];
+            in.gr[k] = w.Ghi[off];
+            in.gi[k] = w.Ghi[plane + off];
+            in.lr[k] = w.Glo[off];
+            in.li[k] = w.Glo[plane + off];
+        }
+        in.ca[k] = ops.c32[I * TS + a];
+    }
+    in.cb = ops.c32[J * TS + (tid % TS)];  // the column of every element of this thread
+}
+
+// Epilogue of one tile pair (I, J) of stage STAGE from the products
+// sX1 = X_IJ and (unless I == J) sX2 = X_JI of X = H delta, [a][LDX] rows
+// (real part, then imaginary part), and, on a diagonal pair, the gain of
+// its rows in sg, with the operands `in` loaded by epi_load. Writes tile
+// (I, J) and its conjugate mirror (J, I); stage 1 leaves this pair's
+// residual-estimate partial in partials32[pidx]. sO32: 4 * TS * LDO floats
+// of shared memory; NTH threads. Ends with a barrier.
+template <int STAGE, int NTH>
+__device__ __forceinline__ void tile_epilogue_in(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                 const float *sX1, const float *sX2, const float *sg, float *sO32,
+                                                 const EpiIn<STAGE, NTH> &in) {
+    __shared__ float red[NTH / 32];
+    const bool diag = (I == J);
+    const int np = ops.np;
+    const size_t plane = (size_t)np * np;
     float *dnext = (STAGE == 2) ? w.db : w.da;
     const float *X2 = diag ? sX1 : sX2;
 
@@ -376,42 +430,44 @@ __device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float nrm = 0.f;  // this thread's share of ||k1||^2 (an FP32-accurate estimate)
 #pragma unroll
-    for (int e = tid; e < TS * TS; e += NT) {
+    for (int k = 0; k < EpiIn<STAGE, NTH>::K; ++k) {
+        const int e = tid + k * NTH;
         const int a = e / TS, b = e - (e / TS) * TS;
         const int ga = I * TS + a, gb = J * TS + b;
         const size_t off = (size_t)ga * np + gb;
         const float Aab = sX1[a * LDX + b], Bab = sX1[a * LDX + TS + b];
         const float Aba = X2[b * LDX + a], Bba = X2[b * LDX + TS + a];
-        const float dr = din[off], di = din[plane + off];
+        const float dr = in.dr[k], di = in.di[k];
         // kd = f(delta) in FP32; k = F + kd. Explicit round-to-nearest
         // intrinsics: the same rounding in every kernel inlining this code.
-        const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(ops.c32[ga], ops.c32[gb])));
+        const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(in.ca[k], in.cb)));
         float kdr = __fmaf_rn(-omhc, dr, __fmul_rn(cm, __fadd_rn(Bab, Bba)));
         const float kdi = __fmaf_rn(-omhc, di, __fmul_rn(-cm, __fsub_rn(Aab, Aba)));
         if (ga == gb) kdr = __fmaf_rn(om, sg[a], kdr);
         if (STAGE <= 3) {
-            const float kr = __fadd_rn(kdr, w.F32[off]), ki = __fadd_rn(kdi, w.F32[plane + off]);
+            const float kr = __fadd_rn(kdr, in.ur[k]), ki = __fadd_rn(kdi, in.ui[k]);
             if (STAGE == 1) nrm = __fmaf_rn(kr, kr, __fmaf_rn(ki, ki, nrm));
-            const float Dr = w.D[off], Di = w.D[plane + off];
+            const float Dr = in.vr[k], Di = in.vi[k];
             float sr, si;
             if (STAGE == 1) { sr = kdr; si = kdi; }
-            else { sr = __fmaf_rn(2.0f, kdr, w.S[off]); si = __fmaf_rn(2.0f, kdi, w.S[plane + off]); }
+            else { sr = __fmaf_rn(2.0f, kdr, in.sr[k]); si = __fmaf_rn(2.0f, kdi, in.si[k]); }
             const float cst = (STAGE == 3) ? dtf : __fmul_rn(0.5f, dtf);
             const float nr = __fmaf_rn(cst, kr, Dr), ni = __fmaf_rn(cst, ki, Di);
             w.S[off] = sr; w.S[plane + off] = si;
             dnext[off] = nr; dnext[plane + off] = ni;
+            if (ga == gb && w.pv) w.pv[ga] = nr;
             sO32[0 * TS * LDO + a * LDO + b] = sr;
             sO32[1 * TS * LDO + a * LDO + b] = si;
             sO32[2 * TS * LDO + a * LDO + b] = nr;
             sO32[3 * TS * LDO + a * LDO + b] = ni;
         } else {
             // delta += dt F + dt/6 (S + kd4) in float-float
-            const float sr = __fadd_rn(w.S[off], kdr), si = __fadd_rn(w.S[plane + off], kdi);
-            const ff vr = delta_update(w.D[off], w.Dlo[off], w.Ghi[off], w.Glo[off], dt6h, dt6l, sr);
-            const ff vi = delta_update(w.D[plane + off], w.Dlo[plane + off], w.Ghi[plane + off], w.Glo[plane + off],
-                                       dt6h, dt6l, si);
+            const float sr = __fadd_rn(in.ur[k], kdr), si = __fadd_rn(in.ui[k], kdi);
+            const ff vr = delta_update(in.vr[k], in.sr[k], in.gr[k], in.lr[k], dt6h, dt6l, sr);
+            const ff vi = delta_update(in.vi[k], in.si[k], in.gi[k], in.li[k], dt6h, dt6l, si);
             w.D[off] = vr.hi; w.D[plane + off] = vi.hi;
             w.Dlo[off] = vr.lo; w.Dlo[plane + off] = vi.lo;
+            if (ga == gb && w.pv) w.pv[ga] = vr.hi;
             sO32[0 * TS * LDO + a * LDO + b] = vr.hi;
             sO32[1 * TS * LDO + a * LDO + b] = vi.hi;
             sO32[2 * TS * LDO + a * LDO + b] = vr.lo;
@@ -424,13 +480,13 @@ __device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork
         __syncthreads();
         if (tid == 0) {
             float s = 0.f;
-            for (int q = 0; q < NT / 32; ++q) s = __fadd_rn(s, red[q]);
+            for (int q = 0; q < NTH / 32; ++q) s = __fadd_rn(s, red[q]);
             w.partials32[pidx] = diag ? s : __fmul_rn(2.0f, s);
         }
     }
     if (!diag) {
         __syncthreads();
-        for (int e = tid; e < TS * TS; e += NT) {
+        for (int e = tid; e < TS * TS; e += NTH) {
             const int b = e / TS, a = e - (e / TS) * TS;
             const size_t off = (size_t)(J * TS + b) * np + I * TS + a;
             if (STAGE <= 3) {
@@ -447,6 +503,15 @@ __device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork
         }
     }
     __syncthreads();
+}
+
+// The same with the operands loaded here.
+template <int STAGE, int NTH = NT>
+__device__ __forceinline__ void tile_epilogue(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                              const float *sX1, const float *sX2, const float *sg, float *sO32) {
+    EpiIn<STAGE, NTH> in;
+    epi_load<STAGE, NTH>(ops, w, I, J, in);
+    tile_epilogue_in<STAGE, NTH>(ops, w, I, J, pidx, sX1, sX2, sg, sO32, in);
 }
 
 // One tile pair (I, J) of stage STAGE of the sparse mixed form: products
@@ -528,6 +593,8 @@ __device__ __forceinline__ void refresh_normalize_body(const DevOps &ops, const 
         w.D[i] = 0.0f;
         w.Dlo[i] = 0.0f;
     }
+    if (w.pv)
+        for (size_t i = i0; i < (size_t)ops.np; i += stride) w.pv[i] = 0.0f;
     if (w.splitD) {
         const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
         for (size_t i = i0; i < 3 * tot; i += stride) w.splitD[i] = z;

@@ -50,6 +50,8 @@ struct qpr_ctx {
     int4 *d_colpieces = nullptr;
     float *d_X = nullptr;
     qpr::ColMaps colmaps{};
+    int persist_grid = 0;       // > 0: the persistent column-block form, CTAs per launch
+    int persist_smem = 0, epi_off = 0;
     qpr::MixedWork mw{};
     double *d_g = nullptr;
     double *d_partials = nullptr;
@@ -228,6 +230,18 @@ qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     return QPR_OK;
 }
 
+// One block of the mixed form: the exact refresh, then `steps` delta steps
+// (one persistent launch, or the kernels of every stage).
+qpr_status launch_mixed_block(qpr_ctx *ctx, int steps) {
+    qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+    if (ctx->persist_grid > 0) {
+        QPR_CUDA(ctx, qpr::launch_cols_block(ctx->ops, ctx->mw, steps, ctx->persist_grid, ctx->stream));
+        ctx->launches += qpr::kMixedLaunchesPerRefresh + 1;
+        return QPR_OK;
+    }
+    return QPR_OK;
+}
+
 int mixed_launches_per_step(const qpr_ctx *ctx) {
     if (ctx->mw.cmaps) return qpr::kMixedLaunchesPerStepCols;
     return (ctx->mw.splitD ? 2 : 1) * qpr::kMixedLaunchesPerStep;
@@ -240,7 +254,7 @@ void enqueue_mixed_block(qpr_ctx *ctx, int steps) {
 }
 
 qpr_status ensure_mixed_graph(qpr_ctx *ctx) {
-    if (ctx->graph || ctx->opt.graph_steps <= 0) return QPR_OK;
+    if (ctx->graph || ctx->opt.graph_steps <= 0 || ctx->persist_grid > 0) return QPR_OK;
     cudaGraph_t g = nullptr;
     QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     enqueue_mixed_block(ctx, ctx->opt.ref_refresh);
@@ -278,12 +292,17 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     if (st != QPR_OK) return st;
     const int block = ctx->opt.ref_refresh;
     for (;;) {
-        if (ctx->graph) {
-            QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+        if (ctx->persist_grid > 0) {
+            st = launch_mixed_block(ctx, block);
+            if (st != QPR_OK) return st;
         } else {
-            enqueue_mixed_block(ctx, block);
+            if (ctx->graph) {
+                QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+            } else {
+                enqueue_mixed_block(ctx, block);
+            }
+            ctx->launches += qpr::kMixedLaunchesPerRefresh + mixed_launches_per_step(ctx) * (int64_t)block;
         }
-        ctx->launches += qpr::kMixedLaunchesPerRefresh + mixed_launches_per_step(ctx) * (int64_t)block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
         if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
@@ -516,6 +535,12 @@ const char *qpr_last_error(const qpr_ctx *ctx) {
 
 int64_t qpr_n(const qpr_ctx *ctx) { return ctx ? ctx->n : 0; }
 int32_t qpr_backend(const qpr_ctx *ctx) { return ctx ? ctx->backend : 0; }
+
+int32_t qpr_sparse_form(const qpr_ctx *ctx) {
+    if (!ctx || ctx->opt.precision != QPR_MIXED || ctx->mw.splitD) return 0;
+    if (!ctx->mw.cmaps) return QPR_SPARSE_FORM_TILES;
+    return ctx->persist_grid > 0 ? QPR_SPARSE_FORM_COLUMNS_PERSISTENT : QPR_SPARSE_FORM_COLUMNS;
+}
 double qpr_h_spread(const qpr_ctx *ctx) { return ctx ? ctx->spread : 0.0; }
 
 double qpr_max_stable_dt(const qpr_ctx *ctx) {
@@ -528,6 +553,7 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (!ctx) return;
     DeviceGuard dg(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->colmaps.side) cudaStreamSynchronize(ctx->colmaps.side);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_hptr);
@@ -563,6 +589,9 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_p);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
+    if (ctx->colmaps.fork) cudaEventDestroy(ctx->colmaps.fork);
+    if (ctx->colmaps.join) cudaEventDestroy(ctx->colmaps.join);
+    if (ctx->colmaps.side) cudaStreamDestroy(ctx->colmaps.side);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
@@ -597,7 +626,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
     if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
-    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_TILES)
+    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_COLUMNS_PERSISTENT)
         return arg_err(QPR_E_ARG, "unknown sparse_form");
     HostOps hops;
     {
@@ -758,7 +787,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         CREATE_CUDA(cudaMemset(ctx->d_mix64, 0, 4 * plane * sizeof(double)));
         CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 16 * plane * sizeof(float)));
         CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 16 * plane * sizeof(float)));
-        CREATE_CUDA(cudaMalloc(&ctx->d_g32, np * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_g32, 2 * np * sizeof(float)));  // g, then the diagonal vector pv
+        CREATE_CUDA(cudaMemset(ctx->d_g32, 0, 2 * np * sizeof(float)));
         CREATE_CUDA(cudaMalloc(&ctx->d_partials32, std::max<size_t>(pairs.size(), (size_t)npairs_tc) * sizeof(float)));
         std::vector<float> sv32(std::max<size_t>(1, sval.size()));
         for (size_t q = 0; q < sval.size(); ++q) sv32[q] = (float)sval[q];
@@ -768,7 +798,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     qpr::ColPlan cplan;
     const bool cols = (o.precision == QPR_MIXED) && !tc && o.sparse_form != QPR_SPARSE_FORM_TILES &&
                       qpr::plan_columns(hops, np, ctx->device, cplan);
-    if (o.precision == QPR_MIXED && !tc && o.sparse_form == QPR_SPARSE_FORM_COLUMNS && !cols) {
+    if (o.precision == QPR_MIXED && !tc && !cols &&
+        (o.sparse_form == QPR_SPARSE_FORM_COLUMNS || o.sparse_form == QPR_SPARSE_FORM_COLUMNS_PERSISTENT)) {
         ctx->err = "sparse_form COLUMNS: the staged operands of N = " + std::to_string(n) +
                    " do not fit one CTA's shared memory";
         return bail(QPR_E_ARG);
@@ -788,6 +819,14 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
                                cudaMemcpyHostToDevice));
         CREATE_CUDA(cudaMalloc(&ctx->d_X, 2 * plane * sizeof(float)));
         CREATE_CUDA(cudaMemset(ctx->d_X, 0, 2 * plane * sizeof(float)));
+        if (o.sparse_form == QPR_SPARSE_FORM_COLUMNS_PERSISTENT) {
+            ctx->persist_grid =
+                qpr::persist_grid(np, cplan.splits, cplan.smem, ctx->device, &ctx->persist_smem, &ctx->epi_off);
+            if (ctx->persist_grid <= 0) {
+                ctx->err = "sparse_form COLUMNS_PERSISTENT: no cooperative launch of the block kernel fits";
+                return bail(QPR_E_ARG);
+            }
+        }
     }
     CREATE_CUDA(cudaMalloc(&ctx->d_ctl, sizeof(Ctl)));
     CREATE_CUDA(cudaMemset(ctx->d_ctl, 0, sizeof(Ctl)));
@@ -856,6 +895,9 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
             ops.col_splits = cplan.splits;
             ops.col_smem = cplan.smem;
             ops.col_p_off = cplan.p_off;
+            ops.col_sp_off = cplan.sp_off;
+            ops.col_epi_off = ctx->epi_off;
+            ops.col_psmem = ctx->persist_smem;
             mw.X = ctx->d_X;
             const float *din[3] = {mw.D, mw.da, mw.db};
             if (!qpr::make_col_maps(ops, din, &ctx->colmaps)) {
@@ -864,9 +906,22 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
                 qpr_destroy(ctx);
                 return QPR_E_CUDA;
             }
+            if (cudaStreamCreateWithFlags(&ctx->colmaps.side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->colmaps.fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->colmaps.join, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->err = "stream or event creation failed";
+                g_create_error = ctx->err;
+                qpr_destroy(ctx);
+                return QPR_E_CUDA;
+            }
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+            ctx->colmaps.gain_ctas = std::min(64, std::max(8, sms - (np / 16) * cplan.splits));
             mw.cmaps = &ctx->colmaps;
         }
         mw.g = ctx->d_g32;
+        mw.pv = ctx->d_g32 + np;
         mw.g64 = ctx->d_g;
         mw.partials = ctx->d_partials;
         mw.pairs = ctx->d_pairs;

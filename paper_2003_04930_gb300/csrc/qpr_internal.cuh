@@ -38,6 +38,8 @@ struct Ctl {
     // FP32 forms of dt for the mixed form's delta stages, written by its
     // refresh: dtf = fl(dt) and dt / 6 = dt6h + dt6l as a float-float pair
     float dtf, dt6h, dt6l, pad2_;
+    // grid barrier of the persistent column-block kernel: arrivals, generation
+    unsigned gb_count, gb_gen;
 };
 
 // kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
@@ -71,9 +73,10 @@ struct DevOps {
     const float *s_val32;
     float alpha32, oma32, omega32, inv_nm1_32, inv_n32;
     // column-block form of the sparse mixed stage (plan of ColPlan; 0 splits:
-    // not used): the CSR of H packed as (column, FP32 value bits); per row
-    // split its entry range {first (even), end} and bundle range; bundles of
-    // 4 row pieces {row, q0, len, flags}; per (split, warp) the first bundle
+    // not used): the entries of H as (column, FP32 value bits), per bundle
+    // interleaved and zero-padded; per row split its entry range {first
+    // (even), end} and bundle range; bundle descriptors (2 int4 each); per
+    // (split, warp) the first bundle
     const int2 *col_kh;
     const int *col_q;      // 2 per split
     const int *col_sb;     // splits + 1: bundles of split r are [col_sb[r], col_sb[r + 1])
@@ -82,6 +85,9 @@ struct DevOps {
     int col_splits;
     int col_smem;          // dynamic shared memory of the SpMM kernel
     int col_p_off;         // byte offset of the staged bundles in it
+    int col_sp_off;        // byte offset of the staged diagonal (np floats) in it
+    int col_epi_off;       // persistent form: byte offset of the epilogue buffers (0: over the column block)
+    int col_psmem;         // persistent form: dynamic shared memory of its launch
 };
 
 // RK4 work buffers. Every state buffer holds two np x np FP64 planes,
@@ -109,6 +115,7 @@ struct MixedWork {
     double *R, *F;
     float *F32, *D, *Dlo, *da, *db, *S, *Ghi, *Glo;
     float *g;             // gain of the stage delta, np
+    float *pv;            // np: diagonal of the next stage input (written by every epilogue, zeroed by a refresh)
     double *g64;          // FP64 gain used by the refresh, np
     double *partials;     // exact residual partials of the refresh
     float *partials32;    // residual-estimate partials of the stage-1 kernel
@@ -135,6 +142,10 @@ struct MixedWork {
 // each pair of planes seen as 2 np rows of np FP32, boxes of 8 x 256.
 struct ColMaps {
     CUtensorMap d[3];
+    // host side: the gain kernel runs on a forked branch beside the SpMM
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+    int gain_ctas;
 };
 
 constexpr int kTileTc = 128;
@@ -196,10 +207,11 @@ struct ColPlan {
     int splits = 0;
     int smem = 0;                 // dynamic shared memory per CTA
     int p_off = 0;                // byte offset of the staged bundles
-    std::vector<int2> kh;         // packed CSR, padded by 2 entries
+    int sp_off = 0;               // byte offset of the staged diagonal
+    std::vector<int2> kh;         // entries of the bundles, interleaved and padded
     std::vector<int> q;           // 2 per split
     std::vector<int> sb;          // splits + 1
-    std::vector<int4> pieces;     // 4 per bundle
+    std::vector<int4> pieces;     // 2 per bundle
     std::vector<int> wb;          // splits * 16 + 1
 };
 // Plans the column-block form of an np x np problem on `device`; false if
@@ -208,6 +220,15 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan);
 // Opt in to `bytes` of dynamic shared memory for the SpMM kernels.
 cudaError_t set_cols_smem(int bytes);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+// Persistent form (stage_persist.cu): one cooperative launch runs up to
+// `steps` RK4 steps of the column-block form, grid barriers between the
+// phases. persist_grid: CTAs of that launch for an np x np problem with the
+// given plan on `device` (0: the form does not apply).
+// On success also the launch's dynamic shared memory and the offset of the
+// epilogue buffers in it.
+int persist_grid(int np, int splits, int smem, int device, int *persist_smem, int *epi_off);
+cudaError_t set_persist_smem(int bytes);
+cudaError_t launch_cols_block(const DevOps &ops, const MixedWork &w, int steps, int grid, cudaStream_t s);
 // Kernel launches per RK4 step and per refresh of the mixed form.
 constexpr int kMixedLaunchesPerStep = 4;   // tile-pair sparse kernel (the dense one adds 4 gain kernels)
 constexpr int kMixedLaunchesPerStepCols = 8;  // column-block form: SpMM + epilogue per stage

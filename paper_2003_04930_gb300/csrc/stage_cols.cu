@@ -49,16 +49,14 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
     const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
     const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
     if (tid == 0) {
-        const uint32_t kh_bytes = (uint32_t)(((q_end - q_base) * 8 + 15) / 16 * 16);
-        const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 64);
+        const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
+        const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 32);
         tma::mbar_expect_tx(&bar, (uint32_t)np * kRowFloats * 4 + kh_bytes + p_bytes);
         for (int b = 0; b < np; b += kBoxRows)
             tma::load_3d(sD + (size_t)b * kRowFloats, &tm, &bar, J * kCW, 0, b);
         if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
-        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 4 * (size_t)p_base, p_bytes, &bar);
+        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar);
     }
-    // while the operands are in flight: a share of the gain
-    cta_gain(ops, w, stage_input<STAGE>(w), r * gridDim.x + J, gridDim.x * gridDim.y);
     const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
     const bool ok = tma::mbar_wait(&bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -67,11 +65,22 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
         tma::mbar_wait(&bar, 0);
         return;
     }
-    warp_bundles(sD, sKH, sP, q_base, p_base, wb0, wb1, J, np, w.X);
+    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X);
+}
+
+// The gain of the stage input, rows shared over the grid; runs beside the
+// SpMM kernel (on SMs it leaves free).
+__global__ void __launch_bounds__(kANT) cols_gain_kernel(DevOps ops, MixedWork w) {
+    extern __shared__ float sp_dyn[];
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    if (s_done) return;
+    cta_gain(ops, w, blockIdx.x, gridDim.x, sp_dyn);
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(NT) cols_epi_kernel(DevOps ops, MixedWork w) {
+__global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork w) {
     __shared__ __align__(16) float sX1[TS * LDX];
     __shared__ __align__(16) float sX2[TS * LDX];
     __shared__ __align__(16) float sO[4 * TS * LDO];
@@ -99,26 +108,32 @@ cudaError_t set_spmm_attr(int bytes) {
 }
 
 // Bundles of one split's rows [r0, r1): long rows alone, the others 4 at a
-// time by decreasing length; then dealt to the warps longest first, each to
-// the least loaded warp. Appends the pieces and the warps' first bundles.
-void split_bundles(const HostOps &h, int r0, int r1, int n, std::vector<int4> &pieces, std::vector<int> &wb) {
+// time by decreasing length; dealt to the warps longest first, each to the
+// least loaded warp. Appends, per warp, the bundles' descriptors and their
+// interleaved, zero-padded entries (relative offsets from `kh_base`), and
+// the warps' first bundles.
+void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std::vector<int2> &kh,
+                   std::vector<int4> &pieces, std::vector<int> &wb) {
     struct Bundle {
-        int4 p[4];
+        int rows[4];
+        int T;
+        bool lng;
         long long cost;
     };
     std::vector<Bundle> bs;
     std::vector<int> shortrows;
     auto row_len = [&](int i) { return i < n ? (int)(h.hptr[i + 1] - h.hptr[i]) : 0; };
-    auto row_q0 = [&](int i) { return i < n ? (int)h.hptr[i] : (int)h.hptr[n]; };
-    const int4 empty = make_int4(-1, 0, 0, 0);
+    auto entry = [&](int i, int e) {
+        const size_t q = (size_t)h.hptr[i] + e;
+        const float v = (float)h.hval[q];
+        int bits;
+        memcpy(&bits, &v, 4);
+        return make_int2(h.hcol[q], bits);
+    };
     for (int i = r0; i < r1; ++i) {
-        const int len = row_len(i);
-        if (len > kLongRow) {
-            const int T = (len + 3) / 4;
-            Bundle b;
-            b.p[0] = make_int4(i, row_q0(i), len, kPieceLong | (T << 1));
-            b.p[1] = b.p[2] = b.p[3] = empty;
-            b.cost = T + 8;
+        if (row_len(i) > kLongRow) {
+            Bundle b{{i, -1, -1, -1}, (row_len(i) + 3) / 4, true, 0};
+            b.cost = b.T + 8;
             bs.push_back(b);
         } else {
             shortrows.push_back(i);
@@ -126,18 +141,10 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, std::vector<int4> &p
     }
     std::stable_sort(shortrows.begin(), shortrows.end(), [&](int a, int b) { return row_len(a) > row_len(b); });
     for (size_t k = 0; k < shortrows.size(); k += 4) {
-        Bundle b;
-        const int T = row_len(shortrows[k]);
-        for (int j = 0; j < 4; ++j) {
-            if (k + j < shortrows.size()) {
-                const int i = shortrows[k + j];
-                b.p[j] = make_int4(i, row_q0(i), row_len(i), 0);
-            } else {
-                b.p[j] = empty;
-            }
-        }
-        b.p[0].w = T << 1;
-        b.cost = T + 8;
+        Bundle b{{-1, -1, -1, -1}, row_len(shortrows[k]), false, 0};
+        for (int j = 0; j < 4; ++j)
+            if (k + j < shortrows.size()) b.rows[j] = shortrows[k + j];
+        b.cost = b.T + 8;
         bs.push_back(b);
     }
     std::stable_sort(bs.begin(), bs.end(), [](const Bundle &a, const Bundle &b) { return a.cost > b.cost; });
@@ -149,9 +156,22 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, std::vector<int4> &p
         load[wmin] += bs[k].cost;
     }
     for (int wi = 0; wi < kAWarps; ++wi) {
-        wb.push_back((int)(pieces.size() / 4));
-        for (int k : per[wi])
-            for (int j = 0; j < 4; ++j) pieces.push_back(bs[k].p[j]);
+        wb.push_back((int)(pieces.size() / 2));
+        for (int k : per[wi]) {
+            const Bundle &b = bs[k];
+            pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T, b.lng ? kPieceLong : 0, 0));
+            pieces.push_back(make_int4(b.rows[0], b.rows[1], b.rows[2], b.rows[3]));
+            for (int t = 0; t < b.T; ++t)
+                for (int g = 0; g < 4; ++g) {
+                    int2 v = make_int2(0, 0);
+                    if (b.lng) {
+                        if (4 * t + g < row_len(b.rows[0])) v = entry(b.rows[0], 4 * t + g);
+                    } else if (b.rows[g] >= 0 && t < row_len(b.rows[g])) {
+                        v = entry(b.rows[g], t);
+                    }
+                    kh.push_back(v);
+                }
+        }
     }
 }
 
@@ -173,7 +193,7 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan) {
         const double nz = (i < n) ? (double)(h.hptr[i + 1] - h.hptr[i]) : 0.0;
         cum[i + 1] = cum[i] + nz + 4.0;
     }
-    for (int s = std::max(1, sms / ncb); s <= 16; ++s) {
+    for (int s = std::min(std::max(1, sms / ncb), 16); s <= 16; ++s) {
         ColPlan pl;
         pl.splits = s;
         std::vector<int> rows(s + 1, 0);
@@ -186,32 +206,26 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan) {
         rows[s] = np;
         size_t kh_max = 0, p_max = 0;
         for (int k = 0; k < s; ++k) {
-            const int qs = (int)h.hptr[std::min(rows[k], n)], qe = (int)h.hptr[std::min(rows[k + 1], n)];
-            const int qs_even = qs & ~1;
-            pl.q.push_back(qs_even);
-            pl.q.push_back(qe);
-            kh_max = std::max(kh_max, (size_t)((qe - qs_even) * 8 + 15) / 16 * 16);
-            const int first = (int)(pl.pieces.size() / 4);
+            const size_t kb = pl.kh.size();  // even: every split's block starts 16-byte aligned
+            const int first = (int)(pl.pieces.size() / 2);
             pl.sb.push_back(first);
-            split_bundles(h, rows[k], rows[k + 1], n, pl.pieces, pl.wb);
-            p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / 4) - first) * 64);
+            split_bundles(h, rows[k], rows[k + 1], n, kb, pl.kh, pl.pieces, pl.wb);
+            if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
+            pl.q.push_back((int)kb);
+            pl.q.push_back((int)pl.kh.size());
+            kh_max = std::max(kh_max, (pl.kh.size() - kb) * 8);
+            p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / 2) - first) * 32);
         }
-        pl.sb.push_back((int)(pl.pieces.size() / 4));
-        pl.wb.push_back((int)(pl.pieces.size() / 4));
+        pl.sb.push_back((int)(pl.pieces.size() / 2));
+        pl.wb.push_back((int)(pl.pieces.size() / 2));
         pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
-        const size_t smem = (size_t)pl.p_off + p_max + 128;
+        pl.sp_off = (int)((size_t)pl.p_off + p_max);
+        const size_t smem = (size_t)pl.sp_off + (size_t)np * 4 + 128;
         // 1 KB left for the static shared memory of the kernels (the batched
         // kernel keeps its problem descriptor there)
         if (smem_max > 1024 && smem <= (size_t)smem_max - 1024) {
             pl.smem = (int)smem;
-            pl.kh.resize(h.hval.size() + 2);
-            for (size_t q = 0; q < h.hval.size(); ++q) {
-                const float v = (float)h.hval[q];
-                int bits;
-                memcpy(&bits, &v, 4);
-                pl.kh[q] = make_int2(h.hcol[q], bits);
-            }
-            pl.kh[h.hval.size()] = pl.kh[h.hval.size() + 1] = make_int2(0, 0);
+            if (pl.kh.empty()) pl.kh.assign(2, make_int2(0, 0));
             plan = std::move(pl);
             return true;
         }
@@ -252,19 +266,25 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
     const dim3 ga(ops.np / kCW, ops.col_splits);
     const size_t sm = (size_t)ops.col_smem;
     if (parts & 1) {
+        // fork: the gain on the side stream, the SpMM here; join before the epilogue
+        cudaEventRecord(m.fork, s);
+        cudaStreamWaitEvent(m.side, m.fork, 0);
+        cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
+        cudaEventRecord(m.join, m.side);
         switch (stage) {
             case 1: cols_spmm_kernel<1><<<ga, kANT, sm, s>>>(m.d[0], ops, w); break;
             case 2: cols_spmm_kernel<2><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
             case 3: cols_spmm_kernel<3><<<ga, kANT, sm, s>>>(m.d[2], ops, w); break;
             default: cols_spmm_kernel<4><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
         }
+        cudaStreamWaitEvent(s, m.join, 0);
     }
     if (parts & 2) {
         switch (stage) {
-            case 1: cols_epi_kernel<1><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            case 2: cols_epi_kernel<2><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            case 3: cols_epi_kernel<3><<<w.npairs, NT, 0, s>>>(ops, w); break;
-            default: cols_epi_kernel<4><<<w.npairs, NT, 0, s>>>(ops, w); break;
+            case 1: cols_epi_kernel<1><<<w.npairs, kENT, 0, s>>>(ops, w); break;
+            case 2: cols_epi_kernel<2><<<w.npairs, kENT, 0, s>>>(ops, w); break;
+            case 3: cols_epi_kernel<3><<<w.npairs, kENT, 0, s>>>(ops, w); break;
+            default: cols_epi_kernel<4><<<w.npairs, kENT, 0, s>>>(ops, w); break;
         }
     }
 }

@@ -22,12 +22,12 @@ QPR_FP64, QPR_MIXED = 0, 1
 QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
 QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
-QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES = 0, 1, 2
+QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES, QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 0, 1, 2, 3
 
 # every entry point declared in include/qpr.h
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
-    "qpr_n", "qpr_backend", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
+    "qpr_n", "qpr_backend", "qpr_sparse_form", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
     "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune",
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_n.restype = i64
     lib.qpr_backend.argtypes = [vp]
     lib.qpr_backend.restype = ctypes.c_int32
+    lib.qpr_sparse_form.argtypes = [vp]
+    lib.qpr_sparse_form.restype = ctypes.c_int32
     lib.qpr_h_spread.argtypes = [vp]
     lib.qpr_h_spread.restype = f64
     lib.qpr_max_stable_dt.argtypes = [vp]
@@ -234,6 +236,12 @@ class Solver:
     @property
     def backend(self) -> int:
         return int(self._lib.qpr_backend(self._h))
+
+    @property
+    def sparse_form(self) -> int:
+        """QPR_SPARSE_FORM_COLUMNS, _COLUMNS_PERSISTENT or _TILES (0: not the
+        mixed sparse form)."""
+        return int(self._lib.qpr_sparse_form(self._h))
 
     @property
     def h_spread(self) -> float:
