@@ -187,16 +187,13 @@ __device__ __forceinline__ void stage1_last_decides(const MixedWork &w, int npar
 // stage 4 advances the step counter (first pair). kENT threads. Shared
 // memory: sX1, sX2 (TS * LDX floats each), sg (TS), sO (4 * TS * LDO).
 template <int STAGE, bool TICKET = true>
-__device__ __forceinline__ void epilogue_pair(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
-                                              bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO) {
+__device__ __forceinline__ void epilogue_pair_in(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                 bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO,
+                                                 const mixed::EpiIn<STAGE, kENT> &in) {
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const bool diag = (I == J);
     const int ntiles = diag ? 1 : 2;
-    // the elementwise operands first, so that their loads and the X tiles'
-    // are in flight together
-    mixed::EpiIn<STAGE, kENT> in;
-    mixed::epi_load<STAGE, kENT>(ops, w, I, J, in);
     // X tiles as [a][LDX] rows (real part, then imaginary part), float4 loads
     for (int t = threadIdx.x; t < ntiles * TS * (2 * TS / 4); t += kENT) {
         const int which = t / (TS * (2 * TS / 4));
@@ -216,6 +213,16 @@ __device__ __forceinline__ void epilogue_pair(const DevOps &ops, const MixedWork
     mixed::tile_epilogue_in<STAGE, kENT>(ops, w, I, J, pidx, sX1, sX2, sg, sO, in);
     if (STAGE == 1 && TICKET) stage1_last_decides(w, nparts);
     if (STAGE == 4 && first && threadIdx.x == 0) w.ctl->step += 1;
+}
+
+// The same with the elementwise operands loaded first, so that their loads
+// and the X tiles' are in flight together.
+template <int STAGE, bool TICKET = true>
+__device__ __forceinline__ void epilogue_pair(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                              bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO) {
+    mixed::EpiIn<STAGE, kENT> in;
+    mixed::epi_load<STAGE, kENT>(ops, w, I, J, in);
+    epilogue_pair_in<STAGE, TICKET>(ops, w, I, J, pidx, first, nparts, sX1, sX2, sg, sO, in);
 }
 
 }  // namespace cols

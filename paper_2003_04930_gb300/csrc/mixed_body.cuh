@@ -374,33 +374,35 @@ __device__ __forceinline__ void epi_load(const DevOps &ops, const MixedWork &w, 
     const size_t plane = (size_t)np * np;
     const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
     const int tid = threadIdx.x;
+    // from L2: another CTA (or SM) of an earlier kernel wrote these, and the
+    // caller may read them before its grid dependency wait
 #pragma unroll
     for (int k = 0; k < EpiIn<STAGE, NTH>::K; ++k) {
         const int e = tid + k * NTH;
         const int a = e / TS, b = e - (e / TS) * TS;
         const size_t off = (size_t)(I * TS + a) * np + J * TS + b;
-        in.dr[k] = din[off];
-        in.di[k] = din[plane + off];
+        in.dr[k] = __ldcg(din + off);
+        in.di[k] = __ldcg(din + plane + off);
         if (STAGE <= 3) {
-            in.ur[k] = w.F32[off];
-            in.ui[k] = w.F32[plane + off];
-            in.vr[k] = w.D[off];
-            in.vi[k] = w.D[plane + off];
+            in.ur[k] = __ldcg(w.F32 + off);
+            in.ui[k] = __ldcg(w.F32 + plane + off);
+            in.vr[k] = __ldcg(w.D + off);
+            in.vi[k] = __ldcg(w.D + plane + off);
             if (STAGE >= 2) {
-                in.sr[k] = w.S[off];
-                in.si[k] = w.S[plane + off];
+                in.sr[k] = __ldcg(w.S + off);
+                in.si[k] = __ldcg(w.S + plane + off);
             }
         } else {
-            in.ur[k] = w.S[off];
-            in.ui[k] = w.S[plane + off];
-            in.vr[k] = w.D[off];
-            in.vi[k] = w.D[plane + off];
-            in.sr[k] = w.Dlo[off];
-            in.si[k] = w.Dlo[plane + off];
-            in.gr[k] = w.Ghi[off];
-            in.gi[k] = w.Ghi[plane + off];
-            in.lr[k] = w.Glo[off];
-            in.li[k] = w.Glo[plane + off];
+            in.ur[k] = __ldcg(w.S + off);
+            in.ui[k] = __ldcg(w.S + plane + off);
+            in.vr[k] = __ldcg(w.D + off);
+            in.vi[k] = __ldcg(w.D + plane + off);
+            in.sr[k] = __ldcg(w.Dlo + off);
+            in.si[k] = __ldcg(w.Dlo + plane + off);
+            in.gr[k] = __ldcg(w.Ghi + off);
+            in.gi[k] = __ldcg(w.Ghi + plane + off);
+            in.lr[k] = __ldcg(w.Glo + off);
+            in.li[k] = __ldcg(w.Glo + plane + off);
         }
         in.ca[k] = ops.c32[I * TS + a];
     }

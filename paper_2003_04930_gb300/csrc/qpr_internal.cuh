@@ -231,7 +231,7 @@ cudaError_t set_persist_smem(int bytes);
 cudaError_t launch_cols_block(const DevOps &ops, const MixedWork &w, int steps, int grid, cudaStream_t s);
 // Kernel launches per RK4 step and per refresh of the mixed form.
 constexpr int kMixedLaunchesPerStep = 4;   // tile-pair sparse kernel (the dense one adds 4 gain kernels)
-constexpr int kMixedLaunchesPerStepCols = 8;  // column-block form: SpMM + epilogue per stage
+constexpr int kMixedLaunchesPerStepCols = 12;  // column-block form: gain, SpMM and epilogue per stage
 constexpr int kMixedLaunchesPerRefresh = 5;
 
 // ---- host assembly (qpr_api.cu) ----

@@ -24,22 +24,16 @@ namespace {
 
 using namespace cols;
 
+// Launched with programmatic dependent launch: the prologue (barriers, this
+// CTA's CSR entries and bundles, which no kernel writes) overlaps the end of
+// the previous kernel; the stage input is read after grid_dependency_wait.
 template <int STAGE>
 __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
                                                          MixedWork w) {
     extern __shared__ uint8_t dyn_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar_csr, bar_d;
     __shared__ int s_done;
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid == 0) {
-        s_done = *(volatile int *)&w.ctl->done;
-        if (!s_done) {
-            tma::mbar_init(&bar, 1);
-            tma::mbar_init_fence();
-        }
-    }
-    __syncthreads();
-    if (s_done) return;
     const int J = blockIdx.x, r = blockIdx.y, np = ops.np;
     const uint32_t s0 = tma::smem_u32(dyn_raw);
     uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);  // 128-byte aligned, shared provenance kept
@@ -48,21 +42,36 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
     int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
     const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
     const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
+    const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
+    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 32);
     if (tid == 0) {
-        const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
-        const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 32);
-        tma::mbar_expect_tx(&bar, (uint32_t)np * kRowFloats * 4 + kh_bytes + p_bytes);
-        for (int b = 0; b < np; b += kBoxRows)
-            tma::load_3d(sD + (size_t)b * kRowFloats, &tm, &bar, J * kCW, 0, b);
-        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
-        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar);
+        tma::mbar_init(&bar_csr, 1);
+        tma::mbar_init(&bar_d, 1);
+        tma::mbar_init_fence();
+        tma::mbar_expect_tx(&bar_csr, kh_bytes + p_bytes);
+        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar_csr);
+        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar_csr);
     }
     const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
-    const bool ok = tma::mbar_wait(&bar, 0);
+    tma::grid_dependency_wait();
+    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    if (s_done) {
+        tma::mbar_wait(&bar_csr, 0);  // the copies in flight land before the CTA leaves (bounded)
+        return;
+    }
+    tma::launch_dependents();
+    if (tid == 0) {
+        tma::mbar_expect_tx(&bar_d, (uint32_t)np * kRowFloats * 4);
+        for (int b = 0; b < np; b += kBoxRows)
+            tma::load_3d(sD + (size_t)b * kRowFloats, &tm, &bar_d, J * kCW, 0, b);
+    }
+    const bool ok = tma::mbar_wait(&bar_csr, 0) && tma::mbar_wait(&bar_d, 0);
     if (__syncthreads_or(!ok)) {
         // bounded wait gave up: report, give the copies one more bounded wait, return
         if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
-        tma::mbar_wait(&bar, 0);
+        tma::mbar_wait(&bar_csr, 0);
+        tma::mbar_wait(&bar_d, 0);
         return;
     }
     warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X);
@@ -79,6 +88,10 @@ __global__ void __launch_bounds__(kANT) cols_gain_kernel(DevOps ops, MixedWork w
     cta_gain(ops, w, blockIdx.x, gridDim.x, sp_dyn);
 }
 
+// Launched with programmatic dependent launch: the elementwise operands (the
+// stage input, F32, D, S, ...: written two kernels back, complete once the
+// SpMM kernel has passed its own dependency wait) are loaded before
+// grid_dependency_wait; X, the gain and the control block after it.
 template <int STAGE>
 __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork w) {
     __shared__ __align__(16) float sX1[TS * LDX];
@@ -86,11 +99,15 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     __shared__ __align__(16) float sO[4 * TS * LDO];
     __shared__ float sg[TS];
     __shared__ int s_done;
+    const int2 pr = w.pairs[blockIdx.x];
+    mixed::EpiIn<STAGE, kENT> in;
+    mixed::epi_load<STAGE, kENT>(ops, w, pr.x, pr.y, in);
+    tma::grid_dependency_wait();
     if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
     __syncthreads();
     if (s_done) return;
-    const int2 pr = w.pairs[blockIdx.x];
-    epilogue_pair<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO);
+    tma::launch_dependents();
+    epilogue_pair_in<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
 }
 
 int max_smem_optin(int device) {
@@ -261,10 +278,26 @@ cudaError_t set_cols_smem(int bytes) {
 
 // Stage inputs: stage 1 D (map 0), stage 2 da (map 1), stage 3 db (map 2),
 // stage 4 da (map 1). parts & 1: the SpMM kernel, parts & 2: the epilogue.
+template <typename K, typename... A>
+void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts) {
     const ColMaps &m = *w.cmaps;
     const dim3 ga(ops.np / kCW, ops.col_splits);
     const size_t sm = (size_t)ops.col_smem;
+    const CUtensorMap &tm = m.d[stage == 1 ? 0 : (stage == 3 ? 2 : 1)];
     if (parts & 1) {
         // fork: the gain on the side stream, the SpMM here; join before the epilogue
         cudaEventRecord(m.fork, s);
@@ -272,19 +305,20 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
         cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
         cudaEventRecord(m.join, m.side);
         switch (stage) {
-            case 1: cols_spmm_kernel<1><<<ga, kANT, sm, s>>>(m.d[0], ops, w); break;
-            case 2: cols_spmm_kernel<2><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
-            case 3: cols_spmm_kernel<3><<<ga, kANT, sm, s>>>(m.d[2], ops, w); break;
-            default: cols_spmm_kernel<4><<<ga, kANT, sm, s>>>(m.d[1], ops, w); break;
+            case 1: launch_pdl(cols_spmm_kernel<1>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+            case 2: launch_pdl(cols_spmm_kernel<2>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+            case 3: launch_pdl(cols_spmm_kernel<3>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+            default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, tm, ops, w); break;
         }
         cudaStreamWaitEvent(s, m.join, 0);
     }
     if (parts & 2) {
+        const dim3 ge(w.npairs);
         switch (stage) {
-            case 1: cols_epi_kernel<1><<<w.npairs, kENT, 0, s>>>(ops, w); break;
-            case 2: cols_epi_kernel<2><<<w.npairs, kENT, 0, s>>>(ops, w); break;
-            case 3: cols_epi_kernel<3><<<w.npairs, kENT, 0, s>>>(ops, w); break;
-            default: cols_epi_kernel<4><<<w.npairs, kENT, 0, s>>>(ops, w); break;
+            case 1: launch_pdl(cols_epi_kernel<1>, ge, dim3(kENT), 0, s, ops, w); break;
+            case 2: launch_pdl(cols_epi_kernel<2>, ge, dim3(kENT), 0, s, ops, w); break;
+            case 3: launch_pdl(cols_epi_kernel<3>, ge, dim3(kENT), 0, s, ops, w); break;
+            default: launch_pdl(cols_epi_kernel<4>, ge, dim3(kENT), 0, s, ops, w); break;
         }
     }
 }

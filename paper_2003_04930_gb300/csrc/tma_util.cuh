@@ -77,5 +77,11 @@ __device__ __forceinline__ void load_bulk(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// Programmatic dependent launch: wait until the previous kernel in the
+// stream has completed and its memory is visible; let the next kernel start
+// its prologue. Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 }  // namespace tma
 }  // namespace qpr
