@@ -398,7 +398,8 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     size_t nkh = 0, nci = 0, npc = 0, nxc = 0, na_max = 0;
     int smem_a = 0;
     for (size_t g = 0; g < G; ++g) {
-        if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g])) {
+        // one split where it fits: the batch fills the SMs with many problems
+        if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g], 1)) {
             if (o.sparse_form == QPR_SPARSE_FORM_COLUMNS || o.sparse_form == QPR_SPARSE_FORM_COLUMNS_PERSISTENT)
                 return err(QPR_E_ARG, "problem " + std::to_string(g) +
                                           ": sparse_form COLUMNS does not fit one CTA's shared memory");

@@ -215,8 +215,12 @@ struct ColPlan {
     std::vector<int> wb;          // splits * 16 + 1
 };
 // Plans the column-block form of an np x np problem on `device`; false if
-// its staged operands do not fit one CTA's shared memory.
-bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan);
+// its staged operands do not fit one CTA's shared memory. Row splits: the
+// fewest from min_splits up that fit (0: enough CTAs for every SM when the
+// problem runs alone). A row's product does not depend on the plan (its
+// group sums its entries in order; zero padding never changes a sum that
+// starts at +0), so every plan gives bitwise the same X.
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits = 0);
 // Opt in to `bytes` of dynamic shared memory for the SpMM kernels.
 cudaError_t set_cols_smem(int bytes);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);

@@ -194,7 +194,7 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
 
 }  // namespace
 
-bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan) {
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits) {
     if (np > kColMaxNp || np % kBoxRows != 0) return false;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
@@ -210,7 +210,8 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan) {
         const double nz = (i < n) ? (double)(h.hptr[i + 1] - h.hptr[i]) : 0.0;
         cum[i + 1] = cum[i] + nz + 4.0;
     }
-    for (int s = std::min(std::max(1, sms / ncb), 16); s <= 16; ++s) {
+    const int s0 = min_splits > 0 ? min_splits : std::min(std::max(1, sms / ncb), 16);
+    for (int s = s0; s <= 16; ++s) {
         ColPlan pl;
         pl.splits = s;
         std::vector<int> rows(s + 1, 0);
