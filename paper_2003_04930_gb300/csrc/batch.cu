@@ -26,6 +26,7 @@
 #include "mixed_body.cuh"
 #include "qpr_internal.cuh"
 #include "sparse_body.cuh"
+#include "tma_util.cuh"
 
 namespace qpr {
 
@@ -116,16 +117,23 @@ __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGrap
     }
 }
 
-// Column-block form: the SpMM over (problem, J, split) items. The column
-// block, the split's CSR entries and bundles are staged with plain loads
-// (each problem has its own layout); the arithmetic is the single-problem
-// form's (warp_bundles, cta_gain), so the results are bitwise the same.
+// Column-block form: the SpMM over (problem, J, split) items. The split's
+// entries and bundles are staged with two bulk copies (one mbarrier), the
+// column block with plain loads, 8 in flight per thread (each problem has its
+// own layout, so no tensor map); the arithmetic is the single-problem form's
+// (warp_bundles, cta_gain), so the results are bitwise the same.
 template <int STAGE>
 __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
                                                                  int nitems) {
-    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar, 1);
+        tma::mbar_init_fence();
+    }
+    uint32_t phase = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 t = items[it];
         load_graph(gs, t.x, sg);
@@ -139,19 +147,46 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
             const float *din = cols::stage_input<STAGE>(sg.mw);
             const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
             const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
-            for (int u = threadIdx.x; u < np * 8; u += blockDim.x) {
-                const int k = u >> 3, part = u & 7;  // parts 0..3: real quads, 4..7: imaginary quads
-                const float4 v = *reinterpret_cast<const float4 *>(din + (part < 4 ? 0 : plane) + (size_t)k * np +
-                                                                   J * cols::kCW + 4 * (part & 3));
-                *reinterpret_cast<float4 *>(sD + k * cols::kRowFloats + 4 * part) = v;
+            if (threadIdx.x < 32) {
+                // the previous item's reads of these buffers came through the generic proxy
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8), p_bytes = (uint32_t)((p_end - p_base) * 32);
+                if (threadIdx.x == 0) {
+                    tma::mbar_expect_tx(&bar, kh_bytes + p_bytes);
+                    if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
+                    if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar);
+                }
             }
-            for (int u = threadIdx.x; u < q_end - q_base; u += blockDim.x) sKH[u] = ops.col_kh[q_base + u];
-            for (int u = threadIdx.x; u < 2 * (p_end - p_base); u += blockDim.x)
-                sP[u] = ops.col_pieces[2 * (size_t)p_base + u];
+            // the column block with plain loads, 8 float4 in flight per thread
+            // (parts 0..3: real quads, 4..7: imaginary quads of a row)
+            for (int u0 = threadIdx.x; u0 < np * 8; u0 += 8 * (int)blockDim.x) {
+                float4 v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int u = u0 + i * (int)blockDim.x;
+                    if (u < np * 8) {
+                        const int k = u >> 3, part = u & 7;
+                        v[i] = __ldcg(reinterpret_cast<const float4 *>(din + (part < 4 ? 0 : plane) +
+                                                                       (size_t)k * np + J * cols::kCW +
+                                                                       4 * (part & 3)));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int u = u0 + i * (int)blockDim.x;
+                    if (u < np * 8) *reinterpret_cast<float4 *>(sD + (u >> 3) * cols::kRowFloats + 4 * (u & 7)) = v[i];
+                }
+            }
             const int ncb = np / cols::kCW;
             cols::cta_gain(ops, sg.mw, r * ncb + J, ncb * ops.col_splits,
                            reinterpret_cast<float *>(dyn_smem + ops.col_sp_off));
-            __syncthreads();
+            const bool ok = tma::mbar_wait(&bar, phase & 1);
+            ++phase;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicExch(&sg.mw.ctl->err_timeout, 1);
+                tma::mbar_wait(&bar, (phase - 1) & 1);
+                return;
+            }
             const int warp = threadIdx.x >> 5;
             cols::warp_bundles(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
                                ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X);
