@@ -150,11 +150,13 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
             if (threadIdx.x < 32) {
                 // the previous item's reads of these buffers came through the generic proxy
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8), p_bytes = (uint32_t)((p_end - p_base) * 32);
+                const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);
+                const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * cols::kBundleInt4);
                 if (threadIdx.x == 0) {
                     tma::mbar_expect_tx(&bar, kh_bytes + p_bytes);
                     if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
-                    if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar);
+                    if (p_bytes)
+                        tma::load_bulk(sP, ops.col_pieces + cols::kBundleInt4 * (size_t)p_base, p_bytes, &bar);
                 }
             }
             // the column block with plain loads, 8 float4 in flight per thread

@@ -43,14 +43,14 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
     const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
     const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
     const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
-    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 32);
+    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * kBundleInt4);
     if (tid == 0) {
         tma::mbar_init(&bar_csr, 1);
         tma::mbar_init(&bar_d, 1);
         tma::mbar_init_fence();
         tma::mbar_expect_tx(&bar_csr, kh_bytes + p_bytes);
         if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar_csr);
-        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar_csr);
+        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + kBundleInt4 * (size_t)p_base, p_bytes, &bar_csr);
     }
     const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
     tma::grid_dependency_wait();
@@ -124,7 +124,7 @@ cudaError_t set_spmm_attr(int bytes) {
     return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Bundles of one split's rows [r0, r1): long rows alone, the others 4 at a
+// Bundles of one split's rows [r0, r1): long rows alone, the others 8 at a
 // time by decreasing length; dealt to the warps longest first, each to the
 // least loaded warp. Appends, per warp, the bundles' descriptors and their
 // interleaved, zero-padded entries (relative offsets from `kh_base`), and
@@ -132,7 +132,7 @@ cudaError_t set_spmm_attr(int bytes) {
 void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std::vector<int2> &kh,
                    std::vector<int4> &pieces, std::vector<int> &wb) {
     struct Bundle {
-        int rows[4];
+        int rows[8];
         int T;
         bool lng;
         long long cost;
@@ -149,19 +149,19 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
     };
     for (int i = r0; i < r1; ++i) {
         if (row_len(i) > kLongRow) {
-            Bundle b{{i, -1, -1, -1}, (row_len(i) + 3) / 4, true, 0};
-            b.cost = b.T + 8;
+            Bundle b{{i, -1, -1, -1, -1, -1, -1, -1}, (row_len(i) + 7) / 8, true, 0};
+            b.cost = 2 * b.T + 8;
             bs.push_back(b);
         } else {
             shortrows.push_back(i);
         }
     }
     std::stable_sort(shortrows.begin(), shortrows.end(), [&](int a, int b) { return row_len(a) > row_len(b); });
-    for (size_t k = 0; k < shortrows.size(); k += 4) {
-        Bundle b{{-1, -1, -1, -1}, row_len(shortrows[k]), false, 0};
-        for (int j = 0; j < 4; ++j)
+    for (size_t k = 0; k < shortrows.size(); k += 8) {
+        Bundle b{{-1, -1, -1, -1, -1, -1, -1, -1}, row_len(shortrows[k]), false, 0};
+        for (int j = 0; j < 8; ++j)
             if (k + j < shortrows.size()) b.rows[j] = shortrows[k + j];
-        b.cost = b.T + 8;
+        b.cost = 2 * b.T + 8;
         bs.push_back(b);
     }
     std::stable_sort(bs.begin(), bs.end(), [](const Bundle &a, const Bundle &b) { return a.cost > b.cost; });
@@ -173,21 +173,26 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
         load[wmin] += bs[k].cost;
     }
     for (int wi = 0; wi < kAWarps; ++wi) {
-        wb.push_back((int)(pieces.size() / 2));
+        wb.push_back((int)(pieces.size() / kBundleInt4));
         for (int k : per[wi]) {
             const Bundle &b = bs[k];
             pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T, b.lng ? kPieceLong : 0, 0));
             pieces.push_back(make_int4(b.rows[0], b.rows[1], b.rows[2], b.rows[3]));
+            pieces.push_back(make_int4(b.rows[4], b.rows[5], b.rows[6], b.rows[7]));
+            // round t, group g, slot s -> position 8 t + 2 g + s
             for (int t = 0; t < b.T; ++t)
-                for (int g = 0; g < 4; ++g) {
-                    int2 v = make_int2(0, 0);
-                    if (b.lng) {
-                        if (4 * t + g < row_len(b.rows[0])) v = entry(b.rows[0], 4 * t + g);
-                    } else if (b.rows[g] >= 0 && t < row_len(b.rows[g])) {
-                        v = entry(b.rows[g], t);
+                for (int g = 0; g < 4; ++g)
+                    for (int sl = 0; sl < 2; ++sl) {
+                        int2 v = make_int2(0, 0);
+                        if (b.lng) {
+                            const int e = 8 * t + 2 * g + sl;
+                            if (e < row_len(b.rows[0])) v = entry(b.rows[0], e);
+                        } else {
+                            const int row = b.rows[g + 4 * sl];
+                            if (row >= 0 && t < row_len(row)) v = entry(row, t);
+                        }
+                        kh.push_back(v);
                     }
-                    kh.push_back(v);
-                }
         }
     }
 }
@@ -225,17 +230,17 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         size_t kh_max = 0, p_max = 0;
         for (int k = 0; k < s; ++k) {
             const size_t kb = pl.kh.size();  // even: every split's block starts 16-byte aligned
-            const int first = (int)(pl.pieces.size() / 2);
+            const int first = (int)(pl.pieces.size() / kBundleInt4);
             pl.sb.push_back(first);
             split_bundles(h, rows[k], rows[k + 1], n, kb, pl.kh, pl.pieces, pl.wb);
             if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
             pl.q.push_back((int)kb);
             pl.q.push_back((int)pl.kh.size());
             kh_max = std::max(kh_max, (pl.kh.size() - kb) * 8);
-            p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / 2) - first) * 32);
+            p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / kBundleInt4) - first) * 16 * kBundleInt4);
         }
-        pl.sb.push_back((int)(pl.pieces.size() / 2));
-        pl.wb.push_back((int)(pl.pieces.size() / 2));
+        pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
+        pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
         pl.sp_off = (int)((size_t)pl.p_off + p_max);
         const size_t smem = (size_t)pl.sp_off + (size_t)np * 4 + 128;

@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(kANT, 1) cols_block_kernel(const __grid_consta
         const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
         if (tid == 0) {
             const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
-            const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 32);
+            const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * kBundleInt4);
             tma::mbar_expect_tx(&bar, kh_bytes + p_bytes);
             if (kh_bytes) tma::load_bulk(sm.sKH, ops.col_kh + q_base, kh_bytes, &bar);
-            if (p_bytes) tma::load_bulk(sm.sP, ops.col_pieces + 2 * (size_t)p_base, p_bytes, &bar);
+            if (p_bytes) tma::load_bulk(sm.sP, ops.col_pieces + kBundleInt4 * (size_t)p_base, p_bytes, &bar);
         }
         const bool ok = tma::mbar_wait(&bar, 0);
         ++phase;
