@@ -11,15 +11,15 @@
 // X_JI, as the tile-pair form does.
 //
 // Work list: the rows of a split are cut into bundles handled by one warp:
-// 8 rows of similar length, two per 8-lane group (lane p of a group holds 4
-// of the 32 values of a staged row: one 16-byte read per nonzero, a whole
-// row per group, no bank conflict), or one row longer than kLongRow
-// nonzeros whose nonzeros are dealt to the 4 groups, two at a time. A
+// 4 kRPG rows of similar length, kRPG per 8-lane group (lane p of a group
+// holds 4 of the 32 values of a staged row: one 16-byte read per nonzero, a
+// whole row per group, no bank conflict), or one row longer than kLongRow
+// nonzeros whose nonzeros are dealt to the 4 groups, kRPG at a time. A
 // bundle's CSR entries are stored interleaved and zero-padded to its T
-// rounds (round t, group g: entries 8 t + 2 g and 8 t + 2 g + 1, one 16-byte
-// read), so each round is one entry read and two independent row reads per
-// group, without predicates. Bundles go to warps longest first, each to the
-// least loaded warp.
+// rounds (round t, group g, slot s at 4 kRPG t + kRPG g + s), so each round is
+// kRPG / 2 16-byte entry reads and kRPG independent row reads per group,
+// without predicates. Bundles go to warps longest first, each to the least
+// loaded warp.
 #pragma once
 
 #include "mixed_body.cuh"
@@ -40,23 +40,26 @@ constexpr int kAWarps = kANT / 32;
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
 constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
+constexpr int kRPG = 2;            // rows (slots) per 8-lane group of a bundle (4 measured slower: more padding)
 
-// A bundle descriptor is three int4: {first entry (relative to its split's
-// entries, even), rounds T, flags, 0} and the rows of the 8 slots (slot g and
-// g + 4 belong to group g; -1: none; a long-row bundle has only the first).
-constexpr int kBundleInt4 = 3;
+// A bundle descriptor is 1 + kRPG int4: {first entry (relative to its
+// split's entries, even), rounds T, flags, 0} and the rows of the 4 kRPG
+// slots, int4 k + 1 holding slot k of groups 0..3 (-1: none; a long-row
+// bundle has only the first).
+constexpr int kBundleInt4 = 1 + kRPG;
 
 __device__ __forceinline__ float4 f4fma(float h, float4 v, float4 acc) { return mixed::f4fma(h, v, acc); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
     return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
 }
+__device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g == 1) ? v.y : (g == 2) ? v.z : v.w; }
 
 // Bundles [b0, b1) of one warp: X[row, J] for each row, from the staged
 // block sD ([row][kRowFloats]), the split's staged entries sKH and the
-// staged bundles sP (bundle b at sP[3 (b - p_base)]). Sums are formed in a
-// fixed order (per row in entry order; for a long row per group two
-// interleaved sums, added, then over the groups by xor-shuffle), so the
-// result does not depend on timing.
+// staged bundles sP (bundle b at sP[kBundleInt4 (b - p_base)]). Sums are
+// formed in a fixed order (per row in entry order; for a long row per group
+// kRPG interleaved sums added in slot order, then over the groups by
+// xor-shuffle), so the result does not depend on timing.
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
                                              float *__restrict__ X) {
@@ -68,26 +71,35 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
     for (int b = b0; b < b1; ++b) {
         const int4 *bd = sP + kBundleInt4 * (b - p_base);
         const int4 d0 = bd[0];
-        const int4 *__restrict__ kh = reinterpret_cast<const int4 *>(sKH + d0.x) + g;
+        const int4 *__restrict__ kh = reinterpret_cast<const int4 *>(sKH + d0.x) + g * (kRPG / 2);
         const int T = d0.y;
-        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-#pragma unroll 4
+        float4 acc[kRPG];
+#pragma unroll
+        for (int s = 0; s < kRPG; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
         for (int t = 0; t < T; ++t) {
-            const int4 e = kh[4 * t];
-            acc0 = f4fma(__int_as_float(e.y), *reinterpret_cast<const float4 *>(sDp + e.x * kRowFloats), acc0);
-            acc1 = f4fma(__int_as_float(e.w), *reinterpret_cast<const float4 *>(sDp + e.z * kRowFloats), acc1);
+#pragma unroll
+            for (int s2 = 0; s2 < kRPG / 2; ++s2) {
+                const int4 e = kh[2 * kRPG * t + s2];
+                acc[2 * s2] = f4fma(__int_as_float(e.y), *reinterpret_cast<const float4 *>(sDp + e.x * kRowFloats),
+                                    acc[2 * s2]);
+                acc[2 * s2 + 1] = f4fma(__int_as_float(e.w),
+                                        *reinterpret_cast<const float4 *>(sDp + e.z * kRowFloats), acc[2 * s2 + 1]);
+            }
         }
         if (d0.z & kPieceLong) {
-            float4 acc = f4add(acc0, acc1);
-            acc = mixed::f4xor(acc, 8);
-            acc = mixed::f4xor(acc, 16);
-            if (g == 0) *reinterpret_cast<float4 *>(Xp + (size_t)bd[1].x * np) = acc;
+            float4 a = acc[0];
+#pragma unroll
+            for (int s = 1; s < kRPG; ++s) a = f4add(a, acc[s]);
+            a = mixed::f4xor(a, 8);
+            a = mixed::f4xor(a, 16);
+            if (g == 0) *reinterpret_cast<float4 *>(Xp + (size_t)bd[1].x * np) = a;
         } else {
-            const int4 ra = bd[1], rb = bd[2];
-            const int r0 = (g == 0) ? ra.x : (g == 1) ? ra.y : (g == 2) ? ra.z : ra.w;
-            const int r1 = (g == 0) ? rb.x : (g == 1) ? rb.y : (g == 2) ? rb.z : rb.w;
-            if (r0 >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)r0 * np) = acc0;
-            if (r1 >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)r1 * np) = acc1;
+#pragma unroll
+            for (int s = 0; s < kRPG; ++s) {
+                const int row = pick(bd[1 + s], g);
+                if (row >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = acc[s];
+            }
         }
     }
 }

@@ -124,15 +124,16 @@ cudaError_t set_spmm_attr(int bytes) {
     return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Bundles of one split's rows [r0, r1): long rows alone, the others 8 at a
-// time by decreasing length; dealt to the warps longest first, each to the
-// least loaded warp. Appends, per warp, the bundles' descriptors and their
-// interleaved, zero-padded entries (relative offsets from `kh_base`), and
-// the warps' first bundles.
+// Bundles of one split's rows [r0, r1): long rows alone, the others 4 kRPG
+// at a time by decreasing length; dealt to the warps longest first, each to
+// the least loaded warp. Appends, per warp, the bundles' descriptors and
+// their interleaved, zero-padded entries (relative offsets from `kh_base`),
+// and the warps' first bundles.
 void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std::vector<int2> &kh,
                    std::vector<int4> &pieces, std::vector<int> &wb) {
+    constexpr int kSlots = 4 * kRPG;
     struct Bundle {
-        int rows[8];
+        int rows[kSlots];
         int T;
         bool lng;
         long long cost;
@@ -147,21 +148,28 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
         memcpy(&bits, &v, 4);
         return make_int2(h.hcol[q], bits);
     };
+    auto fresh = [&](int T, bool lng) {
+        Bundle b;
+        for (int j = 0; j < kSlots; ++j) b.rows[j] = -1;
+        b.T = T;
+        b.lng = lng;
+        b.cost = (long long)kRPG * T + 8;
+        return b;
+    };
     for (int i = r0; i < r1; ++i) {
         if (row_len(i) > kLongRow) {
-            Bundle b{{i, -1, -1, -1, -1, -1, -1, -1}, (row_len(i) + 7) / 8, true, 0};
-            b.cost = 2 * b.T + 8;
+            Bundle b = fresh((row_len(i) + kSlots - 1) / kSlots, true);
+            b.rows[0] = i;
             bs.push_back(b);
         } else {
             shortrows.push_back(i);
         }
     }
     std::stable_sort(shortrows.begin(), shortrows.end(), [&](int a, int b) { return row_len(a) > row_len(b); });
-    for (size_t k = 0; k < shortrows.size(); k += 8) {
-        Bundle b{{-1, -1, -1, -1, -1, -1, -1, -1}, row_len(shortrows[k]), false, 0};
-        for (int j = 0; j < 8; ++j)
+    for (size_t k = 0; k < shortrows.size(); k += kSlots) {
+        Bundle b = fresh(row_len(shortrows[k]), false);
+        for (int j = 0; j < kSlots; ++j)
             if (k + j < shortrows.size()) b.rows[j] = shortrows[k + j];
-        b.cost = 2 * b.T + 8;
         bs.push_back(b);
     }
     std::stable_sort(bs.begin(), bs.end(), [](const Bundle &a, const Bundle &b) { return a.cost > b.cost; });
@@ -177,15 +185,16 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
         for (int k : per[wi]) {
             const Bundle &b = bs[k];
             pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T, b.lng ? kPieceLong : 0, 0));
-            pieces.push_back(make_int4(b.rows[0], b.rows[1], b.rows[2], b.rows[3]));
-            pieces.push_back(make_int4(b.rows[4], b.rows[5], b.rows[6], b.rows[7]));
-            // round t, group g, slot s -> position 8 t + 2 g + s
+            // slot s of group g is rows[g + 4 s]
+            for (int s = 0; s < kRPG; ++s)
+                pieces.push_back(make_int4(b.rows[4 * s], b.rows[4 * s + 1], b.rows[4 * s + 2], b.rows[4 * s + 3]));
+            // round t, group g, slot s -> position kSlots t + kRPG g + s
             for (int t = 0; t < b.T; ++t)
                 for (int g = 0; g < 4; ++g)
-                    for (int sl = 0; sl < 2; ++sl) {
+                    for (int sl = 0; sl < kRPG; ++sl) {
                         int2 v = make_int2(0, 0);
                         if (b.lng) {
-                            const int e = 8 * t + 2 * g + sl;
+                            const int e = kSlots * t + kRPG * g + sl;
                             if (e < row_len(b.rows[0])) v = entry(b.rows[0], e);
                         } else {
                             const int row = b.rows[g + 4 * sl];
