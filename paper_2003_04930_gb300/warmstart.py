@@ -7,6 +7,8 @@ the result, so a poor prediction costs steps, never accuracy.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import graphs
@@ -47,6 +49,19 @@ def warm_rho(p_hat: np.ndarray) -> np.ndarray:
 # omega = 0.2 (the coherent part must rebuild the coherences it was not
 # given, and the populations move away meanwhile).
 WARM_OMEGA_MIN = 0.5
+
+
+TRAINED_PARAMS = os.path.join(os.path.dirname(__file__), "data", "warmstart_gnn.npy")
+
+
+def load_network(path: str = TRAINED_PARAMS, device: int = -1):
+    """The network with the parameters train_warmstart saved (None if the
+    file is absent)."""
+    if not os.path.exists(path):
+        return None
+    net = Q.Gnn(seed=0, device=device)
+    net.set_params(np.load(path).astype(np.float32))
+    return net
 
 
 def initial_state(net, g, omega: float, alpha: float = 0.85) -> np.ndarray:

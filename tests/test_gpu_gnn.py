@@ -72,3 +72,21 @@ def test_warm_start_saves_steps_and_keeps_the_answer():
     assert np.linalg.norm(a - b) <= 1e-6
     pa, pb = np.real(np.diag(a)), np.real(np.diag(b))
     assert np.abs(pa - pb).max() <= 1e-7 * pa.max()
+
+
+def test_shipped_network_saves_steps_at_n922():
+    """The weights train_warmstart saved in the package (256 solver-generated
+    steady states, seeds 10000+) on the N = 922 benchmark graph (seed 1)."""
+    net = warmstart.load_network()
+    assert net is not None
+    g = graphs.heavy_tailed(922, 1)
+    s = Solver.from_edges(g, alpha=0.85, omega=0.8, precision=Q.QPR_MIXED)
+    cold = torch.from_numpy(graphs.maximally_mixed(922)).to(DEV)
+    st_cold = s.steady_state(cold, 0.01, 1e-8, 400000)
+    warm = torch.from_numpy(warmstart.initial_state(net, g, 0.8)).to(DEV)
+    st_warm = s.steady_state(warm, 0.01, 1e-8, 400000)
+    assert st_warm["converged"] == 1 and st_warm["steps"] < st_cold["steps"], (st_warm["steps"], st_cold["steps"])
+    s.steady_state(cold, 0.01, 1e-11, 400000)
+    s.steady_state(warm, 0.01, 1e-11, 400000)
+    pa, pb = np.real(np.diag(cold.cpu().numpy())), np.real(np.diag(warm.cpu().numpy()))
+    assert np.abs(pa - pb).max() <= 1e-7 * pa.max()

@@ -92,3 +92,12 @@ def test_softmax_loss_properties_and_equivariance():
     A2 = gnn.adjacency(20, src, dst, g.w)
     _, ph2, _ = gnn.forward(th, gnn.features(A2, 0.4, 0.85), gnn.aggregation(A2))
     np.testing.assert_allclose(ph2[inv], ph, atol=1e-14)
+
+
+def test_shipped_network_parameters_have_the_oracle_layout():
+    import os
+    from paper_2003_04930_gb300 import warmstart
+    assert os.path.exists(warmstart.TRAINED_PARAMS)
+    th = np.load(warmstart.TRAINED_PARAMS)
+    assert th.dtype == np.float32 and th.shape == (gnn.param_count(),)
+    assert np.all(np.isfinite(th))
