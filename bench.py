@@ -302,7 +302,8 @@ def run_ours(a):
                 "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
                 "peak_source": f"bf16_tflops of {peak_src}"}
     elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
-            s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
+            s.sparse_form in (qpr.QPR_SPARSE_FORM_COLUMNS, qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED):
+        chunked = s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED
         # column-block SpMM: every nonzero of H reads its row slice of each
         # column block from shared memory, nnz(H) x np x 8 bytes per launch;
         # bound by shared-memory bandwidth, peak derived from the unit counts
@@ -320,7 +321,7 @@ def run_ours(a):
         # pass, so one cold pass over the operands): SpMM 7.03 MB, epilogue 14.04 MB
         spmm_traffic, epi_traffic = (7028736, 14042880) if n == 922 else (None, None)
         roof = {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
-                "traffic": spmm_traffic, "kernel": "cols_spmm_kernel",
+                "traffic": spmm_traffic, "kernel": "cols_chunk_kernel" if chunked else "cols_spmm_kernel",
                 "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
                 "peak_source": f"derived: 128 B/clk/SM x {SMS} SMs x {SM_MAX_GHZ} GHz",
                 "epilogue": {"kernel": "cols_epi_kernel", "bound": "hbm", "launch_ms": prof["stage_ms"],
@@ -328,8 +329,9 @@ def run_ours(a):
                              "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                              "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                              "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
-                "note": "launch_ms from CUDA events around each launch (includes the launch gap); the state "
-                        "is L2-resident at this N, so the epilogue's HBM fraction can exceed 1"}
+                "note": "launch_ms from CUDA events around each launch (includes the launch gap)" +
+                        ("; the state is L2-resident at this N, so the epilogue's HBM fraction can exceed 1"
+                         if 16 * 4 * n * n < 100e6 else "")}
     elif s.backend == qpr.QPR_BACKEND_SPARSE:
         if prec == qpr.QPR_MIXED:
             # mean over the 4 stages of the N x N planes read or written: FP32
@@ -364,6 +366,9 @@ def run_ours(a):
     if s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
         form = ("mixed: fp32 column-block SpMM from TMA-staged shared memory + tile-pair epilogue, "
                 "float-float delta accumulation, fp64 reference/residual")
+    elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED:
+        form = ("mixed: fp32 column-block SpMM, block streamed in chunks multicast over a thread-block cluster "
+                "+ tile-pair epilogue, float-float delta accumulation, fp64 reference/residual")
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",

@@ -100,13 +100,27 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
  *   cooperative launch support).
  * TILES: one launch per stage; each 32 x 32 tile pair gathers, from L2, the
  *   row slices of the delta that its rows' nonzeros select.
- * AUTO (default): COLUMNS where it applies, else TILES. The column forms give
- * bitwise the same results; TILES differs only in FP32 summation order. */
+ * COLUMNS_CHUNKED: the column-block product for any N: a cluster of CTAs
+ *   (one per row split) streams the column block in chunks of chunk_rows
+ *   staged rows, each chunk loaded once and multicast to the cluster, and
+ *   keeps its rows' sums in shared memory; the same epilogue. Needs thread
+ *   block clusters.
+ * COLUMNS_GATHER: the column-block product for any N without staging the
+ *   block: each CTA (row split r, block J) stages only its CSR entries and
+ *   reads every nonzero's 16 values of block J from L2; the splits of a
+ *   block run side by side, so the block is read from DRAM about once.
+ * AUTO (default): COLUMNS where it applies, else COLUMNS_GATHER, else TILES.
+ * COLUMNS, COLUMNS_PERSISTENT and COLUMNS_GATHER give bitwise the same
+ * results (each row's products summed in entry order); COLUMNS_CHUNKED (per
+ * row: chunk by chunk) and TILES differ from them only in FP32 summation
+ * order. */
 enum {
     QPR_SPARSE_FORM_AUTO = 0,
     QPR_SPARSE_FORM_COLUMNS = 1,
     QPR_SPARSE_FORM_TILES = 2,
-    QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 3
+    QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 3,
+    QPR_SPARSE_FORM_COLUMNS_CHUNKED = 4,
+    QPR_SPARSE_FORM_COLUMNS_GATHER = 5
 };
 
 typedef struct {
@@ -119,7 +133,11 @@ typedef struct {
     int32_t backend;     /* QPR_BACKEND_AUTO (default), QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE */
     int32_t ref_refresh; /* QPR_MIXED: steps between exact FP64 reference refreshes (default 32) */
     int32_t sparse_form; /* QPR_MIXED, sparse backend: QPR_SPARSE_FORM_* (default AUTO) */
-    int32_t reserved[4];
+    int32_t chunk_rows;  /* COLUMNS_CHUNKED: staged rows per chunk, a positive multiple of 32
+                            (default 0: chosen by the plan) */
+    int32_t row_splits;  /* COLUMNS, COLUMNS_GATHER: row splits of the product, at least this many
+                            (default 0: chosen by the plan; at most 16, 64 for the gather form) */
+    int32_t reserved[2];
 } qpr_options;
 
 typedef struct {
@@ -162,11 +180,18 @@ QPR_API const char *qpr_status_string(qpr_status s);
  * of H used by the RK4 step-size check. qpr_backend: the backend in use
  * (QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE). qpr_sparse_form: the form of
  * the FP32 sparse stage in use (QPR_SPARSE_FORM_COLUMNS,
- * _COLUMNS_PERSISTENT or _TILES; 0 when the context is not QPR_MIXED with
- * the sparse backend). */
+ * _COLUMNS_PERSISTENT, _COLUMNS_CHUNKED, _COLUMNS_GATHER or _TILES; 0 when
+ * the context is not QPR_MIXED with the sparse backend). */
 QPR_API int64_t qpr_n(const qpr_ctx *ctx);
 QPR_API int32_t qpr_backend(const qpr_ctx *ctx);
 QPR_API int32_t qpr_sparse_form(const qpr_ctx *ctx);
+/* Geometry of the column-block product in use, into out[4]: row splits
+ * (the cluster size of COLUMNS_CHUNKED), staged rows per chunk (0: the whole
+ * block or, for COLUMNS_GATHER, none), chunks per column block (1 unless
+ * chunked) and the product kernel's dynamic shared memory in bytes. All 0
+ * for the tile-pair form.
+ * Errors: QPR_E_ARG (ctx or out NULL). */
+QPR_API qpr_status qpr_sparse_plan(const qpr_ctx *ctx, int32_t *out);
 QPR_API double qpr_h_spread(const qpr_ctx *ctx);
 
 /* Largest dt for which the context considers one RK4 step stable: it needs

@@ -105,14 +105,14 @@ __global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const
 
 template <int STAGE>
 __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
-    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    extern __shared__ __align__(16) uint8_t tile_smem[];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 t = items[it];
         load_graph(gs, t.x, sg);
         if (!graph_done(sg, &s_flag))
-            mixed::mixed_sparse_tile<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0, dyn_smem);
+            mixed::mixed_sparse_tile<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0, tile_smem);
         __syncthreads();
     }
 }

@@ -36,7 +36,23 @@ constexpr int kCW = 16;            // complex columns per block
 constexpr int kRowFloats = 2 * kCW; // staged row: kCW real, then kCW imaginary values (128 bytes)
 constexpr int kBoxRows = 32;       // rows of one TMA box
 constexpr int kANT = 512;          // threads of the SpMM kernel
-constexpr int kAWarps = kANT / 32;
+constexpr int kAWarps = kANT / 32;   // (32 warps measured slower, for both the whole-block and chunked kernels)
+#ifndef QPR_GATHER_CTAS
+#define QPR_GATHER_CTAS 2
+#endif
+#ifndef QPR_GATHER_UNROLL
+#define QPR_GATHER_UNROLL 8
+#endif
+#ifndef QPR_SMEM_UNROLL
+#define QPR_SMEM_UNROLL 0
+#endif
+constexpr int kGatherCtasPerSm = QPR_GATHER_CTAS;  // resident CTAs per SM the gather form's plan sizes for
+constexpr int kGatherUnroll = QPR_GATHER_UNROLL;   // rounds whose row loads the gather form issues together
+constexpr int kGatherWaves = 3;                    // waves of CTAs the gather form's plan asks for at least
+constexpr int kGatherSplitBytes = 56 << 10;        // largest staged entries + bundles of one gather split
+// rounds whose shared-memory row loads the staged forms issue together (0:
+// one round at a time, the compiler unrolling by 2)
+constexpr int kSmemUnroll = QPR_SMEM_UNROLL;
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
 constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
@@ -60,14 +76,34 @@ __device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g 
 // formed in a fixed order (per row in entry order; for a long row per group
 // kRPG interleaved sums added in slot order, then over the groups by
 // xor-shuffle), so the result does not depend on timing.
+//
+// ACC (the chunked form): instead of storing X, add each row's sums to its
+// accumulator acc[(row - row0) kRowFloats + 4 p .. + 3] in shared memory.
+// GMEM (the gather form): sD is the stage input in global memory (two np x
+// np planes); row q's 16 values of block J are read there from L2 (the
+// input was written by the previous kernel, which may still be draining
+// under programmatic dependent launch when this one starts).
+template <bool ACC = false, bool GMEM = false>
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
-                                             float *__restrict__ X) {
+                                             float *__restrict__ X, float *acc_rows = nullptr, int row0 = 0) {
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
-    const float *__restrict__ sDp = sD + 4 * p;
     const size_t plane = (size_t)np * np;
     const int col = J * kCW + 4 * (p & 3);
+    const float *__restrict__ sDp = GMEM ? sD + (p < 4 ? 0 : plane) + col : sD + 4 * p;
+    auto row_of = [&](int q) {
+        if (GMEM) return __ldcg(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
+        return *reinterpret_cast<const float4 *>(sDp + q * kRowFloats);
+    };
     float *__restrict__ Xp = X + (p < 4 ? 0 : plane) + col;
+    auto put = [&](int row, float4 v) {
+        if (ACC) {
+            float4 *a = reinterpret_cast<float4 *>(acc_rows + (row - row0) * kRowFloats + 4 * p);
+            *a = f4add(*a, v);
+        } else {
+            *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = v;
+        }
+    };
     for (int b = b0; b < b1; ++b) {
         const int4 *bd = sP + kBundleInt4 * (b - p_base);
         const int4 d0 = bd[0];
@@ -76,15 +112,57 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
         float4 acc[kRPG];
 #pragma unroll
         for (int s = 0; s < kRPG; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
-        for (int t = 0; t < T; ++t) {
+        constexpr int U = GMEM ? kGatherUnroll : kSmemUnroll;
+        // a row load; from global memory, padding entries (value 0) load nothing
+        auto fetch = [&](int q, int hbits) {
+            if (GMEM && hbits == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+            return row_of(q);
+        };
+        if (U > 0) {
+            // U rounds at a time: their entries, then all their row loads,
+            // then the FMAs in round order (the same sums as one round at a
+            // time)
+            int t = 0;
+            for (; t + U <= T; t += U) {
+                int4 e[U > 0 ? U : 1][kRPG / 2];
+                float4 v[U > 0 ? U : 1][kRPG];
 #pragma unroll
-            for (int s2 = 0; s2 < kRPG / 2; ++s2) {
-                const int4 e = kh[2 * kRPG * t + s2];
-                acc[2 * s2] = f4fma(__int_as_float(e.y), *reinterpret_cast<const float4 *>(sDp + e.x * kRowFloats),
-                                    acc[2 * s2]);
-                acc[2 * s2 + 1] = f4fma(__int_as_float(e.w),
-                                        *reinterpret_cast<const float4 *>(sDp + e.z * kRowFloats), acc[2 * s2 + 1]);
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int s2 = 0; s2 < kRPG / 2; ++s2) e[u][s2] = kh[2 * kRPG * (t + u) + s2];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int s2 = 0; s2 < kRPG / 2; ++s2) {
+                        v[u][2 * s2] = fetch(e[u][s2].x, e[u][s2].y);
+                        v[u][2 * s2 + 1] = fetch(e[u][s2].z, e[u][s2].w);
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int s2 = 0; s2 < kRPG / 2; ++s2) {
+                        acc[2 * s2] = f4fma(__int_as_float(e[u][s2].y), v[u][2 * s2], acc[2 * s2]);
+                        acc[2 * s2 + 1] = f4fma(__int_as_float(e[u][s2].w), v[u][2 * s2 + 1], acc[2 * s2 + 1]);
+                    }
+            }
+            for (; t < T; ++t) {
+#pragma unroll
+                for (int s2 = 0; s2 < kRPG / 2; ++s2) {
+                    const int4 e = kh[2 * kRPG * t + s2];
+                    const float4 v0 = fetch(e.x, e.y), v1 = fetch(e.z, e.w);
+                    acc[2 * s2] = f4fma(__int_as_float(e.y), v0, acc[2 * s2]);
+                    acc[2 * s2 + 1] = f4fma(__int_as_float(e.w), v1, acc[2 * s2 + 1]);
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int t = 0; t < T; ++t) {
+#pragma unroll
+                for (int s2 = 0; s2 < kRPG / 2; ++s2) {
+                    const int4 e = kh[2 * kRPG * t + s2];
+                    acc[2 * s2] = f4fma(__int_as_float(e.y), row_of(e.x), acc[2 * s2]);
+                    acc[2 * s2 + 1] = f4fma(__int_as_float(e.w), row_of(e.z), acc[2 * s2 + 1]);
+                }
             }
         }
         if (d0.z & kPieceLong) {
@@ -93,12 +171,12 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             for (int s = 1; s < kRPG; ++s) a = f4add(a, acc[s]);
             a = mixed::f4xor(a, 8);
             a = mixed::f4xor(a, 16);
-            if (g == 0) *reinterpret_cast<float4 *>(Xp + (size_t)bd[1].x * np) = a;
+            if (g == 0) put(bd[1].x, a);
         } else {
 #pragma unroll
             for (int s = 0; s < kRPG; ++s) {
                 const int row = pick(bd[1 + s], g);
-                if (row >= 0) *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = acc[s];
+                if (row >= 0) put(row, acc[s]);
             }
         }
     }

@@ -539,7 +539,20 @@ int32_t qpr_backend(const qpr_ctx *ctx) { return ctx ? ctx->backend : 0; }
 int32_t qpr_sparse_form(const qpr_ctx *ctx) {
     if (!ctx || ctx->opt.precision != QPR_MIXED || ctx->mw.splitD) return 0;
     if (!ctx->mw.cmaps) return QPR_SPARSE_FORM_TILES;
+    if (ctx->ops.col_cs > 0) return QPR_SPARSE_FORM_COLUMNS_CHUNKED;
+    if (ctx->ops.col_gather) return QPR_SPARSE_FORM_COLUMNS_GATHER;
     return ctx->persist_grid > 0 ? QPR_SPARSE_FORM_COLUMNS_PERSISTENT : QPR_SPARSE_FORM_COLUMNS;
+}
+qpr_status qpr_sparse_plan(const qpr_ctx *ctx, int32_t *out) {
+    if (!ctx || !out) return QPR_E_ARG;
+    out[0] = out[1] = out[2] = out[3] = 0;
+    if (!ctx->mw.cmaps) return QPR_OK;
+    const qpr::DevOps &o = ctx->ops;
+    out[0] = o.col_splits;
+    out[1] = o.col_cs > 0 ? o.col_kc : 0;
+    out[2] = o.col_cs > 0 ? o.col_nc : 1;
+    out[3] = o.col_smem;
+    return QPR_OK;
 }
 double qpr_h_spread(const qpr_ctx *ctx) { return ctx ? ctx->spread : 0.0; }
 
@@ -626,8 +639,11 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
     if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
-    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_COLUMNS_PERSISTENT)
+    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_COLUMNS_GATHER)
         return arg_err(QPR_E_ARG, "unknown sparse_form");
+    if (o.chunk_rows < 0 || o.chunk_rows % 32 != 0 || o.chunk_rows > 4096)
+        return arg_err(QPR_E_ARG, "chunk_rows must be 0 or a multiple of 32 up to 4096");
+    if (o.row_splits < 0 || o.row_splits > 64) return arg_err(QPR_E_ARG, "row_splits outside [0, 64]");
     HostOps hops;
     {
         std::string aerr;
@@ -795,27 +811,47 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         CREATE_CUDA(cudaMalloc(&ctx->d_sval32, sv32.size() * sizeof(float)));
         CREATE_CUDA(cudaMemcpy(ctx->d_sval32, sv32.data(), sv32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
+    // column-block form: the whole column block staged (cplan) or, for larger
+    // N, streamed in chunks by clusters (kplan)
     qpr::ColPlan cplan;
-    const bool cols = (o.precision == QPR_MIXED) && !tc && o.sparse_form != QPR_SPARSE_FORM_TILES &&
-                      qpr::plan_columns(hops, np, ctx->device, cplan);
-    if (o.precision == QPR_MIXED && !tc && !cols &&
-        (o.sparse_form == QPR_SPARSE_FORM_COLUMNS || o.sparse_form == QPR_SPARSE_FORM_COLUMNS_PERSISTENT)) {
-        ctx->err = "sparse_form COLUMNS: the staged operands of N = " + std::to_string(n) +
-                   " do not fit one CTA's shared memory";
+    qpr::ChunkPlan kplan;
+    const int form = o.sparse_form;
+    const bool want_cols = (o.precision == QPR_MIXED) && !tc && form != QPR_SPARSE_FORM_TILES;
+    bool cols = want_cols && form != QPR_SPARSE_FORM_COLUMNS_CHUNKED && form != QPR_SPARSE_FORM_COLUMNS_GATHER &&
+                qpr::plan_columns(hops, np, ctx->device, cplan, o.row_splits);
+    const bool gathered = want_cols && !cols && (form == QPR_SPARSE_FORM_AUTO || form == QPR_SPARSE_FORM_COLUMNS_GATHER) &&
+                          qpr::plan_columns(hops, np, ctx->device, cplan, o.row_splits, true);
+    const bool chunked = want_cols && !cols && !gathered && form == QPR_SPARSE_FORM_COLUMNS_CHUNKED &&
+                         qpr::plan_chunks(hops, np, ctx->device, kplan, o.chunk_rows);
+    cols = cols || gathered || chunked;
+    if (o.precision == QPR_MIXED && !tc && !cols && form != QPR_SPARSE_FORM_AUTO && form != QPR_SPARSE_FORM_TILES) {
+        ctx->err = form == QPR_SPARSE_FORM_COLUMNS_CHUNKED ? "sparse_form COLUMNS_CHUNKED: no cluster plan fits this device"
+                   : form == QPR_SPARSE_FORM_COLUMNS_GATHER
+                       ? "sparse_form COLUMNS_GATHER: no row split fits one CTA's shared memory"
+                       : "sparse_form COLUMNS: the staged operands of N = " + std::to_string(n) +
+                             " do not fit one CTA's shared memory";
         return bail(QPR_E_ARG);
     }
     if (cols) {
-        CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
+        if (chunked) {
+            CREATE_CUDA(qpr::set_chunk_attrs(kplan.smem, kplan.cs));
+        } else if (gathered) {
+            CREATE_CUDA(qpr::set_gather_smem(cplan.smem));
+        } else {
+            CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
+        }
+        const std::vector<int2> &kh = chunked ? kplan.kh : cplan.kh;
+        const std::vector<int4> &pieces = chunked ? kplan.pieces : cplan.pieces;
         std::vector<int> ints;
-        ints.insert(ints.end(), cplan.q.begin(), cplan.q.end());
-        ints.insert(ints.end(), cplan.sb.begin(), cplan.sb.end());
-        ints.insert(ints.end(), cplan.wb.begin(), cplan.wb.end());
-        CREATE_CUDA(cudaMalloc(&ctx->d_colkh, cplan.kh.size() * sizeof(int2)));
-        CREATE_CUDA(cudaMemcpy(ctx->d_colkh, cplan.kh.data(), cplan.kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        for (const std::vector<int> *v : {chunked ? &kplan.q : &cplan.q, chunked ? &kplan.sb : &cplan.sb,
+                                          chunked ? &kplan.wb : &cplan.wb, &kplan.rows})
+            ints.insert(ints.end(), v->begin(), v->end());
+        CREATE_CUDA(cudaMalloc(&ctx->d_colkh, kh.size() * sizeof(int2)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_colkh, kh.data(), kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
         CREATE_CUDA(cudaMalloc(&ctx->d_colint, ints.size() * sizeof(int)));
         CREATE_CUDA(cudaMemcpy(ctx->d_colint, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
-        CREATE_CUDA(cudaMalloc(&ctx->d_colpieces, std::max<size_t>(1, cplan.pieces.size()) * sizeof(int4)));
-        CREATE_CUDA(cudaMemcpy(ctx->d_colpieces, cplan.pieces.data(), cplan.pieces.size() * sizeof(int4),
+        CREATE_CUDA(cudaMalloc(&ctx->d_colpieces, std::max<size_t>(1, pieces.size()) * sizeof(int4)));
+        CREATE_CUDA(cudaMemcpy(ctx->d_colpieces, pieces.data(), pieces.size() * sizeof(int4),
                                cudaMemcpyHostToDevice));
         CREATE_CUDA(cudaMalloc(&ctx->d_X, 2 * plane * sizeof(float)));
         CREATE_CUDA(cudaMemset(ctx->d_X, 0, 2 * plane * sizeof(float)));
@@ -887,15 +923,33 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         mw.Glo = ctx->d_mix32 + 14 * plane;
         mw.partials32 = ctx->d_partials32;
         if (cols) {
+            const size_t nq = chunked ? kplan.q.size() : cplan.q.size();
+            const size_t nsb = chunked ? kplan.sb.size() : cplan.sb.size();
+            const size_t nwb = chunked ? kplan.wb.size() : cplan.wb.size();
             ops.col_kh = ctx->d_colkh;
             ops.col_q = ctx->d_colint;
-            ops.col_sb = ctx->d_colint + cplan.q.size();
-            ops.col_wb = ctx->d_colint + cplan.q.size() + cplan.sb.size();
+            ops.col_sb = ctx->d_colint + nq;
+            ops.col_wb = ctx->d_colint + nq + nsb;
             ops.col_pieces = ctx->d_colpieces;
-            ops.col_splits = cplan.splits;
-            ops.col_smem = cplan.smem;
-            ops.col_p_off = cplan.p_off;
-            ops.col_sp_off = cplan.sp_off;
+            if (chunked) {
+                ops.col_rowb = ctx->d_colint + nq + nsb + nwb;
+                ops.col_cs = kplan.cs;
+                ops.col_kc = kplan.kc;
+                ops.col_nc = kplan.nc;
+                ops.col_smem = kplan.smem;
+                ops.col_acc_off = kplan.acc_off;
+                ops.col_kh_off = kplan.kh_off;
+                ops.col_kh_slot = kplan.kh_slot;
+                ops.col_p_off = kplan.p_off;
+                ops.col_p_slot = kplan.p_slot;
+                ops.col_splits = kplan.cs;
+            } else {
+                ops.col_gather = gathered ? 1 : 0;
+                ops.col_splits = cplan.splits;
+                ops.col_smem = cplan.smem;
+                ops.col_p_off = cplan.p_off;
+                ops.col_sp_off = cplan.sp_off;
+            }
             ops.col_epi_off = ctx->epi_off;
             ops.col_psmem = ctx->persist_smem;
             mw.X = ctx->d_X;
@@ -917,7 +971,7 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
             }
             int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-            ctx->colmaps.gain_ctas = std::min(64, std::max(8, sms - (np / 16) * cplan.splits));
+            ctx->colmaps.gain_ctas = std::min(64, std::max(8, sms - (np / 16) * ops.col_splits));
             mw.cmaps = &ctx->colmaps;
         }
         mw.g = ctx->d_g32;

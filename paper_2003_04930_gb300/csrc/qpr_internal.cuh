@@ -86,6 +86,16 @@ struct DevOps {
     int col_smem;          // dynamic shared memory of the SpMM kernel
     int col_p_off;         // byte offset of the staged bundles in it
     int col_sp_off;        // byte offset of the staged diagonal (np floats) in it
+    // chunked column-block form (col_cs > 0): clusters of col_cs CTAs (the row
+    // splits [col_rowb[r], col_rowb[r + 1]) of one column block) share chunks
+    // of col_kc staged rows by multicast; col_nc chunks; per (split, chunk)
+    // block r * col_nc + c the entry range (col_q), bundles (col_sb) and warp
+    // starts (col_wb); shared memory: 2 chunk buffers, the accumulators
+    // (col_acc_off), 2 entry buffers of col_kh_slot bytes (col_kh_off), 2
+    // bundle buffers of col_p_slot bytes (col_p_off)
+    const int *col_rowb;
+    int col_cs, col_kc, col_nc, col_acc_off, col_kh_off, col_kh_slot, col_p_slot;
+    int col_gather;        // 1: the gather form (the SpMM reads delta from L2; plan of ColPlan, gather)
     int col_epi_off;       // persistent form: byte offset of the epilogue buffers (0: over the column block)
     int col_psmem;         // persistent form: dynamic shared memory of its launch
 };
@@ -220,9 +230,31 @@ struct ColPlan {
 // problem runs alone). A row's product does not depend on the plan (its
 // group sums its entries in order; zero padding never changes a sum that
 // starts at +0), so every plan gives bitwise the same X.
-bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits = 0);
+// gather: the plan of the gather form (no staged column block, any np; row
+// splits from enough CTAs for every SM several times over).
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits = 0, bool gather = false);
+cudaError_t set_gather_smem(int bytes);
 // Opt in to `bytes` of dynamic shared memory for the SpMM kernels.
 cudaError_t set_cols_smem(int bytes);
+// Host plan of the chunked column-block form (N too large to stage a whole
+// column block): device copies go to DevOps col_* as for ColPlan, plus the
+// split rows and the chunk geometry.
+struct ChunkPlan {
+    int cs = 0, kc = 0, nc = 0;
+    int smem = 0, acc_off = 0, kh_off = 0, kh_slot = 0, p_off = 0, p_slot = 0;
+    std::vector<int> rows;        // cs + 1
+    std::vector<int2> kh;
+    std::vector<int> q, sb, wb;   // per (split, chunk) block, as in ColPlan
+    std::vector<int4> pieces;
+};
+// Plans the chunked form (a cluster size and chunk rows whose shared memory
+// fits and whose clusters can be scheduled); false if none does. Sets the
+// kernel's attributes for the plan it returns.
+// kc > 0: chunks of kc staged rows (a multiple of 32) instead of the plan's choice.
+bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc = 0);
+// Opt in to `bytes` of dynamic shared memory (and clusters of cs > 8 CTAs)
+// for the chunked SpMM kernel.
+cudaError_t set_chunk_attrs(int bytes, int cs);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
 // Persistent form (stage_persist.cu): one cooperative launch runs up to
 // `steps` RK4 steps of the column-block form, grid barriers between the

@@ -77,6 +77,48 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
     warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X);
 }
 
+// Gather form of the SpMM, for N too large to stage a column block: CTA
+// (r, J) stages only its split's entries and bundles and reads each
+// nonzero's 16 values of block J straight from the stage input (two 64-byte
+// segments per row, from L2). The grid runs the row splits of one
+// column block next to each other, so the block's rows (np x 128 bytes) are
+// read from DRAM about once and then served by L2 to the splits.
+template <int STAGE>
+__global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(DevOps ops, MixedWork w) {
+    extern __shared__ uint8_t dyn_raw[];
+    __shared__ __align__(8) uint64_t bar_csr;
+    __shared__ int s_done;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = blockIdx.x, J = blockIdx.y;
+    const uint32_t s0 = tma::smem_u32(dyn_raw);
+    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);
+    int2 *sKH = reinterpret_cast<int2 *>(base);
+    int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
+    const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
+    const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
+    const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);
+    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * kBundleInt4);
+    if (tid == 0) {
+        tma::mbar_init(&bar_csr, 1);
+        tma::mbar_init_fence();
+        tma::mbar_expect_tx(&bar_csr, kh_bytes + p_bytes);
+        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar_csr);
+        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + kBundleInt4 * (size_t)p_base, p_bytes, &bar_csr);
+    }
+    const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
+    tma::grid_dependency_wait();
+    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    const bool ok = tma::mbar_wait(&bar_csr, 0);  // also before leaving: the copies land first (bounded)
+    if (s_done) return;
+    tma::launch_dependents();
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
+        return;
+    }
+    warp_bundles<false, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X);
+}
+
 // The gain of the stage input, rows shared over the grid; runs beside the
 // SpMM kernel (on SMs it leaves free).
 __global__ void __launch_bounds__(kANT) cols_gain_kernel(DevOps ops, MixedWork w) {
@@ -110,6 +152,115 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     epilogue_pair_in<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
 }
 
+// Chunked form, for N too large to stage a whole column block: a cluster of
+// col_cs CTAs (rank r: the row split [col_rowb[r], col_rowb[r + 1])) works on
+// one column block J = blockIdx.y. The block is streamed in chunks of col_kc
+// staged rows, double-buffered; each chunk is loaded once for the cluster
+// (its 32-row boxes dealt to the ranks round-robin, each box multicast to
+// every rank) and every CTA adds its rows' products with the chunk's
+// columns of H to accumulators in shared memory (per row: chunk by chunk,
+// in entry order within a chunk). A cluster barrier after each chunk frees
+// its buffer for the chunk two ahead. The accumulators go to X at the end.
+//
+// Every wait is bounded; a CTA whose wait gave up reports it and stops
+// computing but still issues its copies, waits for every chunk and takes
+// every cluster barrier, so no peer is left at a barrier or without its
+// boxes, and no copy into the CTA is in flight when it leaves.
+__global__ void __launch_bounds__(kANT, 1) cols_chunk_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
+                                                            MixedWork w) {
+    extern __shared__ uint8_t dyn_raw[];
+    __shared__ __align__(8) uint64_t full[2], csr[2];
+    __shared__ int s_done;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = blockIdx.x, J = blockIdx.y;  // cluster (col_cs, 1, 1): the rank is blockIdx.x
+    const int np = ops.np, kc = ops.col_kc, nc = ops.col_nc, cs = ops.col_cs;
+    const uint32_t s0 = tma::smem_u32(dyn_raw);
+    // the same offset in every CTA of the cluster (multicast writes there)
+    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);
+    // buffer b of the chunks, entries and bundles
+    auto buf = [&](int b) { return reinterpret_cast<float *>(base) + (size_t)b * kc * kRowFloats; };
+    auto skh = [&](int b) { return reinterpret_cast<int2 *>(base + ops.col_kh_off + b * ops.col_kh_slot); };
+    auto spc = [&](int b) { return reinterpret_cast<int4 *>(base + ops.col_p_off + b * ops.col_p_slot); };
+    float *acc = reinterpret_cast<float *>(base + ops.col_acc_off);
+    const int row0 = ops.col_rowb[r], nrows = ops.col_rowb[r + 1] - row0;
+    const uint16_t mask = (uint16_t)((1u << cs) - 1u);
+    // block (r, c): this split's entries and bundles for chunk c, into buffer b
+    auto issue_csr = [&](int c, int b) {
+        const int blk = r * nc + c;
+        const int q0 = ops.col_q[2 * blk], q1 = ops.col_q[2 * blk + 1];
+        const int p0 = ops.col_sb[blk], p1 = ops.col_sb[blk + 1];
+        const uint32_t kh_bytes = (uint32_t)((q1 - q0) * 8), p_bytes = (uint32_t)((p1 - p0) * 16 * kBundleInt4);
+        tma::mbar_expect_tx(&csr[b], kh_bytes + p_bytes);
+        if (kh_bytes) tma::load_bulk(skh(b), ops.col_kh + q0, kh_bytes, &csr[b]);
+        if (p_bytes) tma::load_bulk(spc(b), ops.col_pieces + kBundleInt4 * (size_t)p0, p_bytes, &csr[b]);
+    };
+    // chunk c (staged rows [c kc, min(np, (c + 1) kc)), a multiple of 32):
+    // this rank's boxes, multicast; every rank expects the whole chunk
+    auto issue_chunk = [&](int c, int b) {
+        const int c0 = c * kc, rows = min(kc, np - c0);
+        tma::mbar_expect_tx(&full[b], (uint32_t)rows * kRowFloats * 4);
+        for (int m = r; m * kBoxRows < rows; m += cs)
+            tma::load_3d_multicast(buf(b) + (size_t)m * kBoxRows * kRowFloats, &tm, &full[b], J * kCW, 0,
+                                   c0 + m * kBoxRows, mask);
+    };
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tma::mbar_init(&full[b], 1);
+            tma::mbar_init(&csr[b], 1);
+        }
+        tma::mbar_init_fence();
+        issue_csr(0, 0);
+        if (nc > 1) issue_csr(1, 1);
+    }
+    for (int e = tid; e < nrows * (kRowFloats / 4); e += kANT)
+        reinterpret_cast<float4 *>(acc)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tma::grid_dependency_wait();
+    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    if (s_done) {
+        // uniform over the cluster (set by an earlier kernel); no multicast was issued
+        if (tid == 0) {
+            tma::mbar_wait(&csr[0], 0);
+            if (nc > 1) tma::mbar_wait(&csr[1], 0);
+        }
+        return;
+    }
+    tma::launch_dependents();
+    tma::cluster_sync();  // every rank's barriers are initialised before the first multicast
+    if (tid == 0) {
+        issue_chunk(0, 0);
+        if (nc > 1) issue_chunk(1, 1);
+    }
+    bool bad = false;
+    for (int c = 0; c < nc; ++c) {
+        const int b = c & 1;
+        const uint32_t par = (uint32_t)(c >> 1) & 1u;
+        const bool ok_csr = tma::mbar_wait(&csr[b], par);
+        const bool ok_full = tma::mbar_wait(&full[b], par);
+        if (__syncthreads_or(!(ok_csr && ok_full)) && !bad) {
+            bad = true;
+            if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
+        }
+        if (!bad) {
+            const int blk = r * nc + c;
+            const int *wb = ops.col_wb + blk * kAWarps + warp;
+            warp_bundles<true>(buf(b), skh(b), spc(b), ops.col_sb[blk], wb[0], wb[1], J, np, w.X, acc, row0);
+        }
+        tma::cluster_sync();  // every rank is done with buffer b
+        if (c + 2 < nc && tid == 0) {
+            issue_csr(c + 2, b);
+            issue_chunk(c + 2, b);
+        }
+    }
+    if (bad) return;
+    const size_t plane = (size_t)np * np;
+    for (int e = tid; e < nrows * (kRowFloats / 4); e += kANT) {
+        const int i = e >> 3, p = e & 7;
+        float *dst = w.X + (p < 4 ? 0 : plane) + (size_t)(row0 + i) * np + J * kCW + 4 * (p & 3);
+        *reinterpret_cast<float4 *>(dst) = reinterpret_cast<const float4 *>(acc)[e];
+    }
+}
+
 int max_smem_optin(int device) {
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -124,13 +275,18 @@ cudaError_t set_spmm_attr(int bytes) {
     return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Bundles of one split's rows [r0, r1): long rows alone, the others 4 kRPG
-// at a time by decreasing length; dealt to the warps longest first, each to
-// the least loaded warp. Appends, per warp, the bundles' descriptors and
-// their interleaved, zero-padded entries (relative offsets from `kh_base`),
-// and the warps' first bundles.
-void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std::vector<int2> &kh,
-                   std::vector<int4> &pieces, std::vector<int> &wb) {
+// The entries of row i (column relative to a chunk start, FP32 value bits).
+using RowEntries = std::vector<std::vector<int2>>;
+
+// Bundles of one split's rows [r0, r1) with the entries ent[i - r0]: long
+// rows alone, the others 4 kRPG at a time by decreasing length; dealt to the
+// warps longest first, each to the least loaded warp. Appends, per warp, the
+// bundles' descriptors and their interleaved, zero-padded entries (relative
+// offsets from `kh_base`), and the warps' first bundles.
+// skip_empty: rows without entries get no bundle (their sums are kept
+// elsewhere); otherwise they get zero rounds, which store zeros.
+void split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::vector<int2> &kh,
+                   std::vector<int4> &pieces, std::vector<int> &wb, bool skip_empty = false) {
     constexpr int kSlots = 4 * kRPG;
     struct Bundle {
         int rows[kSlots];
@@ -140,14 +296,7 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
     };
     std::vector<Bundle> bs;
     std::vector<int> shortrows;
-    auto row_len = [&](int i) { return i < n ? (int)(h.hptr[i + 1] - h.hptr[i]) : 0; };
-    auto entry = [&](int i, int e) {
-        const size_t q = (size_t)h.hptr[i] + e;
-        const float v = (float)h.hval[q];
-        int bits;
-        memcpy(&bits, &v, 4);
-        return make_int2(h.hcol[q], bits);
-    };
+    auto row_len = [&](int i) { return (int)ent[i - r0].size(); };
     auto fresh = [&](int T, bool lng) {
         Bundle b;
         for (int j = 0; j < kSlots; ++j) b.rows[j] = -1;
@@ -161,7 +310,7 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
             Bundle b = fresh((row_len(i) + kSlots - 1) / kSlots, true);
             b.rows[0] = i;
             bs.push_back(b);
-        } else {
+        } else if (row_len(i) > 0 || !skip_empty) {
             shortrows.push_back(i);
         }
     }
@@ -195,10 +344,10 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
                         int2 v = make_int2(0, 0);
                         if (b.lng) {
                             const int e = kSlots * t + kRPG * g + sl;
-                            if (e < row_len(b.rows[0])) v = entry(b.rows[0], e);
+                            if (e < row_len(b.rows[0])) v = ent[b.rows[0] - r0][e];
                         } else {
                             const int row = b.rows[g + 4 * sl];
-                            if (row >= 0 && t < row_len(row)) v = entry(row, t);
+                            if (row >= 0 && t < row_len(row)) v = ent[row - r0][t];
                         }
                         kh.push_back(v);
                     }
@@ -206,10 +355,25 @@ void split_bundles(const HostOps &h, int r0, int r1, int n, size_t kh_base, std:
     }
 }
 
+// Row i's entries with a column in [c0, c1), columns relative to c0, in CSR order.
+std::vector<int2> row_entries(const HostOps &h, int i, int c0, int c1) {
+    std::vector<int2> out;
+    if (i >= (int)h.n) return out;
+    for (int64_t q = h.hptr[i]; q < h.hptr[i + 1]; ++q) {
+        const int k = h.hcol[q];
+        if (k < c0 || k >= c1) continue;
+        const float v = (float)h.hval[q];
+        int bits;
+        memcpy(&bits, &v, 4);
+        out.push_back(make_int2(k - c0, bits));
+    }
+    return out;
+}
+
 }  // namespace
 
-bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits) {
-    if (np > kColMaxNp || np % kBoxRows != 0) return false;
+bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_splits, bool gather) {
+    if ((!gather && np > kColMaxNp) || np % kBoxRows != 0) return false;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
         cudaGetLastError();
@@ -224,8 +388,18 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         const double nz = (i < n) ? (double)(h.hptr[i + 1] - h.hptr[i]) : 0.0;
         cum[i + 1] = cum[i] + nz + 4.0;
     }
-    const int s0 = min_splits > 0 ? min_splits : std::min(std::max(1, sms / ncb), 16);
-    for (int s = s0; s <= 16; ++s) {
+    // gather form: at least kGatherWaves waves of kGatherCtasPerSm CTAs per
+    // SM, up to 64 splits
+    const int s_max = gather ? 64 : 16;
+    const int s0 = min_splits > 0 ? min_splits
+                   : gather ? std::min(std::max(1, (kGatherWaves * kGatherCtasPerSm * sms + ncb - 1) / ncb), s_max)
+                            : std::min(std::max(1, sms / ncb), 16);
+    int sm_per_sm = 0;
+    if (cudaDeviceGetAttribute(&sm_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
+        cudaGetLastError();
+        sm_per_sm = 0;
+    }
+    for (int s = s0; s <= s_max; ++s) {
         ColPlan pl;
         pl.splits = s;
         std::vector<int> rows(s + 1, 0);
@@ -241,7 +415,9 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
             const size_t kb = pl.kh.size();  // even: every split's block starts 16-byte aligned
             const int first = (int)(pl.pieces.size() / kBundleInt4);
             pl.sb.push_back(first);
-            split_bundles(h, rows[k], rows[k + 1], n, kb, pl.kh, pl.pieces, pl.wb);
+            RowEntries ent;
+            for (int i = rows[k]; i < rows[k + 1]; ++i) ent.push_back(row_entries(h, i, 0, np));
+            split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb);
             if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
             pl.q.push_back((int)kb);
             pl.q.push_back((int)pl.kh.size());
@@ -250,12 +426,25 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         }
         pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
-        pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
-        pl.sp_off = (int)((size_t)pl.p_off + p_max);
-        const size_t smem = (size_t)pl.sp_off + (size_t)np * 4 + 128;
+        size_t smem, cap;
+        if (gather) {
+            // entries, then bundles; small enough for kGatherCtasPerSm CTAs per SM
+            pl.p_off = (int)kh_max;
+            pl.sp_off = 0;
+            smem = (size_t)pl.p_off + p_max + 128;
+            // per CTA: its dynamic and static shared memory and the 1 KB the
+            // system reserves (the 1 KB below covers the static part)
+            cap = std::min({(size_t)smem_max, (size_t)sm_per_sm / kGatherCtasPerSm - 1024,
+                            (size_t)kGatherSplitBytes + 1024});
+        } else {
+            pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
+            pl.sp_off = (int)((size_t)pl.p_off + p_max);
+            smem = (size_t)pl.sp_off + (size_t)np * 4 + 128;
+            cap = (size_t)smem_max;
+        }
         // 1 KB left for the static shared memory of the kernels (the batched
         // kernel keeps its problem descriptor there)
-        if (smem_max > 1024 && smem <= (size_t)smem_max - 1024) {
+        if (cap > 1024 && smem <= cap - 1024) {
             pl.smem = (int)smem;
             if (pl.kh.empty()) pl.kh.assign(2, make_int2(0, 0));
             plan = std::move(pl);
@@ -263,6 +452,108 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         }
     }
     return false;
+}
+
+bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc_force) {
+    if (np % kBoxRows != 0) return false;
+    int sms = 0, cl = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, device) != cudaSuccess || sms <= 0 || !cl) {
+        cudaGetLastError();
+        return false;
+    }
+    const int smem_max = max_smem_optin(device);
+    const int n = (int)h.n;
+    const int ncb = np / kCW;
+    // each row's entries (column, FP32 value bits) in CSR order
+    RowEntries all(np);
+    for (int i = 0; i < n && i < np; ++i) all[i] = row_entries(h, i, 0, np);
+    std::vector<double> cum(np + 1, 0.0);
+    for (int i = 0; i < np; ++i) cum[i + 1] = cum[i] + (double)all[i].size() + 16.0;
+    // (cluster size, rows per chunk): the portable cluster size and the
+    // largest chunks first
+    std::vector<int2> cands = {{8, 512}, {8, 256}, {16, 512}, {16, 256}, {8, 128}, {16, 128}, {4, 128}};
+    if (kc_force > 0) cands = {{8, kc_force}, {16, kc_force}, {4, kc_force}};
+    for (const int2 cand : cands) {
+        const int cs = cand.x, kc = std::min(cand.y, np);
+        ChunkPlan pl;
+        pl.cs = cs;
+        pl.kc = kc;
+        pl.nc = (np + kc - 1) / kc;
+        // row splits by cost (nonzeros + a per-row overhead)
+        pl.rows.assign(cs + 1, 0);
+        int i = 0;
+        for (int k = 1; k < cs; ++k) {
+            const double target = cum[np] * (double)k / (double)cs;
+            while (i < np && cum[i] < target) ++i;
+            pl.rows[k] = std::max(pl.rows[k - 1], i);
+        }
+        pl.rows[cs] = np;
+        int rows_max = 0;
+        for (int k = 0; k < cs; ++k) rows_max = std::max(rows_max, pl.rows[k + 1] - pl.rows[k]);
+        size_t kh_max = 0, p_max = 0;
+        for (int k = 0; k < cs; ++k) {
+            const int r0 = pl.rows[k], r1 = pl.rows[k + 1];
+            for (int c = 0; c < pl.nc; ++c) {
+                const int c0 = c * kc, c1 = std::min(np, c0 + kc);
+                RowEntries ent(r1 - r0);
+                for (int row = r0; row < r1; ++row)
+                    for (const int2 &e : all[row])
+                        if (e.x >= c0 && e.x < c1) ent[row - r0].push_back(make_int2(e.x - c0, e.y));
+                const size_t kb = pl.kh.size();  // even: every block starts 16-byte aligned
+                const int first = (int)(pl.pieces.size() / kBundleInt4);
+                pl.sb.push_back(first);
+                split_bundles(r0, r1, ent, kb, pl.kh, pl.pieces, pl.wb, /*skip_empty=*/true);
+                if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
+                pl.q.push_back((int)kb);
+                pl.q.push_back((int)pl.kh.size());
+                kh_max = std::max(kh_max, (pl.kh.size() - kb) * 8);
+                p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / kBundleInt4) - first) * 16 * kBundleInt4);
+            }
+        }
+        pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
+        pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
+        pl.kh_slot = (int)std::max<size_t>(16, kh_max);
+        pl.p_slot = (int)std::max<size_t>(16, p_max);
+        pl.acc_off = 2 * kc * kRowFloats * 4;
+        pl.kh_off = pl.acc_off + rows_max * kRowFloats * 4;
+        pl.p_off = pl.kh_off + 2 * pl.kh_slot;
+        const size_t smem = (size_t)pl.p_off + 2 * (size_t)pl.p_slot + 128;
+        if (smem_max <= 1024 || smem > (size_t)smem_max - 1024) continue;
+        pl.smem = (int)smem;
+        // the cluster must be schedulable with this shared memory
+        if (set_chunk_attrs(pl.smem, cs) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int clusters = 0;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs, ncb);
+        cfg.blockDim = dim3(kANT);
+        cfg.dynamicSmemBytes = (size_t)pl.smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&clusters, cols_chunk_kernel, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        if (pl.kh.empty()) pl.kh.assign(2, make_int2(0, 0));
+        plan = std::move(pl);
+        return true;
+    }
+    return false;
+}
+
+cudaError_t set_chunk_attrs(int bytes, int cs) {
+    cudaError_t e = cudaFuncSetAttribute(cols_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && cs > 8)
+        e = cudaFuncSetAttribute(cols_chunk_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
 bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps) {
@@ -291,6 +582,15 @@ cudaError_t set_cols_smem(int bytes) {
     return e;
 }
 
+cudaError_t set_gather_smem(int bytes) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 // Stage inputs: stage 1 D (map 0), stage 2 da (map 1), stage 3 db (map 2),
 // stage 4 da (map 1). parts & 1: the SpMM kernel, parts & 2: the epilogue.
 template <typename K, typename... A>
@@ -308,9 +608,30 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, A.
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// The chunked SpMM: clusters of col_cs CTAs along x, with programmatic
+// dependent launch.
+static void launch_chunks(const CUtensorMap &tm, const DevOps &ops, const MixedWork &w, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ops.col_cs, ops.np / kCW);
+    cfg.blockDim = dim3(kANT);
+    cfg.dynamicSmemBytes = (size_t)ops.col_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = ops.col_cs;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, cols_chunk_kernel, tm, ops, w);
+}
+
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts) {
     const ColMaps &m = *w.cmaps;
-    const dim3 ga(ops.np / kCW, ops.col_splits);
+    // whole block: (J, r); gather: (r, J), the splits of a block side by side
+    const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCW) : dim3(ops.np / kCW, ops.col_splits);
     const size_t sm = (size_t)ops.col_smem;
     const CUtensorMap &tm = m.d[stage == 1 ? 0 : (stage == 3 ? 2 : 1)];
     if (parts & 1) {
@@ -319,11 +640,22 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
         cudaStreamWaitEvent(m.side, m.fork, 0);
         cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
         cudaEventRecord(m.join, m.side);
-        switch (stage) {
-            case 1: launch_pdl(cols_spmm_kernel<1>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-            case 2: launch_pdl(cols_spmm_kernel<2>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-            case 3: launch_pdl(cols_spmm_kernel<3>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-            default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+        if (ops.col_cs > 0) {
+            launch_chunks(tm, ops, w, s);
+        } else if (ops.col_gather) {
+            switch (stage) {
+                case 1: launch_pdl(cols_gather_kernel<1>, ga, dim3(kANT), sm, s, ops, w); break;
+                case 2: launch_pdl(cols_gather_kernel<2>, ga, dim3(kANT), sm, s, ops, w); break;
+                case 3: launch_pdl(cols_gather_kernel<3>, ga, dim3(kANT), sm, s, ops, w); break;
+                default: launch_pdl(cols_gather_kernel<4>, ga, dim3(kANT), sm, s, ops, w); break;
+            }
+        } else {
+            switch (stage) {
+                case 1: launch_pdl(cols_spmm_kernel<1>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+                case 2: launch_pdl(cols_spmm_kernel<2>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+                case 3: launch_pdl(cols_spmm_kernel<3>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+                default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+            }
         }
         cudaStreamWaitEvent(s, m.join, 0);
     }

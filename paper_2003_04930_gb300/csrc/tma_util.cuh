@@ -77,6 +77,30 @@ __device__ __forceinline__ void load_bulk(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// 3-D tiled load multicast to the CTAs of the cluster in cta_mask: the box
+// lands at the same shared-memory offset in each, and each CTA's mbarrier at
+// the offset of `bar` receives the bytes.
+__device__ __forceinline__ void load_3d_multicast(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                                  int c2, uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%3, %4, %5}], [%2], %6;\n" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
+        : "memory");
+}
+
+// Thread-block cluster: this CTA's rank, and the cluster-wide barrier (every
+// thread of every CTA of the cluster; release/acquire of shared and global
+// memory).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // Programmatic dependent launch: wait until the previous kernel in the
 // stream has completed and its memory is visible; let the next kernel start
 // its prologue. Both are no-ops in a kernel launched without the attribute.

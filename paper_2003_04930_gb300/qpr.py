@@ -22,12 +22,13 @@ QPR_FP64, QPR_MIXED = 0, 1
 QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
 QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
-QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES, QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 0, 1, 2, 3
+(QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES, QPR_SPARSE_FORM_COLUMNS_PERSISTENT,
+ QPR_SPARSE_FORM_COLUMNS_CHUNKED, QPR_SPARSE_FORM_COLUMNS_GATHER) = 0, 1, 2, 3, 4, 5
 
 # every entry point declared in include/qpr.h
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
-    "qpr_n", "qpr_backend", "qpr_sparse_form", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
+    "qpr_n", "qpr_backend", "qpr_sparse_form", "qpr_sparse_plan", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
     "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune",
@@ -40,7 +41,7 @@ class qpr_options(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("backend", ctypes.c_int32),
                 ("ref_refresh", ctypes.c_int32), ("sparse_form", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("chunk_rows", ctypes.c_int32), ("row_splits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class qpr_stats(ctypes.Structure):
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_backend.restype = ctypes.c_int32
     lib.qpr_sparse_form.argtypes = [vp]
     lib.qpr_sparse_form.restype = ctypes.c_int32
+    lib.qpr_sparse_plan.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.qpr_sparse_plan.restype = st
     lib.qpr_h_spread.argtypes = [vp]
     lib.qpr_h_spread.restype = f64
     lib.qpr_max_stable_dt.argtypes = [vp]
@@ -183,7 +186,7 @@ class Solver:
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0, row_splits=0):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -198,6 +201,8 @@ class Solver:
         opt.backend = int(backend)
         opt.ref_refresh = int(ref_refresh)
         opt.sparse_form = int(sparse_form)
+        opt.chunk_rows = int(chunk_rows)
+        opt.row_splits = int(row_splits)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         h = ctypes.c_void_p()
@@ -239,9 +244,17 @@ class Solver:
 
     @property
     def sparse_form(self) -> int:
-        """QPR_SPARSE_FORM_COLUMNS, _COLUMNS_PERSISTENT or _TILES (0: not the
-        mixed sparse form)."""
+        """QPR_SPARSE_FORM_COLUMNS, _COLUMNS_PERSISTENT, _COLUMNS_CHUNKED,
+        _COLUMNS_GATHER or _TILES (0: not the mixed sparse form)."""
         return int(self._lib.qpr_sparse_form(self._h))
+
+    @property
+    def sparse_plan(self) -> dict:
+        """Geometry of the column-block product: row splits (cluster size),
+        chunk rows (0: whole block), chunks, shared-memory bytes."""
+        out = (ctypes.c_int32 * 4)()
+        self._raise(self._lib.qpr_sparse_plan(self._h, out))
+        return {"splits": out[0], "chunk_rows": out[1], "chunks": out[2], "smem": out[3]}
 
     @property
     def h_spread(self) -> float:

@@ -1,14 +1,20 @@
 """The forms of the FP32 sparse stage of QPR_MIXED: the column-block form
 (two launches per stage), its persistent form (one cooperative launch per
-block of steps) and the tile-pair form.
+block of steps), its gather form (rows of the block read from L2, for any
+N), its chunked form (clusters streaming the column block in chunks, for any
+N) and the tile-pair form.
 
-The two column forms run the same device arithmetic (row products in entry
-order, the same gain and epilogue sums, the same stop decision), so their
-states, step counts and residuals are bitwise equal. The tile-pair form sums
-the products in another FP32 order and is held, like every form, to the
-mixed form's tolerances against the FP64 oracle: trajectories (t = 1.5)
+The whole-block and gather column forms run the same device arithmetic (row
+products in entry order, the same gain and epilogue sums, the same stop
+decision), so their states, step counts and residuals are bitwise equal.
+The chunked form sums each row chunk by chunk, so it equals them bitwise
+when the block is one chunk. The chunked and tile-pair forms sum the
+products in other FP32 orders and are held, like every form, to the mixed
+form's tolerances against the FP64 oracle: trajectories (t = 1.5)
 ||drho||_F <= 1e-6 and max|dp| <= 1e-6 max p, steady states ||drho||_F <= 1e-6
-and max|dp| <= 1e-7 max p.
+and max|dp| <= 1e-7 max p. Small chunk_rows make the chunked form stream
+several chunks (both buffers, both barrier phases, a ragged last chunk
+where 32-row boxes do not fill it) at sizes the oracle runs quickly.
 """
 import numpy as np
 import pytest
@@ -21,12 +27,21 @@ from paper_2003_04930_gb300 import qpr as Q
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-FORMS = (Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_TILES)
+FORMS = (Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_COLUMNS_GATHER,
+         Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, Q.QPR_SPARSE_FORM_TILES)
+BITWISE = (Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_COLUMNS_GATHER)  # equal to COLUMNS
 
 
-def _solver(g, omega, form, refresh=32):
+def _chunk_rows(n):
+    """Chunks of 32 to 128 rows: 2 to 7 chunks at these sizes."""
+    return 32 if n <= 200 else (64 if n <= 320 else 128)
+
+
+def _solver(g, omega, form, refresh=32, chunk_rows=None):
+    if chunk_rows is None:
+        chunk_rows = _chunk_rows(g.n) if form == Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED else 0
     return Solver.from_edges(g, alpha=0.85, omega=omega, precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE,
-                             sparse_form=form, ref_refresh=refresh)
+                             sparse_form=form, ref_refresh=refresh, chunk_rows=chunk_rows)
 
 
 def _close(got, ref, prel):
@@ -39,14 +54,17 @@ def test_default_form_is_columns_where_it_fits():
     s = Solver.from_edges(graphs.heavy_tailed(300, 1), precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE)
     assert s.sparse_form == Q.QPR_SPARSE_FORM_COLUMNS
     big = Solver.from_edges(graphs.heavy_tailed(2000, 1), precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE)
-    assert big.sparse_form == Q.QPR_SPARSE_FORM_TILES  # 2016 padded rows: the staged block does not fit
+    assert big.sparse_form == Q.QPR_SPARSE_FORM_COLUMNS_GATHER  # 2016 padded rows: the whole block does not fit
+    plan = big.sparse_plan
+    assert plan["splits"] >= 1 and plan["chunk_rows"] == 0 and plan["chunks"] == 1
     fp64 = Solver.from_edges(graphs.heavy_tailed(300, 1), backend=Q.QPR_BACKEND_SPARSE)
     assert fp64.sparse_form == 0
 
 
-def test_columns_form_refused_where_it_does_not_fit():
+@pytest.mark.parametrize("form", [Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT])
+def test_whole_block_forms_refused_where_they_do_not_fit(form):
     with pytest.raises(Q.QprError) as e:
-        _solver(graphs.heavy_tailed(2000, 1), 0.8, Q.QPR_SPARSE_FORM_COLUMNS)
+        _solver(graphs.heavy_tailed(2000, 1), 0.8, form)
     assert e.value.status == Q.QPR_E_ARG
 
 
@@ -65,7 +83,13 @@ def test_forms_trajectory(n, omega, refresh):
         got[form] = d.cpu().numpy()
         _close(got[form], ref, 1e-6)
         assert np.abs(got[form] - got[form].conj().T).max() == 0.0
-    np.testing.assert_array_equal(got[Q.QPR_SPARSE_FORM_COLUMNS], got[Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT])
+    for form in BITWISE:
+        np.testing.assert_array_equal(got[form], got[Q.QPR_SPARSE_FORM_COLUMNS])
+    # one chunk: the whole-block sums
+    s = _solver(g, omega, Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, refresh, chunk_rows=4096)
+    d = torch.from_numpy(rho0.copy()).to(DEV)
+    s.evolve(d, 0.01, 150)
+    np.testing.assert_array_equal(d.cpu().numpy(), got[Q.QPR_SPARSE_FORM_COLUMNS])
 
 
 @pytest.mark.parametrize("n,omega", [(150, 0.8), (400, 0.3)])
@@ -84,9 +108,10 @@ def test_forms_steady_state(n, omega):
         assert abs(st["steps"] - steps_ref) <= 1
         stats[form], states[form] = st, d.cpu().numpy()
         _close(states[form], ref, 1e-7)
-    a, b = Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT
-    assert stats[a]["steps"] == stats[b]["steps"] and stats[a]["residual"] == stats[b]["residual"]
-    np.testing.assert_array_equal(states[a], states[b])
+    a = Q.QPR_SPARSE_FORM_COLUMNS
+    for b in BITWISE:
+        assert stats[a]["steps"] == stats[b]["steps"] and stats[a]["residual"] == stats[b]["residual"]
+        np.testing.assert_array_equal(states[a], states[b])
 
 
 def test_persistent_form_stops_at_max_steps():
@@ -98,3 +123,31 @@ def test_persistent_form_stops_at_max_steps():
     assert e.value.status == Q.QPR_E_NOT_CONVERGED
     ref = Oracle.from_edges(g, alpha=0.85, omega=0.8).evolve(graphs.maximally_mixed(120), 0.01, 45)
     _close(d.cpu().numpy(), ref, 1e-6)
+
+
+@pytest.fixture(scope="module")
+def large_case():
+    n, omega = 2000, 0.8
+    g = graphs.heavy_tailed(n, 5)
+    rho0 = graphs.random_density(n, 4, rank=3)
+    ref = Oracle.from_edges(g, alpha=0.85, omega=omega).evolve(rho0, 0.01, 40)
+    return g, omega, rho0, ref
+
+
+@pytest.mark.parametrize("form,chunk_rows", [(Q.QPR_SPARSE_FORM_COLUMNS_GATHER, 0),
+                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 0),
+                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 96),
+                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 512),
+                                             (Q.QPR_SPARSE_FORM_TILES, 0)])
+def test_large_n_trajectory(large_case, form, chunk_rows):
+    # N = 2000 (2016 padded rows), beyond the whole-block form; the chunked
+    # form with its default plan, 96-row chunks (21, the last of 96 rows) and
+    # 512-row chunks (4, the last of 480 rows)
+    g, omega, rho0, ref = large_case
+    s = _solver(g, omega, form, chunk_rows=chunk_rows)
+    assert s.sparse_form == form
+    d = torch.from_numpy(rho0.copy()).to(DEV)
+    s.evolve(d, 0.01, 40)
+    got = d.cpu().numpy()
+    _close(got, ref, 1e-6)
+    assert np.abs(got - got.conj().T).max() == 0.0
