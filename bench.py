@@ -302,6 +302,28 @@ def run_ours(a):
                 "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
                 "peak_source": f"bf16_tflops of {peak_src}"}
     elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
+            s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER:
+        # gather SpMM: its DRAM floor is one read of the stage input and one
+        # write of X (2 x 8 np^2 bytes); its nonzeros gather nnz(H) x np x 8
+        # bytes of row segments, served mostly by L2 (no measured L2 peak)
+        npad = ((n + 31) // 32) * 32
+        alg = 16 * npad * npad
+        gathered = h_nonzeros(g) * npad * 8
+        ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
+        epi_alg = 66 * n * n
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "cols_gather_kernel",
+                "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
+                "peak_source": f"hbm_gbs of {peak_src}",
+                "l2_gather": {"bytes_per_launch": gathered,
+                              "achieved_gbs": gathered / (prof["gain_ms"] * 1e-3) / 1e9},
+                "epilogue": {"kernel": "cols_epi_kernel", "bound": "hbm", "launch_ms": prof["stage_ms"],
+                             "alg_bytes_per_launch": epi_alg, "traffic": None,
+                             "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                             "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                             "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
+                "note": "launch_ms from CUDA events around each launch (includes the launch gap)"}
+    elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
             s.sparse_form in (qpr.QPR_SPARSE_FORM_COLUMNS, qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED):
         chunked = s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED
         # column-block SpMM: every nonzero of H reads its row slice of each
@@ -366,13 +388,16 @@ def run_ours(a):
     if s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
         form = ("mixed: fp32 column-block SpMM from TMA-staged shared memory + tile-pair epilogue, "
                 "float-float delta accumulation, fp64 reference/residual")
+    elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER:
+        form = ("mixed: fp32 column-block SpMM gathering row segments from L2 + tile-pair epilogue, "
+                "float-float delta accumulation, fp64 reference/residual")
     elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED:
         form = ("mixed: fp32 column-block SpMM, block streamed in chunks multicast over a thread-block cluster "
                 "+ tile-pair epilogue, float-float delta accumulation, fp64 reference/residual")
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",
-            "config": dict(workload_config(a), form=form, ref_refresh=a.ref_refresh,
+            "config": dict(workload_config(a), form=form, ref_refresh=a.ref_refresh, sparse_plan=s.sparse_plan,
                            parallelism=f"replicas{world}"),
             "rk4_steps_to_converge": steps_conv, "rk4_steps_per_s": steps_conv / (total / a.steps),
             "residual": stats[-1]["residual"], "roofline": roof, "clocks": clocks,
