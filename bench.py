@@ -286,6 +286,7 @@ def run_ours(a):
         total = float(t.item())
     value = total / (a.steps * world)
     steps_conv = stats[-1]["steps"]
+    rho_solved = rho.clone()  # this form's steady state, compared with the FP64 sparse form's below
 
     # per-kernel durations on the solver's stream, same workload and state
     prof = s.profile_step(rho, a.dt, 20)
@@ -429,7 +430,13 @@ def run_ours(a):
         stf = sf.steady_state(rho, a.dt, a.tol, a.max_steps)
         e1.record()
         e1.synchronize()
-        line["fp64_sparse"] = {"time_to_steady_state_s": e0.elapsed_time(e1) / 1e3, "steps": stf["steps"]}
+        # error of this form's steady state against the exact FP64 form (itself held to the oracle by the
+        # tests): the precision form's stated bounds are max|dp| <= 1e-7 max p and ||drho||_F <= 1e-6
+        p_ours = torch.diagonal(rho_solved).real
+        p_fp64 = torch.diagonal(rho).real
+        line["fp64_sparse"] = {"time_to_steady_state_s": e0.elapsed_time(e1) / 1e3, "steps": stf["steps"],
+                               "max_dp_rel": float((p_ours - p_fp64).abs().max() / p_fp64.abs().max()),
+                               "fro_drho": float(torch.linalg.norm(rho_solved - rho))}
         sf.close()
 
     # the learned warm start (network trained by train_warmstart, weights in the package): inference plus the
