@@ -42,9 +42,16 @@ constexpr int B_BYTES = 2 * TB * BK * 2;    // 32 KB (Re rows then -Im rows)
 constexpr int OFF_AI = 0, OFF_AJ = A_BYTES, OFF_BJ = 2 * A_BYTES, OFF_BI = 2 * A_BYTES + B_BYTES;
 constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // 96 KB
 constexpr int NTHREADS = 256;
-constexpr int LDS = 2 * TB + 1;         // staged X_JI row (floats)
+// Epilogue, per chunk of EC columns b of tile (I, J): X_JI rows b staged as
+// [EC][LDX2] (A 128 | B 128), X_IJ columns b as [TB][LDY] (A EC | B EC), and
+// the chunk's outputs transposed as 4 x [EC][LDO2] for the mirrored write;
+// the paddings make every access pattern below bank-conflict free.
+constexpr int EC = 32;
+constexpr int LDX2 = 2 * TB + 1;
+constexpr int LDY = 2 * EC + 1;
+constexpr int LDO2 = TB + 1;
 constexpr int SMEM_PIPE = NSTAGE * STAGE_BYTES;
-constexpr int SMEM_EPI = TB * LDS * 4;
+constexpr int SMEM_EPI = (EC * LDX2 + TB * LDY + 4 * EC * LDO2) * 4;
 constexpr int SMEM_BYTES = (SMEM_PIPE > SMEM_EPI ? SMEM_PIPE : SMEM_EPI) + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -109,23 +116,15 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &h0, __nv_bfloat16
     h2 = __float2bfloat16_rn(r2);
 }
 
-// Write the split of one delta entry (a, b) = (re, im) into the B-operand
-// planes [level][plane][row][k] and its mirror (b, a): plane 0 holds Re delta
-// (symmetric), plane 1 holds -Im delta (whose value at (b, a) is +im).
-__device__ __forceinline__ void put_split(__nv_bfloat16 *sp, size_t plane, int ga, int gb, int np, float re,
-                                          float im, bool mirror) {
-    __nv_bfloat16 r0, r1, r2, i0, i1, i2, m0, m1, m2;
+// Write the split of one delta entry (re, im) at offset o of the B-operand
+// planes [level][plane][row][k]: plane 0 holds Re delta (symmetric), plane 1
+// holds -Im delta (so the mirrored entry, conj, stores +im there).
+__device__ __forceinline__ void put_split(__nv_bfloat16 *sp, size_t plane, size_t o, float re, float im) {
+    __nv_bfloat16 r0, r1, r2, i0, i1, i2;
     split3(re, r0, r1, r2);
     split3(-im, i0, i1, i2);
-    const size_t o = (size_t)ga * np + gb;
     sp[0 * plane + o] = r0; sp[2 * plane + o] = r1; sp[4 * plane + o] = r2;
     sp[1 * plane + o] = i0; sp[3 * plane + o] = i1; sp[5 * plane + o] = i2;
-    if (mirror) {
-        split3(im, m0, m1, m2);
-        const size_t t = (size_t)gb * np + ga;
-        sp[0 * plane + t] = r0; sp[2 * plane + t] = r1; sp[4 * plane + t] = r2;
-        sp[1 * plane + t] = m0; sp[3 * plane + t] = m1; sp[5 * plane + t] = m2;
-    }
 }
 
 template <int STAGE>
@@ -238,44 +237,52 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
         if (tid == 0) atomicExch(&ctl->err_timeout, 1);
     } else {
         const int q = warp & 3;             // TMEM lane quarter this warp may read
-        const int h = warp >> 2;            // column half
-        const int row = q * 32 + lane;      // TMEM lane = row of the tile
+        const int h = warp >> 2;            // A (0) or B (1) columns
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        float *sX = reinterpret_cast<float *>(smem);  // X_JI staged as [row][LDS], aliases the pipeline
-        // stage X_JI (or X_IJ on the diagonal): columns [h*128, h*128 + 128)
-        const uint32_t src = (diag ? tm_ij : tm_ji) + lane_off;
-        for (int c = 0; c < 128; c += 32) {
-            float v[32];
-            tmem_ld32(src + (uint32_t)(h * 128 + c), v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) sX[row * LDS + h * 128 + c + i] = v[i];
-        }
-        __syncthreads();
+        // aliases the pipeline buffers (every MMA has completed)
+        float *sX = reinterpret_cast<float *>(smem);
+        float *sY = sX + EC * LDX2;
+        float *sO = sY + TB * LDY;
+        const uint32_t src_ji = diag ? tm_ij : tm_ji;  // X_JI (X_IJ on the diagonal)
 
         const float om = ops.omega32, cm = 1.0f - om;
         const float dtf = ctl->dtf, dt6h = ctl->dt6h, dt6l = ctl->dt6l;
         const float *__restrict__ din = (STAGE == 1) ? w.D : (STAGE == 3 ? w.db : w.da);
         float *dnext = (STAGE == 2) ? w.db : w.da;
         __nv_bfloat16 *snext = (STAGE == 2) ? w.splitB : (STAGE == 4 ? w.splitD : w.splitA);
-        const int a = row, ga = I * TB + a;
         float nrm = 0.f;
-        for (int c = 0; c < 64; c += 32) {
-            const int b0 = h * 64 + c;
-            float xa[32], xb[32];
-            tmem_ld32(tm_ij + lane_off + (uint32_t)b0, xa);
-            tmem_ld32(tm_ij + lane_off + (uint32_t)(TB + b0), xb);
+        for (int cb = 0; cb < TB / EC; ++cb) {
+            // X_IJ[a][cb EC ..] (A or B) for every row a; X_JI rows b of this chunk
+            {
+                float v[32];
+                tmem_ld32(tm_ij + lane_off + (uint32_t)(h * TB + cb * EC), v);
+                const int a = q * 32 + lane;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int b = b0 + j, gb = J * TB + b;
+                for (int i = 0; i < 32; ++i) sY[a * LDY + h * EC + i] = v[i];
+            }
+            if (q == cb) {
+                for (int c = 0; c < TB; c += 32) {
+                    float v[32];
+                    tmem_ld32(src_ji + lane_off + (uint32_t)(h * TB + c), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sX[lane * LDX2 + h * TB + c + i] = v[i];
+                }
+            }
+            __syncthreads();
+            // elements (a, b) of tile (I, J), lanes along b: the direct accesses are coalesced
+            const int c = lane, b = cb * EC + c, gb = J * TB + b;
+            const float cb32 = ops.c32[gb];
+            for (int a = warp; a < TB; a += NTHREADS / 32) {
+                const int ga = I * TB + a;
                 const size_t off = (size_t)ga * np + gb;
-                const float Aab = xa[j], Bab = xb[j];
-                const float Aba = sX[b * LDS + a], Bba = sX[b * LDS + TB + a];
+                const float Aab = sY[a * LDY + c], Bab = sY[a * LDY + EC + c];
+                const float Aba = sX[c * LDX2 + a], Bba = sX[c * LDX2 + TB + a];
                 const float dr = din[off], di = din[plane + off];
-                const float hc = 0.5f * (ops.c32[ga] + ops.c32[gb]);
+                const float hc = 0.5f * (ops.c32[ga] + cb32);
                 float kdr = cm * (Bab + Bba) - om * hc * dr;
                 const float kdi = -cm * (Aab - Aba) - om * hc * di;
                 if (ga == gb) kdr += om * w.g[ga];
-                const size_t moff = (size_t)gb * np + ga;
+                float o0, o1, o2, o3;  // the outputs the mirrored write needs
                 if (STAGE <= 3) {
                     const float kr = kdr + w.F32[off], ki = kdi + w.F32[plane + off];
                     if (STAGE == 1) nrm += kr * kr + ki * ki;
@@ -287,11 +294,8 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
                     const float nr = Dr + cst * kr, ni = Di + cst * ki;
                     w.S[off] = sr; w.S[plane + off] = si;
                     dnext[off] = nr; dnext[plane + off] = ni;
-                    if (!diag) {
-                        w.S[moff] = sr; w.S[plane + moff] = -si;
-                        dnext[moff] = nr; dnext[plane + moff] = -ni;
-                    }
-                    put_split(snext, plane, ga, gb, np, nr, ni, !diag);
+                    put_split(snext, plane, off, nr, ni);
+                    o0 = sr; o1 = si; o2 = nr; o3 = ni;
                 } else {
                     // delta += dt F + dt/6 (S + kd4) in float-float
                     const float sr = w.S[off] + kdr, si = w.S[plane + off] + kdi;
@@ -301,13 +305,36 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
                                                              w.Glo[plane + off], dt6h, dt6l, si);
                     w.D[off] = vr.hi; w.D[plane + off] = vi.hi;
                     w.Dlo[off] = vr.lo; w.Dlo[plane + off] = vi.lo;
-                    if (!diag) {
-                        w.D[moff] = vr.hi; w.D[plane + moff] = -vi.hi;
-                        w.Dlo[moff] = vr.lo; w.Dlo[plane + moff] = -vi.lo;
-                    }
-                    put_split(snext, plane, ga, gb, np, vr.hi, vi.hi, !diag);
+                    put_split(snext, plane, off, vr.hi, vi.hi);
+                    o0 = vr.lo; o1 = vi.lo; o2 = vr.hi; o3 = vi.hi;
+                }
+                if (!diag) {
+                    sO[(0 * EC + c) * LDO2 + a] = o0;
+                    sO[(1 * EC + c) * LDO2 + a] = o1;
+                    sO[(2 * EC + c) * LDO2 + a] = o2;
+                    sO[(3 * EC + c) * LDO2 + a] = o3;
                 }
             }
+            __syncthreads();
+            if (!diag) {
+                // the conjugate of the chunk at (b, a) of tile (J, I), lanes along a: coalesced
+                for (int e = warp; e < EC * (TB / 32); e += NTHREADS / 32) {
+                    const int cc = e >> 2, a = (e & 3) * 32 + lane;
+                    const int gb2 = J * TB + cb * EC + cc, ga2 = I * TB + a;
+                    const size_t moff = (size_t)gb2 * np + ga2;
+                    const float o0 = sO[(0 * EC + cc) * LDO2 + a], o1 = sO[(1 * EC + cc) * LDO2 + a];
+                    const float o2 = sO[(2 * EC + cc) * LDO2 + a], o3 = sO[(3 * EC + cc) * LDO2 + a];
+                    if (STAGE <= 3) {
+                        w.S[moff] = o0; w.S[plane + moff] = -o1;
+                        dnext[moff] = o2; dnext[plane + moff] = -o3;
+                    } else {
+                        w.Dlo[moff] = o0; w.Dlo[plane + moff] = -o1;
+                        w.D[moff] = o2; w.D[plane + moff] = -o3;
+                    }
+                    put_split(snext, plane, moff, o2, -o3);
+                }
+            }
+            __syncthreads();  // the chunk's buffers are reused by the next
         }
         if (STAGE == 1) {
             nrm = mixed::warp_sum_f(nrm);
