@@ -12,7 +12,7 @@
 //
 // One CTA owns the tile pair (I, J), I <= J, of 128 x 128 complex tiles and
 // accumulates X_IJ and X_JI in TMEM (2 x 256 FP32 columns = all 512). Warp 0
-// (one thread) streams operand tiles with TMA (128-byte swizzle, two stages),
+// (one thread) streams operand tiles with TMA (128-byte swizzle, four stages),
 // warp 1 (one thread) issues tcgen05.mma and commits to mbarriers, and all
 // eight warps run the fused epilogue: X_JI is staged in shared memory for
 // the transposed read, the Lindblad right-hand side of the delta and the RK4
@@ -36,11 +36,11 @@ namespace {
 
 constexpr int TB = kTileTc;             // 128
 constexpr int BK = 64;                  // BF16 K per stage: one 128-byte swizzle row
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 4;
 constexpr int A_BYTES = TB * BK * 2;        // 16 KB
 constexpr int B_BYTES = 2 * TB * BK * 2;    // 32 KB (Re rows then -Im rows)
-constexpr int OFF_AI = 0, OFF_AJ = A_BYTES, OFF_BJ = 2 * A_BYTES, OFF_BI = 2 * A_BYTES + B_BYTES;
-constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // 96 KB
+constexpr int OFF_A = 0, OFF_B = A_BYTES;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
 constexpr int NTHREADS = 256;
 // Epilogue, per chunk of EC columns b of tile (I, J): X_JI rows b staged as
 // [EC][LDX2] (A 128 | B 128), X_IJ columns b as [TB][LDY] (A EC | B EC), and
@@ -181,47 +181,47 @@ stage_mixed_tc_kernel(DevOps ops, MixedWork w, const __grid_constant__ CUtensorM
     // correction products go first and the dominant H0 d0 product last.
     constexpr uint32_t kSegI = 0x010210u, kSegJ = 0x001012u;
 
+    // Two passes over K: X_IJ = H_I. delta_.J, then (off the diagonal) X_JI =
+    // H_J. delta_.I, each K block one stage of A (16 KB) and B (32 KB), so
+    // NSTAGE = 4 stages keep three loads in flight behind the MMAs.
+    const int nit = diag ? nkb : 2 * nkb;
     if (warp == 0 && lane == 0) {
         // TMA producer
-        const uint32_t tx = diag ? (uint32_t)(A_BYTES + B_BYTES) : (uint32_t)STAGE_BYTES;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % NSTAGE;
-            if (kb >= NSTAGE && !mbar_wait(&empty_bar[st], ((kb / NSTAGE) - 1) & 1)) {
+        for (int it = 0; it < nit; ++it) {
+            const int st = it % NSTAGE;
+            if (it >= NSTAGE && !mbar_wait(&empty_bar[st], ((it / NSTAGE) - 1) & 1)) {
                 atomicExch(&s_fail, 1);
                 break;
             }
+            const int pass = it / nkb, kb = it - pass * nkb;
+            const int rt = pass ? J : I, ct = pass ? I : J;  // row tile of H, column tile of delta
             const int seg = kb / kb_per_seg;
             const int k0 = (kb - seg * kb_per_seg) * BK;
             const int li = (int)((kSegI >> (4 * seg)) & 0xFu), lj = (int)((kSegJ >> (4 * seg)) & 0xFu);
             uint8_t *sb = smem + st * STAGE_BYTES;
-            mbar_expect_tx(&full_bar[st], tx);
-            load_3d(sb + OFF_AI, &tmH, &full_bar[st], k0, I * TB, li);
-            load_4d(sb + OFF_BJ, &tmIn, &full_bar[st], k0, J * TB, 0, lj);
-            load_4d(sb + OFF_BJ + B_BYTES / 2, &tmIn, &full_bar[st], k0, J * TB, 1, lj);
-            if (!diag) {
-                load_3d(sb + OFF_AJ, &tmH, &full_bar[st], k0, J * TB, li);
-                load_4d(sb + OFF_BI, &tmIn, &full_bar[st], k0, I * TB, 0, lj);
-                load_4d(sb + OFF_BI + B_BYTES / 2, &tmIn, &full_bar[st], k0, I * TB, 1, lj);
-            }
+            mbar_expect_tx(&full_bar[st], (uint32_t)STAGE_BYTES);
+            load_3d(sb + OFF_A, &tmH, &full_bar[st], k0, rt * TB, li);
+            load_4d(sb + OFF_B, &tmIn, &full_bar[st], k0, ct * TB, 0, lj);
+            load_4d(sb + OFF_B + B_BYTES / 2, &tmIn, &full_bar[st], k0, ct * TB, 1, lj);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % NSTAGE;
-            if (!mbar_wait(&full_bar[st], (kb / NSTAGE) & 1)) {
+        for (int it = 0; it < nit; ++it) {
+            const int st = it % NSTAGE;
+            if (!mbar_wait(&full_bar[st], (it / NSTAGE) & 1)) {
                 atomicExch(&s_fail, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int pass = it / nkb, kb = it - pass * nkb;
             const uint32_t sb = smem_u32(smem + st * STAGE_BYTES);
-            const uint64_t dAI = sw128_desc(sb + OFF_AI), dBJ = sw128_desc(sb + OFF_BJ);
-            const uint64_t dAJ = sw128_desc(sb + OFF_AJ), dBI = sw128_desc(sb + OFF_BI);
+            const uint64_t dA = sw128_desc(sb + OFF_A), dB = sw128_desc(sb + OFF_B);
+            const uint32_t tm_d = pass ? tm_ji : tm_ij;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 16 BF16 = 32 bytes along K
                 const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                umma_bf16(tm_ij, dAI + adv, dBJ + adv, acc);
-                if (!diag) umma_bf16(tm_ji, dAJ + adv, dBI + adv, acc);
+                umma_bf16(tm_d, dA + adv, dB + adv, acc);
             }
             umma_commit(&empty_bar[st]);
         }
