@@ -107,7 +107,7 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
  *   block clusters.
  * COLUMNS_GATHER: the column-block product for any N without staging the
  *   block: each CTA (row split r, block J) stages only its CSR entries and
- *   reads every nonzero's 16 values of block J from L2; the splits of a
+ *   reads every nonzero's 16 values of block J through L1 and L2; the splits of a
  *   block run side by side, so the block is read from DRAM about once.
  * AUTO (default): COLUMNS where it applies, else COLUMNS_GATHER, else TILES.
  * COLUMNS, COLUMNS_PERSISTENT and COLUMNS_GATHER give bitwise the same

@@ -190,8 +190,14 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
                 return;
             }
             const int warp = threadIdx.x >> 5;
+            float *parts = reinterpret_cast<float *>(dyn_smem + ops.col_part_off);
             cols::warp_bundles(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
-                               ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X);
+                               ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X, nullptr, 0, parts);
+            const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
+            if (cb1 > cb0) {
+                __syncthreads();
+                cols::combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, np, sg.mw.X);
+            }
         }
         __syncthreads();
     }
@@ -447,9 +453,9 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         okh[g] = nkh;
         nkh += pl.kh.size();
         oci[g] = nci;
-        nci += pl.q.size() + pl.sb.size() + pl.wb.size();
+        nci += pl.q.size() + pl.sb.size() + pl.wb.size() + pl.cutb.size();
         opc[g] = npc;
-        npc += pl.pieces.size();
+        npc += pl.pieces.size() + pl.cuts.size();
         oxc[g] = nxc;
         nxc += qpr::align_up(2 * (size_t)np[g] * np[g], 64);
         na_max += (size_t)(np[g] / qpr::cols::kCW) * pl.splits;
@@ -507,10 +513,13 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         std::vector<int> ints(pl.q);
         ints.insert(ints.end(), pl.sb.begin(), pl.sb.end());
         ints.insert(ints.end(), pl.wb.begin(), pl.wb.end());
+        ints.insert(ints.end(), pl.cutb.begin(), pl.cutb.end());
+        std::vector<int4> pcs(pl.pieces);
+        pcs.insert(pcs.end(), pl.cuts.begin(), pl.cuts.end());
         BCUDA(cudaMemcpy(dKH + okh[g], pl.kh.data(), pl.kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BCUDA(cudaMemcpy(dCI + oci[g], ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
-        if (!pl.pieces.empty())
-            BCUDA(cudaMemcpy(dPC + opc[g], pl.pieces.data(), pl.pieces.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        if (!pcs.empty())
+            BCUDA(cudaMemcpy(dPC + opc[g], pcs.data(), pcs.size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
     BCUDA(cudaMemset(dD, 0, nd * sizeof(double)));
     BCUDA(cudaMemset(dF, 0, nf * sizeof(float)));
@@ -594,6 +603,9 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
             d.ops.col_sb = dCI + oci[g] + pl.q.size();
             d.ops.col_wb = dCI + oci[g] + pl.q.size() + pl.sb.size();
             d.ops.col_pieces = dPC + opc[g];
+            d.ops.col_cutb = dCI + oci[g] + pl.q.size() + pl.sb.size() + pl.wb.size();
+            d.ops.col_cut = dPC + opc[g] + pl.pieces.size();
+            d.ops.col_part_off = pl.part_off;
             d.ops.col_splits = pl.splits;
             d.ops.col_smem = pl.smem;
             d.ops.col_p_off = pl.p_off;

@@ -43,6 +43,9 @@ constexpr int kAWarps = kANT / 32;   // (32 warps measured slower, for both the 
 #ifndef QPR_GATHER_UNROLL
 #define QPR_GATHER_UNROLL 8
 #endif
+#ifndef QPR_GATHER_LD
+#define QPR_GATHER_LD __ldca
+#endif
 #ifndef QPR_SMEM_UNROLL
 #define QPR_SMEM_UNROLL 0
 #endif
@@ -56,6 +59,20 @@ constexpr int kSmemUnroll = QPR_SMEM_UNROLL;
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
 constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
+constexpr int kPiecePart = 2;      // bundle flags: one part of a cut row (its sum goes to a partial slot)
+// For np above kColMaxNp (the gather and chunked forms, many row splits; the
+// gather form only when its grid has fewer than kCutMaxWaves waves), rows
+// longer than kPartMax nonzeros are cut into parts of at most kPartMax,
+// each a long-row bundle of its own (possibly on another warp) whose sum goes
+// to a partial slot in shared memory; after all warps, the parts of a row are
+// added in part order (combine_cuts). A long row's bundle is otherwise one
+// warp's work, which made the warp holding a hub row of a heavy-tailed graph
+// the critical path of its CTA (N = 2048: 79 -> 67 us per gather launch).
+// With the few splits of smaller problems a hub row is about one warp's
+// share and cutting measured slower, so those plans cut nothing and every
+// form there sums each row the same way.
+constexpr int kPartMax = 256;
+constexpr int kCutMaxWaves = 8;
 constexpr int kRPG = 2;            // rows (slots) per 8-lane group of a bundle (4 measured slower: more padding)
 
 // A bundle descriptor is 1 + kRPG int4: {first entry (relative to its
@@ -80,19 +97,22 @@ __device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g 
 // ACC (the chunked form): instead of storing X, add each row's sums to its
 // accumulator acc[(row - row0) kRowFloats + 4 p .. + 3] in shared memory.
 // GMEM (the gather form): sD is the stage input in global memory (two np x
-// np planes); row q's 16 values of block J are read there from L2 (the
-// input was written by the previous kernel, which may still be draining
-// under programmatic dependent launch when this one starts).
+// np planes); row q's 16 values of block J are read there with L1-cached
+// loads (hub rows, referenced by many rows of a split, hit L1). The input
+// was written by the previous kernel; every load is issued after
+// griddepcontrol.wait, which makes that kernel's writes visible, and no
+// kernel reads the stage inputs through L1 before it.
 template <bool ACC = false, bool GMEM = false>
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
-                                             float *__restrict__ X, float *acc_rows = nullptr, int row0 = 0) {
+                                             float *__restrict__ X, float *acc_rows = nullptr, int row0 = 0,
+                                             float *parts = nullptr) {
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
     const size_t plane = (size_t)np * np;
     const int col = J * kCW + 4 * (p & 3);
     const float *__restrict__ sDp = GMEM ? sD + (p < 4 ? 0 : plane) + col : sD + 4 * p;
     auto row_of = [&](int q) {
-        if (GMEM) return __ldcg(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
+        if (GMEM) return QPR_GATHER_LD(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
         return *reinterpret_cast<const float4 *>(sDp + q * kRowFloats);
     };
     float *__restrict__ Xp = X + (p < 4 ? 0 : plane) + col;
@@ -171,13 +191,42 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             for (int s = 1; s < kRPG; ++s) a = f4add(a, acc[s]);
             a = mixed::f4xor(a, 8);
             a = mixed::f4xor(a, 16);
-            if (g == 0) put(bd[1].x, a);
+            if (g == 0) {
+                if (d0.z & kPiecePart)
+                    *reinterpret_cast<float4 *>(parts + bd[1].x * kRowFloats + 4 * p) = a;
+                else
+                    put(bd[1].x, a);
+            }
         } else {
 #pragma unroll
             for (int s = 0; s < kRPG; ++s) {
                 const int row = pick(bd[1 + s], g);
                 if (row >= 0) put(row, acc[s]);
             }
+        }
+    }
+}
+
+// The rows cut into parts, cuts[0 .. ncut) = {row, first slot, parts, 0}:
+// X[row, J] = the sum of the parts' partial rows in slot order (ACC: added
+// to the row's accumulator). Called by all threads after every warp's
+// bundles (and a barrier).
+template <bool ACC = false>
+__device__ __forceinline__ void combine_cuts(const int4 *__restrict__ cuts, int ncut, const float *parts, int J,
+                                             int np, float *__restrict__ X, float *acc_rows = nullptr,
+                                             int row0 = 0) {
+    const size_t plane = (size_t)np * np;
+    for (int e = threadIdx.x; e < ncut * (kRowFloats / 4); e += blockDim.x) {
+        const int4 c = __ldg(cuts + (e >> 3));
+        const int p = e & 7;
+        float4 s = *reinterpret_cast<const float4 *>(parts + c.y * kRowFloats + 4 * p);
+        for (int k = 1; k < c.z; ++k)
+            s = f4add(s, *reinterpret_cast<const float4 *>(parts + (c.y + k) * kRowFloats + 4 * p));
+        if (ACC) {
+            float4 *a = reinterpret_cast<float4 *>(acc_rows + (c.x - row0) * kRowFloats + 4 * p);
+            *a = f4add(*a, s);
+        } else {
+            *reinterpret_cast<float4 *>(X + (p < 4 ? 0 : plane) + (size_t)c.x * np + J * kCW + 4 * (p & 3)) = s;
         }
     }
 }

@@ -841,10 +841,14 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
             CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
         }
         const std::vector<int2> &kh = chunked ? kplan.kh : cplan.kh;
-        const std::vector<int4> &pieces = chunked ? kplan.pieces : cplan.pieces;
+        // the bundle descriptors, then the cut rows
+        std::vector<int4> pieces(chunked ? kplan.pieces : cplan.pieces);
+        const std::vector<int4> &cuts = chunked ? kplan.cuts : cplan.cuts;
+        pieces.insert(pieces.end(), cuts.begin(), cuts.end());
         std::vector<int> ints;
         for (const std::vector<int> *v : {chunked ? &kplan.q : &cplan.q, chunked ? &kplan.sb : &cplan.sb,
-                                          chunked ? &kplan.wb : &cplan.wb, &kplan.rows})
+                                          chunked ? &kplan.wb : &cplan.wb, chunked ? &kplan.cutb : &cplan.cutb,
+                                          &kplan.rows})
             ints.insert(ints.end(), v->begin(), v->end());
         CREATE_CUDA(cudaMalloc(&ctx->d_colkh, kh.size() * sizeof(int2)));
         CREATE_CUDA(cudaMemcpy(ctx->d_colkh, kh.data(), kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -926,13 +930,17 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
             const size_t nq = chunked ? kplan.q.size() : cplan.q.size();
             const size_t nsb = chunked ? kplan.sb.size() : cplan.sb.size();
             const size_t nwb = chunked ? kplan.wb.size() : cplan.wb.size();
+            const size_t ncb = chunked ? kplan.cutb.size() : cplan.cutb.size();
             ops.col_kh = ctx->d_colkh;
             ops.col_q = ctx->d_colint;
             ops.col_sb = ctx->d_colint + nq;
             ops.col_wb = ctx->d_colint + nq + nsb;
+            ops.col_cutb = ctx->d_colint + nq + nsb + nwb;
             ops.col_pieces = ctx->d_colpieces;
+            ops.col_cut = ctx->d_colpieces + (chunked ? kplan.pieces.size() : cplan.pieces.size());
+            ops.col_part_off = chunked ? kplan.part_off : cplan.part_off;
             if (chunked) {
-                ops.col_rowb = ctx->d_colint + nq + nsb + nwb;
+                ops.col_rowb = ctx->d_colint + nq + nsb + nwb + ncb;
                 ops.col_cs = kplan.cs;
                 ops.col_kc = kplan.kc;
                 ops.col_nc = kplan.nc;

@@ -96,6 +96,12 @@ struct DevOps {
     const int *col_rowb;
     int col_cs, col_kc, col_nc, col_acc_off, col_kh_off, col_kh_slot, col_p_slot;
     int col_gather;        // 1: the gather form (the SpMM reads delta from L2; plan of ColPlan, gather)
+    // rows cut into parts (kPartMax): per split (or per (split, chunk) block)
+    // the cut range [col_cutb[k], col_cutb[k + 1]) of col_cut; the partial
+    // slots at byte col_part_off of the SpMM's shared memory
+    const int4 *col_cut;
+    const int *col_cutb;
+    int col_part_off;
     int col_epi_off;       // persistent form: byte offset of the epilogue buffers (0: over the column block)
     int col_psmem;         // persistent form: dynamic shared memory of its launch
 };
@@ -223,6 +229,9 @@ struct ColPlan {
     std::vector<int> sb;          // splits + 1
     std::vector<int4> pieces;     // 2 per bundle
     std::vector<int> wb;          // splits * 16 + 1
+    std::vector<int4> cuts;       // rows cut into parts: {row, first partial slot, parts, 0}
+    std::vector<int> cutb;        // splits + 1: the cuts of split r are [cutb[r], cutb[r + 1])
+    int part_off = 0;             // byte offset of the partial slots in the SpMM's shared memory
 };
 // Plans the column-block form of an np x np problem on `device`; false if
 // its staged operands do not fit one CTA's shared memory. Row splits: the
@@ -241,11 +250,13 @@ cudaError_t set_cols_smem(int bytes);
 // split rows and the chunk geometry.
 struct ChunkPlan {
     int cs = 0, kc = 0, nc = 0;
-    int smem = 0, acc_off = 0, kh_off = 0, kh_slot = 0, p_off = 0, p_slot = 0;
+    int smem = 0, acc_off = 0, kh_off = 0, kh_slot = 0, p_off = 0, p_slot = 0, part_off = 0;
     std::vector<int> rows;        // cs + 1
     std::vector<int2> kh;
     std::vector<int> q, sb, wb;   // per (split, chunk) block, as in ColPlan
     std::vector<int4> pieces;
+    std::vector<int4> cuts;       // per block, as in ColPlan
+    std::vector<int> cutb;
 };
 // Plans the chunked form (a cluster size and chunk rows whose shared memory
 // fits and whose clusters can be scheduled); false if none does. Sets the

@@ -74,13 +74,19 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
         tma::mbar_wait(&bar_d, 0);
         return;
     }
-    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X);
+    float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
+    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X, nullptr, 0, parts);
+    const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
+    if (cb1 > cb0) {
+        __syncthreads();
+        combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, np, w.X);
+    }
 }
 
 // Gather form of the SpMM, for N too large to stage a column block: CTA
 // (r, J) stages only its split's entries and bundles and reads each
 // nonzero's 16 values of block J straight from the stage input (two 64-byte
-// segments per row, from L2). The grid runs the row splits of one
+// segments per row, L1-cached loads). The grid runs the row splits of one
 // column block next to each other, so the block's rows (np x 128 bytes) are
 // read from DRAM about once and then served by L2 to the splits.
 template <int STAGE>
@@ -116,7 +122,13 @@ __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(Dev
         if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
         return;
     }
-    warp_bundles<false, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X);
+    float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
+    warp_bundles<false, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, nullptr, 0, parts);
+    const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
+    if (cb1 > cb0) {
+        __syncthreads();
+        combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
+    }
 }
 
 // The gain of the stage input, rows shared over the grid; runs beside the
@@ -244,7 +256,13 @@ __global__ void __launch_bounds__(kANT, 1) cols_chunk_kernel(const __grid_consta
         if (!bad) {
             const int blk = r * nc + c;
             const int *wb = ops.col_wb + blk * kAWarps + warp;
-            warp_bundles<true>(buf(b), skh(b), spc(b), ops.col_sb[blk], wb[0], wb[1], J, np, w.X, acc, row0);
+            float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
+            warp_bundles<true>(buf(b), skh(b), spc(b), ops.col_sb[blk], wb[0], wb[1], J, np, w.X, acc, row0, parts);
+            const int cb0 = ops.col_cutb[blk], cb1 = ops.col_cutb[blk + 1];
+            if (cb1 > cb0) {
+                __syncthreads();
+                combine_cuts<true>(ops.col_cut + cb0, cb1 - cb0, parts, J, np, w.X, acc, row0);
+            }
         }
         tma::cluster_sync();  // every rank is done with buffer b
         if (c + 2 < nc && tid == 0) {
@@ -284,33 +302,60 @@ using RowEntries = std::vector<std::vector<int2>>;
 // bundles' descriptors and their interleaved, zero-padded entries (relative
 // offsets from `kh_base`), and the warps' first bundles.
 // skip_empty: rows without entries get no bundle (their sums are kept
-// elsewhere); otherwise they get zero rounds, which store zeros.
-void split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::vector<int2> &kh,
-                   std::vector<int4> &pieces, std::vector<int> &wb, bool skip_empty = false) {
+// elsewhere); otherwise they get zero rounds, which store zeros. part_max >
+// 0: rows longer than part_max are cut into parts (bundles whose sums go to
+// partial slots 0, 1, ... of this block); each cut row appends {row, first
+// slot, parts, 0} to `cuts`. Returns the number of partial slots.
+int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::vector<int2> &kh,
+                  std::vector<int4> &pieces, std::vector<int> &wb, std::vector<int4> &cuts, int part_max,
+                  bool skip_empty = false) {
     constexpr int kSlots = 4 * kRPG;
     struct Bundle {
         int rows[kSlots];
         int T;
-        bool lng;
+        bool lng, part;
+        int src, e0, e1;  // long rows and parts: the row and its entries [e0, e1)
         long long cost;
     };
     std::vector<Bundle> bs;
     std::vector<int> shortrows;
+    int nslots = 0;
     auto row_len = [&](int i) { return (int)ent[i - r0].size(); };
     auto fresh = [&](int T, bool lng) {
         Bundle b;
         for (int j = 0; j < kSlots; ++j) b.rows[j] = -1;
         b.T = T;
         b.lng = lng;
+        b.part = false;
+        b.src = -1;
+        b.e0 = b.e1 = 0;
         b.cost = (long long)kRPG * T + 8;
         return b;
     };
     for (int i = r0; i < r1; ++i) {
-        if (row_len(i) > kLongRow) {
-            Bundle b = fresh((row_len(i) + kSlots - 1) / kSlots, true);
+        const int len = row_len(i);
+        if (part_max > 0 && len > part_max) {
+            // parts [k len / P, (k + 1) len / P) of the row's entries, in order
+            const int P = (len + part_max - 1) / part_max;
+            cuts.push_back(make_int4(i, nslots, P, 0));
+            for (int k = 0; k < P; ++k) {
+                const int e0 = (int)((long long)k * len / P), e1 = (int)((long long)(k + 1) * len / P);
+                Bundle b = fresh((e1 - e0 + kSlots - 1) / kSlots, true);
+                b.part = true;
+                b.rows[0] = nslots + k;
+                b.src = i;
+                b.e0 = e0;
+                b.e1 = e1;
+                bs.push_back(b);
+            }
+            nslots += P;
+        } else if (len > kLongRow) {
+            Bundle b = fresh((len + kSlots - 1) / kSlots, true);
             b.rows[0] = i;
+            b.src = i;
+            b.e1 = len;
             bs.push_back(b);
-        } else if (row_len(i) > 0 || !skip_empty) {
+        } else if (len > 0 || !skip_empty) {
             shortrows.push_back(i);
         }
     }
@@ -333,7 +378,8 @@ void split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::v
         wb.push_back((int)(pieces.size() / kBundleInt4));
         for (int k : per[wi]) {
             const Bundle &b = bs[k];
-            pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T, b.lng ? kPieceLong : 0, 0));
+            pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T,
+                                       (b.lng ? kPieceLong : 0) | (b.part ? kPiecePart : 0), 0));
             // slot s of group g is rows[g + 4 s]
             for (int s = 0; s < kRPG; ++s)
                 pieces.push_back(make_int4(b.rows[4 * s], b.rows[4 * s + 1], b.rows[4 * s + 2], b.rows[4 * s + 3]));
@@ -343,8 +389,8 @@ void split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::v
                     for (int sl = 0; sl < kRPG; ++sl) {
                         int2 v = make_int2(0, 0);
                         if (b.lng) {
-                            const int e = kSlots * t + kRPG * g + sl;
-                            if (e < row_len(b.rows[0])) v = ent[b.rows[0] - r0][e];
+                            const int e = b.e0 + kSlots * t + kRPG * g + sl;
+                            if (e < b.e1) v = ent[b.src - r0][e];
                         } else {
                             const int row = b.rows[g + 4 * sl];
                             if (row >= 0 && t < row_len(row)) v = ent[row - r0][t];
@@ -353,6 +399,7 @@ void split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::v
                     }
         }
     }
+    return nslots;
 }
 
 // Row i's entries with a column in [c0, c1), columns relative to c0, in CSR order.
@@ -411,13 +458,20 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         }
         rows[s] = np;
         size_t kh_max = 0, p_max = 0;
+        int slots_max = 0;
+        // rows are cut into parts above the whole-block range when the grid
+        // has few waves (many waves absorb a long CTA; measured: N = 2048, 3.4
+        // waves, 15% faster with cuts; N = 8192, 40 waves, 5% slower)
+        const bool cut = np > kColMaxNp && (double)s * ncb < kCutMaxWaves * kGatherCtasPerSm * (double)sms;
         for (int k = 0; k < s; ++k) {
             const size_t kb = pl.kh.size();  // even: every split's block starts 16-byte aligned
             const int first = (int)(pl.pieces.size() / kBundleInt4);
             pl.sb.push_back(first);
+            pl.cutb.push_back((int)pl.cuts.size());
             RowEntries ent;
             for (int i = rows[k]; i < rows[k + 1]; ++i) ent.push_back(row_entries(h, i, 0, np));
-            split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb);
+            slots_max = std::max(slots_max, split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb,
+                                                          pl.cuts, cut ? kPartMax : 0));
             if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
             pl.q.push_back((int)kb);
             pl.q.push_back((int)pl.kh.size());
@@ -426,20 +480,25 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         }
         pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
+        pl.cutb.push_back((int)pl.cuts.size());
+        const size_t part_bytes = (size_t)slots_max * kRowFloats * 4;
         size_t smem, cap;
         if (gather) {
-            // entries, then bundles; small enough for kGatherCtasPerSm CTAs per SM
+            // entries, bundles, partial slots; small enough for kGatherCtasPerSm CTAs per SM
             pl.p_off = (int)kh_max;
             pl.sp_off = 0;
-            smem = (size_t)pl.p_off + p_max + 128;
+            pl.part_off = (int)(((size_t)pl.p_off + p_max + 15) / 16 * 16);
+            smem = (size_t)pl.part_off + part_bytes + 128;
             // per CTA: its dynamic and static shared memory and the 1 KB the
             // system reserves (the 1 KB below covers the static part)
             cap = std::min({(size_t)smem_max, (size_t)sm_per_sm / kGatherCtasPerSm - 1024,
                             (size_t)kGatherSplitBytes + 1024});
         } else {
+            // column block, entries, bundles, staged diagonal, partial slots
             pl.p_off = (int)((size_t)np * kRowFloats * 4 + kh_max);
             pl.sp_off = (int)((size_t)pl.p_off + p_max);
-            smem = (size_t)pl.sp_off + (size_t)np * 4 + 128;
+            pl.part_off = (int)(((size_t)pl.sp_off + (size_t)np * 4 + 15) / 16 * 16);
+            smem = (size_t)pl.part_off + part_bytes + 128;
             cap = (size_t)smem_max;
         }
         // 1 KB left for the static shared memory of the kernels (the batched
@@ -492,6 +551,7 @@ bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc_f
         int rows_max = 0;
         for (int k = 0; k < cs; ++k) rows_max = std::max(rows_max, pl.rows[k + 1] - pl.rows[k]);
         size_t kh_max = 0, p_max = 0;
+        int slots_max = 0;
         for (int k = 0; k < cs; ++k) {
             const int r0 = pl.rows[k], r1 = pl.rows[k + 1];
             for (int c = 0; c < pl.nc; ++c) {
@@ -503,7 +563,9 @@ bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc_f
                 const size_t kb = pl.kh.size();  // even: every block starts 16-byte aligned
                 const int first = (int)(pl.pieces.size() / kBundleInt4);
                 pl.sb.push_back(first);
-                split_bundles(r0, r1, ent, kb, pl.kh, pl.pieces, pl.wb, /*skip_empty=*/true);
+                pl.cutb.push_back((int)pl.cuts.size());
+                slots_max = std::max(slots_max, split_bundles(r0, r1, ent, kb, pl.kh, pl.pieces, pl.wb, pl.cuts,
+                                                              np > kColMaxNp ? kPartMax : 0, /*skip_empty=*/true));
                 if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
                 pl.q.push_back((int)kb);
                 pl.q.push_back((int)pl.kh.size());
@@ -513,12 +575,14 @@ bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc_f
         }
         pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
+        pl.cutb.push_back((int)pl.cuts.size());
         pl.kh_slot = (int)std::max<size_t>(16, kh_max);
         pl.p_slot = (int)std::max<size_t>(16, p_max);
         pl.acc_off = 2 * kc * kRowFloats * 4;
         pl.kh_off = pl.acc_off + rows_max * kRowFloats * 4;
         pl.p_off = pl.kh_off + 2 * pl.kh_slot;
-        const size_t smem = (size_t)pl.p_off + 2 * (size_t)pl.p_slot + 128;
+        pl.part_off = pl.p_off + 2 * pl.p_slot;
+        const size_t smem = (size_t)pl.part_off + (size_t)slots_max * kRowFloats * 4 + 128;
         if (smem_max <= 1024 || smem > (size_t)smem_max - 1024) continue;
         pl.smem = (int)smem;
         // the cluster must be schedulable with this shared memory

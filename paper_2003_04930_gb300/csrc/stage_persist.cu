@@ -66,6 +66,7 @@ struct Smem {
     int4 *sP;
     float *sp;   // staged diagonal of the stage input (the gain)
     float *epi;  // epilogue buffers (over the column block when it is large enough)
+    float *parts;  // partial slots of the rows cut into parts
     uint64_t *bar;
     int *flag;
 };
@@ -105,7 +106,12 @@ __device__ __forceinline__ int persist_stage(const CUtensorMap *tm, const DevOps
             return -1;
         }
         warp_bundles(sm.sD, sm.sKH, sm.sP, ops.col_sb[r], ops.col_wb[r * kAWarps + warp],
-                     ops.col_wb[r * kAWarps + warp + 1], J, np, w.X);
+                     ops.col_wb[r * kAWarps + warp + 1], J, np, w.X, nullptr, 0, sm.parts);
+        const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
+        if (cb1 > cb0) {
+            __syncthreads();
+            combine_cuts(ops.col_cut + cb0, cb1 - cb0, sm.parts, J, np, w.X);
+        }
     }
     if (!grid_sync(w.ctl, C, gen, sm.flag)) return -1;
     // ---- epilogue phase (buffers overlay the column block) ----
@@ -147,6 +153,7 @@ __global__ void __launch_bounds__(kANT, 1) cols_block_kernel(const __grid_consta
     sm.sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
     sm.sp = reinterpret_cast<float *>(base + ops.col_sp_off);
     sm.epi = reinterpret_cast<float *>(base + ops.col_epi_off);
+    sm.parts = reinterpret_cast<float *>(base + ops.col_part_off);
     sm.bar = &bar;
     sm.flag = &s_flag;
     const int c = blockIdx.x;
