@@ -311,7 +311,7 @@ def run_ours(a):
         alg = 16 * npad * npad
         gathered = h_nonzeros(g) * npad * 8
         ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
-        epi_alg = 66 * n * n
+        epi_alg = 44 * n * n  # the nested-RK4 epilogue's mean per stage, as below
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "cols_gather_kernel",
                 "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
@@ -335,11 +335,12 @@ def run_ours(a):
         alg = h_nonzeros(g) * npad * 8
         smem_peak = 128.0 * SMS * SM_MAX_GHZ  # GB/s
         ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
-        # epilogue kernel: N x N planes read or written per stage, mean of the
-        # 4 stages: X (8), delta in (8), F32 (8), S (8 read at stages 2-4,
-        # written at 1-3), the next delta (8, stages 1-3); stage 4 adds D, Dlo
-        # (read and written) and Ghi, Glo: 56 + 64 + 64 + 80 = 264 / 4 = 66
-        epi_alg = 66 * n * n
+        # epilogue kernel (nested RK4 form): N x N FP32 plane pairs (8 bytes
+        # per element) read or written per stage: stage 1 X, D, F32, the next
+        # input (32); stages 2-3 X, the input, F32, D, the next input (40);
+        # stage 4 X, the input, D, Dlo, Ghi, Glo, D and Dlo written (64):
+        # mean (32 + 40 + 40 + 64) / 4 = 44
+        epi_alg = 44 * n * n
         # DRAM bytes per launch from one ncu capture of these kernels at N=922 (caches flushed before every replay
         # pass, so one cold pass over the operands): SpMM 7.03 MB, epilogue 14.04 MB
         spmm_traffic, epi_traffic = (7029248, 14043648) if n == 922 else (None, None)

@@ -78,10 +78,12 @@ __device__ __forceinline__ ff ff_mul_f(float ah, float al, float b) {
     return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
-// Delta update of stage 4 for one real component: delta + dt F + dt/6 s4,
-// with dt F = (gh, gl) and dt / 6 = (dt6h, dt6l) in float-float.
-__device__ __forceinline__ ff delta_update(float dh, float dl, float gh, float gl, float dt6h, float dt6l, float s4) {
-    const ff u = ff_mul_f(dt6h, dt6l, s4);
+// Delta update of stage 4 for one real component: delta + dt F + c s4 in
+// float-float, with dt F = (gh, gl) and the step weight c = (ch, cl) (dt for
+// the nested form of the FP32 stages, dt / 6 for the classical form of the
+// tensor-core stage).
+__device__ __forceinline__ ff delta_update(float dh, float dl, float gh, float gl, float ch, float cl, float s4) {
+    const ff u = ff_mul_f(ch, cl, s4);
     const ff t = ff_add(u.hi, u.lo, gh, gl);
     return ff_add(dh, dl, t.hi, t.lo);
 }
@@ -356,11 +358,23 @@ __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
     return s_status != kCtlRunning;
 }
 
+// The RK4 step in nested form. f is linear, so the classical step
+// y + dt/6 (k1 + 2 k2 + 2 k3 + k4) equals
+//     y + dt L (y + dt/2 L (y + dt/3 L (y + dt/4 L y)))
+// (the same polynomial I + dt L + ... + (dt L)^4 / 24 of dt L). Stage s
+// evaluates k = L w_s = F + f(delta_s) of its input w_s = R + delta_s
+// (delta_1 = D) and writes the next input delta_{s+1} = D + c_s dt k with
+// c = 1/4, 1/3, 1/2; stage 4 adds dt k to the state: D + Dlo += dt F +
+// dt f(delta_4) in float-float (dt F = Ghi + Glo). No running sum of the
+// stages is kept, so a stage reads the product, its input, F32 and D and
+// writes one plane pair (stage 4: D and Dlo).
+//
 // Operands of one thread's elements e = tid + k NTH (k < K) of tile (I, J)
 // of stage STAGE, loaded into registers ahead of the products (one round
-// trip to memory for the whole epilogue): the stage input d; stages 1-3: F32
-// (u), D (v), S (s, stages 2-3); stage 4: S (u), D (v), Dlo (s), Ghi (g), Glo
-// (l); and c32 of the element's row (ca) and column (cb).
+// trip to memory for the whole epilogue): the stage input d; stages 1-3:
+// F32 (u) and, at stages 2-3, D (v; at stage 1 the input is D); stage 4: D
+// (v), Dlo (s), Ghi (g), Glo (l); and c32 of the element's row (ca) and
+// column (cb).
 template <int STAGE, int NTH>
 struct EpiIn {
     static constexpr int K = TS * TS / NTH;
@@ -386,15 +400,11 @@ __device__ __forceinline__ void epi_load(const DevOps &ops, const MixedWork &w, 
         if (STAGE <= 3) {
             in.ur[k] = __ldcg(w.F32 + off);
             in.ui[k] = __ldcg(w.F32 + plane + off);
-            in.vr[k] = __ldcg(w.D + off);
-            in.vi[k] = __ldcg(w.D + plane + off);
             if (STAGE >= 2) {
-                in.sr[k] = __ldcg(w.S + off);
-                in.si[k] = __ldcg(w.S + plane + off);
+                in.vr[k] = __ldcg(w.D + off);
+                in.vi[k] = __ldcg(w.D + plane + off);
             }
         } else {
-            in.ur[k] = __ldcg(w.S + off);
-            in.ui[k] = __ldcg(w.S + plane + off);
             in.vr[k] = __ldcg(w.D + off);
             in.vi[k] = __ldcg(w.D + plane + off);
             in.sr[k] = __ldcg(w.Dlo + off);
@@ -428,7 +438,9 @@ __device__ __forceinline__ void tile_epilogue_in(const DevOps &ops, const MixedW
     const float *X2 = diag ? sX1 : sX2;
 
     const float om = ops.omega32, cm = __fsub_rn(1.0f, om);
-    const float dtf = w.ctl->dtf, dt6h = w.ctl->dt6h, dt6l = w.ctl->dt6l;
+    const float dtf = w.ctl->dtf;
+    // c_s dt of the next stage input (dt / 4 and dt / 2 exact from fl(dt); fl(dt / 3))
+    const float cst = (STAGE == 1) ? __fmul_rn(0.25f, dtf) : (STAGE == 2 ? w.ctl->dt3 : __fmul_rn(0.5f, dtf));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float nrm = 0.f;  // this thread's share of ||k1||^2 (an FP32-accurate estimate)
 #pragma unroll
@@ -449,24 +461,16 @@ __device__ __forceinline__ void tile_epilogue_in(const DevOps &ops, const MixedW
         if (STAGE <= 3) {
             const float kr = __fadd_rn(kdr, in.ur[k]), ki = __fadd_rn(kdi, in.ui[k]);
             if (STAGE == 1) nrm = __fmaf_rn(kr, kr, __fmaf_rn(ki, ki, nrm));
-            const float Dr = in.vr[k], Di = in.vi[k];
-            float sr, si;
-            if (STAGE == 1) { sr = kdr; si = kdi; }
-            else { sr = __fmaf_rn(2.0f, kdr, in.sr[k]); si = __fmaf_rn(2.0f, kdi, in.si[k]); }
-            const float cst = (STAGE == 3) ? dtf : __fmul_rn(0.5f, dtf);
+            const float Dr = (STAGE == 1) ? dr : in.vr[k], Di = (STAGE == 1) ? di : in.vi[k];
             const float nr = __fmaf_rn(cst, kr, Dr), ni = __fmaf_rn(cst, ki, Di);
-            w.S[off] = sr; w.S[plane + off] = si;
             dnext[off] = nr; dnext[plane + off] = ni;
             if (ga == gb && w.pv) w.pv[ga] = nr;
-            sO32[0 * TS * LDO + a * LDO + b] = sr;
-            sO32[1 * TS * LDO + a * LDO + b] = si;
-            sO32[2 * TS * LDO + a * LDO + b] = nr;
-            sO32[3 * TS * LDO + a * LDO + b] = ni;
+            sO32[0 * TS * LDO + a * LDO + b] = nr;
+            sO32[1 * TS * LDO + a * LDO + b] = ni;
         } else {
-            // delta += dt F + dt/6 (S + kd4) in float-float
-            const float sr = __fadd_rn(in.ur[k], kdr), si = __fadd_rn(in.ui[k], kdi);
-            const ff vr = delta_update(in.vr[k], in.sr[k], in.gr[k], in.lr[k], dt6h, dt6l, sr);
-            const ff vi = delta_update(in.vi[k], in.si[k], in.gi[k], in.li[k], dt6h, dt6l, si);
+            // delta += dt F + dt f(delta_4) in float-float
+            const ff vr = delta_update(in.vr[k], in.sr[k], in.gr[k], in.lr[k], dtf, w.ctl->dtl, kdr);
+            const ff vi = delta_update(in.vi[k], in.si[k], in.gi[k], in.li[k], dtf, w.ctl->dtl, kdi);
             w.D[off] = vr.hi; w.D[plane + off] = vi.hi;
             w.Dlo[off] = vr.lo; w.Dlo[plane + off] = vi.lo;
             if (ga == gb && w.pv) w.pv[ga] = vr.hi;
@@ -492,10 +496,8 @@ __device__ __forceinline__ void tile_epilogue_in(const DevOps &ops, const MixedW
             const int b = e / TS, a = e - (e / TS) * TS;
             const size_t off = (size_t)(J * TS + b) * np + I * TS + a;
             if (STAGE <= 3) {
-                w.S[off] = sO32[0 * TS * LDO + a * LDO + b];
-                w.S[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
-                dnext[off] = sO32[2 * TS * LDO + a * LDO + b];
-                dnext[plane + off] = -sO32[3 * TS * LDO + a * LDO + b];
+                dnext[off] = sO32[0 * TS * LDO + a * LDO + b];
+                dnext[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
             } else {
                 w.D[off] = sO32[0 * TS * LDO + a * LDO + b];
                 w.D[plane + off] = -sO32[1 * TS * LDO + a * LDO + b];
@@ -581,6 +583,8 @@ __device__ __forceinline__ void refresh_trace_body(const DevOps &ops, const Mixe
         ctl->dtf = (float)ctl->dt;
         ctl->dt6h = (float)dt6;
         ctl->dt6l = (float)(dt6 - (double)ctl->dt6h);
+        ctl->dtl = (float)(ctl->dt - (double)ctl->dtf);
+        ctl->dt3 = (float)(ctl->dt / 3.0);
     }
 }
 

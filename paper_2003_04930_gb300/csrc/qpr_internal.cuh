@@ -36,8 +36,9 @@ struct Ctl {
     int err_timeout;    // a bounded device-side wait gave up
     int ticket;         // CTAs of the current stage-1 epilogue that finished (column-block form)
     // FP32 forms of dt for the mixed form's delta stages, written by its
-    // refresh: dtf = fl(dt) and dt / 6 = dt6h + dt6l as a float-float pair
-    float dtf, dt6h, dt6l, pad2_;
+    // refresh: dtf = fl(dt), dt = dtf + dtl and dt / 6 = dt6h + dt6l as
+    // float-float pairs, dt3 = fl(dt / 3)
+    float dtf, dt6h, dt6l, dtl, dt3, pad2_;
     // grid barrier of the persistent column-block kernel: arrivals, generation
     unsigned gb_count, gb_gen;
 };
