@@ -341,9 +341,9 @@ def run_ours(a):
         # stage 4 X, the input, D, Dlo, Ghi, Glo, D and Dlo written (64):
         # mean (32 + 40 + 40 + 64) / 4 = 44
         epi_alg = 44 * n * n
-        # DRAM bytes per launch from one ncu capture of these kernels at N=922 (caches flushed before every replay
-        # pass, so one cold pass over the operands): SpMM 7.03 MB, epilogue 14.04 MB
-        spmm_traffic, epi_traffic = (7029248, 14043648) if n == 922 else (None, None)
+        # DRAM bytes per launch from one ncu capture of the stage-1 launches of these kernels at N=922 (caches
+        # flushed before every replay pass, so one cold pass over the operands): SpMM 7.03 MB, epilogue 14.04 MB
+        spmm_traffic, epi_traffic = (7033600, 14044160) if n == 922 else (None, None)
         roof = {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
                 "traffic": spmm_traffic, "kernel": "cols_chunk_kernel" if chunked else "cols_spmm_kernel",
                 "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
