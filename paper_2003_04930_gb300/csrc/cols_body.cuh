@@ -37,25 +37,12 @@ constexpr int kRowFloats = 2 * kCW; // staged row: kCW real, then kCW imaginary 
 constexpr int kBoxRows = 32;       // rows of one TMA box
 constexpr int kANT = 512;          // threads of the SpMM kernel
 constexpr int kAWarps = kANT / 32;   // (32 warps measured slower, for both the whole-block and chunked kernels)
-#ifndef QPR_GATHER_CTAS
-#define QPR_GATHER_CTAS 2
-#endif
-#ifndef QPR_GATHER_UNROLL
-#define QPR_GATHER_UNROLL 8
-#endif
-#ifndef QPR_GATHER_LD
-#define QPR_GATHER_LD __ldca
-#endif
-#ifndef QPR_SMEM_UNROLL
-#define QPR_SMEM_UNROLL 0
-#endif
-constexpr int kGatherCtasPerSm = QPR_GATHER_CTAS;  // resident CTAs per SM the gather form's plan sizes for
-constexpr int kGatherUnroll = QPR_GATHER_UNROLL;   // rounds whose row loads the gather form issues together
-constexpr int kGatherWaves = 3;                    // waves of CTAs the gather form's plan asks for at least
-constexpr int kGatherSplitBytes = 56 << 10;        // largest staged entries + bundles of one gather split
-// rounds whose shared-memory row loads the staged forms issue together (0:
-// one round at a time, the compiler unrolling by 2)
-constexpr int kSmemUnroll = QPR_SMEM_UNROLL;
+// Gather form (measured sweeps: 2 CTAs per SM with 8 rounds of loads in
+// flight beat 3 CTAs per SM with 4 or fewer by 10-30%)
+constexpr int kGatherCtasPerSm = 2;   // resident CTAs per SM the gather form's plan sizes for
+constexpr int kGatherUnroll = 8;      // rounds whose row loads the gather form issues together
+constexpr int kGatherWaves = 3;       // waves of CTAs the gather form's plan asks for at least
+constexpr int kGatherSplitBytes = 56 << 10;  // largest staged entries + bundles of one gather split
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
 constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
@@ -112,7 +99,7 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
     const int col = J * kCW + 4 * (p & 3);
     const float *__restrict__ sDp = GMEM ? sD + (p < 4 ? 0 : plane) + col : sD + 4 * p;
     auto row_of = [&](int q) {
-        if (GMEM) return QPR_GATHER_LD(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
+        if (GMEM) return __ldca(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
         return *reinterpret_cast<const float4 *>(sDp + q * kRowFloats);
     };
     float *__restrict__ Xp = X + (p < 4 ? 0 : plane) + col;
@@ -132,7 +119,8 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
         float4 acc[kRPG];
 #pragma unroll
         for (int s = 0; s < kRPG; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        constexpr int U = GMEM ? kGatherUnroll : kSmemUnroll;
+        // (the same pipelining of the shared-memory loads measured no faster)
+        constexpr int U = GMEM ? kGatherUnroll : 0;
         // a row load; from global memory, padding entries (value 0) load nothing
         auto fetch = [&](int q, int hbits) {
             if (GMEM && hbits == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
