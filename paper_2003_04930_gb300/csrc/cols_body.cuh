@@ -44,7 +44,7 @@ constexpr int kGatherUnroll = 8;      // rounds whose row loads the gather form 
 constexpr int kGatherWaves = 3;       // waves of CTAs the gather form's plan asks for at least
 constexpr int kGatherSplitBytes = 56 << 10;  // largest staged entries + bundles of one gather split
 constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to all 4 groups
-constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each)
+constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each; 256 measured slower)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
 constexpr int kPiecePart = 2;      // bundle flags: one part of a cut row (its sum goes to a partial slot)
 // For np above kColMaxNp (the gather and chunked forms, many row splits; the
