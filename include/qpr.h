@@ -137,7 +137,12 @@ typedef struct {
                             (default 0: chosen by the plan) */
     int32_t row_splits;  /* COLUMNS, COLUMNS_GATHER: row splits of the product, at least this many
                             (default 0: chosen by the plan; at most 16, 64 for the gather form) */
-    int32_t reserved[2];
+    int32_t adaptive_refresh; /* QPR_MIXED steady-state solves: 1 (default) lengthens the window between
+                            refreshes as the residual falls, up to 8 x ref_refresh steps, while
+                            (steps since the refresh)^2 x residual <= ref_refresh^2 x the first
+                            residual; 0: a refresh every ref_refresh steps. Trajectories always
+                            refresh every ref_refresh steps. */
+    int32_t reserved[1];
 } qpr_options;
 
 typedef struct {
@@ -258,7 +263,8 @@ typedef struct {
 /* Steady states of `count` independent problems (graphs of any sizes and
  * omegas, shared alpha, dt, tol and options), integrated together by the
  * mixed-precision RK4 form on the sparse backend (QPR_MIXED; options
- * h_diag, dangling, ref_refresh, device and cuda_stream apply). Each block
+ * h_diag, dangling, ref_refresh, adaptive_refresh, device and cuda_stream
+ * apply). Each block
  * of ref_refresh steps is one set of kernel launches over the tile pairs of
  * every problem still running; a problem drops out as soon as its exact
  * FP64 residual passes tol or it reaches max_steps, so problems that

@@ -701,11 +701,32 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         return e;
     };
     bool timeout = false;
+    // per problem, the refresh window of a single-problem steady-state solve
+    // (adaptive_refresh: the same rule on the same residuals, so the same
+    // refresh steps): refresh before the next block, steps since the last
+    // refresh, residual estimate after the first block
+    const int block = o.ref_refresh;
+    const bool adaptive = o.adaptive_refresh != 0;
+    std::vector<char> due(G, 1);
+    std::vector<int64_t> since(G, 0);
+    std::vector<double> r0(G, -1.0);
     while (!active.empty()) {
         qpr::Lists L{};
+        std::vector<int> refresh_list;
+        for (int g : active)
+            if (due[g]) refresh_list.push_back(g);
+        if (!refresh_list.empty() && refresh_list.size() != active.size()) {
+            // refresh a subset: its own lists first (the stream orders their
+            // kernels before the copies of the next lists into the same buffers)
+            qpr::Lists Lr{};
+            BCUDA(make_lists(refresh_list, Lr));
+            qpr::launch_refresh(dG, Lr, max_np, s, launches);
+        }
         BCUDA(make_lists(active, L));
-        qpr::launch_refresh(dG, L, max_np, s, launches);
-        for (int k = 0; k < o.ref_refresh; ++k) qpr::launch_step(dG, L, s, launches);
+        if (!refresh_list.empty() && refresh_list.size() == active.size())
+            qpr::launch_refresh(dG, L, max_np, s, launches);
+        for (int k = 0; k < block; ++k) qpr::launch_step(dG, L, s, launches);
+        for (int g : active) since[g] = (due[g] ? 0 : since[g]) + block;
         BCUDA(cudaMemcpyAsync(hCtl, dCtl, G * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         BCUDA(cudaStreamSynchronize(s));
         BCUDA(cudaGetLastError());
@@ -713,10 +734,23 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         for (int g : active) {
             const Ctl &k = hCtl[g];
             if (k.err_timeout) timeout = true;
-            if (!k.done) keep.push_back(g);
-            else if (k.status == qpr::kCtlNonFinite) continue;
-            else if (k.resid_exact_step == k.step) continue;  // decided by an exact refresh
-            else confirm.push_back(g);
+            if (!k.done) {
+                keep.push_back(g);
+                due[g] = 1;
+                if (adaptive) {
+                    const double r = k.resid;
+                    if (r0[g] < 0.0) r0[g] = r;
+                    const double next = (double)(since[g] + block);
+                    due[g] = !(r > 0.0 && next <= (double)qpr::kMaxRefreshGrowth * block &&
+                               next * next * r <= (double)block * block * r0[g]);
+                }
+            } else if (k.status == qpr::kCtlNonFinite) {
+                continue;
+            } else if (k.resid_exact_step == k.step) {
+                continue;  // decided by an exact refresh
+            } else {
+                confirm.push_back(g);
+            }
         }
         if (!confirm.empty()) {
             for (int g : confirm) {
@@ -731,7 +765,11 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
             BCUDA(cudaStreamSynchronize(s));
             BCUDA(cudaGetLastError());
             for (int g : confirm)
-                if (!hCtl[g].done) keep.push_back(g);
+                if (!hCtl[g].done) {
+                    keep.push_back(g);
+                    due[g] = adaptive ? 0 : 1;  // stepping on from this refresh
+                    since[g] = 0;
+                }
         }
         std::sort(keep.begin(), keep.end());
         active.swap(keep);

@@ -63,6 +63,7 @@ struct qpr_ctx {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_c = nullptr;  // mixed form: a block of steps without the refresh
     int graph_steps = 0;
     qpr::DevOps ops{};
     qpr::Work work{};
@@ -230,15 +231,15 @@ qpr_status run_rk4(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     return QPR_OK;
 }
 
-// One block of the mixed form: the exact refresh, then `steps` delta steps
-// (one persistent launch, or the kernels of every stage).
-qpr_status launch_mixed_block(qpr_ctx *ctx, int steps) {
-    qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
-    if (ctx->persist_grid > 0) {
-        QPR_CUDA(ctx, qpr::launch_cols_block(ctx->ops, ctx->mw, steps, ctx->persist_grid, ctx->stream));
-        ctx->launches += qpr::kMixedLaunchesPerRefresh + 1;
-        return QPR_OK;
+// One block of the persistent mixed form: the exact refresh (unless
+// `refresh` is false), then `steps` delta steps in one launch.
+qpr_status launch_mixed_block(qpr_ctx *ctx, int steps, bool refresh) {
+    if (refresh) {
+        qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+        ctx->launches += qpr::kMixedLaunchesPerRefresh;
     }
+    QPR_CUDA(ctx, qpr::launch_cols_block(ctx->ops, ctx->mw, steps, ctx->persist_grid, ctx->stream));
+    ctx->launches += 1;
     return QPR_OK;
 }
 
@@ -247,24 +248,31 @@ int mixed_launches_per_step(const qpr_ctx *ctx) {
     return (ctx->mw.splitD ? 2 : 1) * qpr::kMixedLaunchesPerStep;
 }
 
-void enqueue_mixed_block(qpr_ctx *ctx, int steps) {
-    qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+void enqueue_mixed_block(qpr_ctx *ctx, int steps, bool refresh = true) {
+    if (refresh) qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
     for (int k = 0; k < steps; ++k)
         for (int s = 1; s <= 4; ++s) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream);
 }
 
+// Two graphs: refresh + ref_refresh steps, and ref_refresh steps alone.
 qpr_status ensure_mixed_graph(qpr_ctx *ctx) {
     if (ctx->graph || ctx->opt.graph_steps <= 0 || ctx->persist_grid > 0) return QPR_OK;
-    cudaGraph_t g = nullptr;
-    QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_mixed_block(ctx, ctx->opt.ref_refresh);
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        ctx->graph = nullptr;
-        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    for (int k = 0; k < 2; ++k) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t *dst = k == 0 ? &ctx->graph : &ctx->graph_c;
+        QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_mixed_block(ctx, ctx->opt.ref_refresh, k == 0);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(dst, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *dst = nullptr;
+            if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph_c) cudaGraphExecDestroy(ctx->graph_c);
+            ctx->graph = nullptr;
+            return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
     }
     ctx->graph_steps = ctx->opt.ref_refresh;
     return QPR_OK;
@@ -279,6 +287,15 @@ qpr_status read_ctl(qpr_ctx *ctx) {
 // device stops. A stop on the FP32-accurate estimate is confirmed by an exact
 // refresh at the same step; the run always ends with a refresh, so R holds
 // the normalised returned state and resid_exact its exact FP64 residual.
+//
+// Steady-state solves (tol > 0) with adaptive_refresh lengthen the window
+// between refreshes as the residual falls: the FP32 error a window adds to
+// the state grows about as (window steps)^2 x ||f||, so a block continues
+// without a refresh while (steps since the refresh)^2 x r stays within
+// ref_refresh^2 x r0 (r: the residual estimate of the last step, r0: the
+// one after the first block), at most kMaxRefreshGrowth x ref_refresh steps.
+// The batched solver applies the same rule per problem.
+using qpr::kMaxRefreshGrowth;
 qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     Ctl *h = ctx->h_ctl;
     memset(h, 0, sizeof(Ctl));
@@ -291,22 +308,39 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     qpr_status st = ensure_mixed_graph(ctx);
     if (st != QPR_OK) return st;
     const int block = ctx->opt.ref_refresh;
+    const bool adaptive = tol > 0.0 && ctx->opt.adaptive_refresh != 0;
+    bool refresh = true;
+    int64_t since = 0;  // steps since the last refresh
+    double r0 = -1.0;
     for (;;) {
         if (ctx->persist_grid > 0) {
-            st = launch_mixed_block(ctx, block);
+            st = launch_mixed_block(ctx, block, refresh);
             if (st != QPR_OK) return st;
         } else {
-            if (ctx->graph) {
-                QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+            cudaGraphExec_t g = refresh ? ctx->graph : ctx->graph_c;
+            if (g) {
+                QPR_CUDA(ctx, cudaGraphLaunch(g, ctx->stream));
             } else {
-                enqueue_mixed_block(ctx, block);
+                enqueue_mixed_block(ctx, block, refresh);
             }
-            ctx->launches += qpr::kMixedLaunchesPerRefresh + mixed_launches_per_step(ctx) * (int64_t)block;
+            ctx->launches += (refresh ? qpr::kMixedLaunchesPerRefresh : 0) +
+                             mixed_launches_per_step(ctx) * (int64_t)block;
         }
+        since = (refresh ? 0 : since) + block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
         if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
-        if (!h->done) continue;
+        if (!h->done) {
+            refresh = true;
+            if (adaptive) {
+                const double r = h->resid;
+                if (r0 < 0.0) r0 = r;
+                const double next = (double)(since + block);
+                refresh = !(r > 0.0 && next <= (double)kMaxRefreshGrowth * block &&
+                            next * next * r <= (double)block * block * r0);
+            }
+            continue;
+        }
         if (h->status == qpr::kCtlNonFinite) return QPR_OK;
         if (h->resid_exact_step == h->step) return QPR_OK;  // stopped by an exact refresh at this step
         // confirm (or finish) with an exact refresh at the current step
@@ -322,6 +356,9 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         if (h->done) return QPR_OK;  // converged, max steps or non-finite, decided exactly
         if (prev == qpr::kCtlMaxSteps) return QPR_OK;
         // the estimate passed but the exact residual did not: keep stepping
+        // from this refresh
+        refresh = !adaptive;
+        since = 0;
     }
 }
 
@@ -520,6 +557,7 @@ qpr_status qpr_default_options(qpr_options *opt) {
     opt->device = -1;
     opt->backend = QPR_BACKEND_AUTO;
     opt->ref_refresh = 32;
+    opt->adaptive_refresh = 1;
     return QPR_OK;
 }
 
@@ -568,6 +606,7 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->colmaps.side) cudaStreamSynchronize(ctx->colmaps.side);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph_c) cudaGraphExecDestroy(ctx->graph_c);
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_hptr);
     cudaFree(ctx->d_rowseg);

@@ -281,6 +281,9 @@ cudaError_t launch_cols_block(const DevOps &ops, const MixedWork &w, int steps, 
 constexpr int kMixedLaunchesPerStep = 4;   // tile-pair sparse kernel (the dense one adds 4 gain kernels)
 constexpr int kMixedLaunchesPerStepCols = 12;  // column-block form: gain, SpMM and epilogue per stage
 constexpr int kMixedLaunchesPerRefresh = 5;
+// Steady-state solves with adaptive_refresh: the longest window between
+// refreshes, in multiples of ref_refresh.
+constexpr int kMaxRefreshGrowth = 8;
 
 // ---- host assembly (qpr_api.cu) ----
 struct HostOps {

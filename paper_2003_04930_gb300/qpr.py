@@ -41,7 +41,8 @@ class qpr_options(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("backend", ctypes.c_int32),
                 ("ref_refresh", ctypes.c_int32), ("sparse_form", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_int32), ("row_splits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("chunk_rows", ctypes.c_int32), ("row_splits", ctypes.c_int32),
+                ("adaptive_refresh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class qpr_stats(ctypes.Structure):
@@ -186,7 +187,7 @@ class Solver:
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0, row_splits=0):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0, row_splits=0, adaptive_refresh=1):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -203,6 +204,7 @@ class Solver:
         opt.sparse_form = int(sparse_form)
         opt.chunk_rows = int(chunk_rows)
         opt.row_splits = int(row_splits)
+        opt.adaptive_refresh = int(adaptive_refresh)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         h = ctypes.c_void_p()

@@ -90,6 +90,28 @@ def test_mixed_steady_state(n, omega):
     assert abs(stats["residual"] - o.residual(got)) <= 1e-12
 
 
+@pytest.mark.parametrize("n,omega", [(150, 0.5), (400, 0.8)])
+def test_adaptive_refresh_window(n, omega):
+    # steady states with the lengthening refresh window (default) and with a
+    # refresh every ref_refresh steps: both within the precision form's
+    # bounds of the oracle, the same step count within 1, fewer launches
+    g = graphs.heavy_tailed(n, 3)
+    o = Oracle.from_edges(g, alpha=0.85, omega=omega)
+    rho0 = graphs.maximally_mixed(n)
+    ref, steps_ref, _, _ = o.steady_state(rho0, 0.01, 1e-8, 200000)
+    got, stats = {}, {}
+    for adaptive in (0, 1):
+        s = _mixed(g, alpha=0.85, omega=omega, backend=Q.QPR_BACKEND_SPARSE, adaptive_refresh=adaptive)
+        d = _dev(rho0)
+        stats[adaptive] = s.steady_state(d, 0.01, 1e-8, 200000)
+        got[adaptive] = d.cpu().numpy()
+        assert stats[adaptive]["converged"] == 1 and stats[adaptive]["residual"] < 1e-8
+        assert abs(stats[adaptive]["steps"] - steps_ref) <= 1
+        assert abs(stats[adaptive]["residual"] - o.residual(got[adaptive])) <= 1e-12
+        _close(got[adaptive], ref)
+    assert stats[1]["kernel_launches"] < stats[0]["kernel_launches"]
+
+
 def test_mixed_not_converged_and_zero_steps():
     g = graphs.heavy_tailed(60, 5)
     o = Oracle.from_edges(g, alpha=0.85, omega=0.5)
