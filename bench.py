@@ -353,7 +353,8 @@ def run_ours(a):
                              "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                              "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                              "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
-                "note": "launch_ms from CUDA events around each launch (includes the launch gap)" +
+                "note": "launch_ms from CUDA events around each launch (includes the launch gap; the SpMM's "
+                        "gain branch runs beside it on a forked stream and is not included)" +
                         ("; the state is L2-resident at this N, so the epilogue's HBM fraction can exceed 1"
                          if 16 * 4 * n * n < 100e6 else "")}
     elif s.backend == qpr.QPR_BACKEND_SPARSE:

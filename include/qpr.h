@@ -236,8 +236,10 @@ QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double t
  * bracketing every kernel launch with CUDA events, and writes the mean
  * durations in milliseconds: ms_out[0] one stage kernel (H rho plus the fused
  * epilogue; the epilogue kernel in the column-block form), ms_out[1] one
- * gain kernel (G p; the SpMM kernel in the column-block form, 0 where the
- * stage kernel computes the gain itself), ms_out[2] one whole step.
+ * gain kernel (G p; in the two-launch column-block forms the SpMM kernel
+ * alone, from the end of the previous launch to an event right after it, the
+ * gain running beside it on a forked stream; 0 where the stage kernel
+ * computes the gain itself), ms_out[2] one whole step.
  * Meant for roofline measurements; steps >= 1. */
 QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out);
 

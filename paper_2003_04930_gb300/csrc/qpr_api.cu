@@ -1188,8 +1188,11 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     h->dt = dt;
     h->scale = 1.0;
     QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
-    std::vector<cudaEvent_t> ev(8 * steps + 1);
+    std::vector<cudaEvent_t> ev(8 * steps + 1), mk(4 * steps);
     for (auto &e : ev) QPR_CUDA(ctx, cudaEventCreate(&e));
+    for (auto &e : mk) QPR_CUDA(ctx, cudaEventCreate(&e));
+    const bool cols = ctx->opt.precision == QPR_MIXED && ctx->mw.cmaps && ctx->persist_grid <= 0;
+    int m = 0;
     const qpr::Work &w = ctx->work;
     const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
     const bool mixed = ctx->opt.precision == QPR_MIXED;
@@ -1198,7 +1201,7 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
     for (int64_t k = 0; k < steps; ++k) {
         for (int s = 1; s <= 4; ++s) {
-            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1);
+            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, cols ? mk[m++] : nullptr);
             else qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
             QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
             if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2);
@@ -1218,8 +1221,18 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
         float tot = 0.f;
         cudaEventElapsedTime(&tot, ev[0], ev[q - 1]);
         total_ms = tot;
+        if (cols) {
+            // the column SpMM alone: from the previous event to the mark after its launch
+            gain_ms = 0.0;
+            for (int i = 0; i < m; ++i) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * i], mk[i]);
+                gain_ms += ms;
+            }
+        }
     }
     for (auto &e : ev) cudaEventDestroy(e);
+    for (auto &e : mk) cudaEventDestroy(e);
     if (st != QPR_OK) return st;
     ms_out[0] = stage_ms / (4.0 * steps);
     ms_out[1] = gain_ms / (4.0 * steps);

@@ -205,7 +205,10 @@ cudaError_t init_stage_sparse();
 void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s);
 // One RK4 stage: parts & 1 launches the gain of the stage delta, parts & 2
 // the FP32 sparse stage kernel (3 = both, in that order).
-void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+// mark (column form, optional): an event recorded on s right after the SpMM
+// launch, before the join with the gain branch (profiling).
+void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
+                        cudaEvent_t mark = nullptr);
 // Opt in to the dynamic shared memory of the sparse mixed stage kernels.
 cudaError_t init_stage_mixed();
 // Dense backend of the mixed form (stage_mixed_tc.cu).
@@ -267,7 +270,8 @@ bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc =
 // Opt in to `bytes` of dynamic shared memory (and clusters of cs > 8 CTAs)
 // for the chunked SpMM kernel.
 cudaError_t set_chunk_attrs(int bytes, int cs);
-void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3);
+void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
+                       cudaEvent_t mark = nullptr);
 // Persistent form (stage_persist.cu): one cooperative launch runs up to
 // `steps` RK4 steps of the column-block form, grid barriers between the
 // phases. persist_grid: CTAs of that launch for an np x np problem with the

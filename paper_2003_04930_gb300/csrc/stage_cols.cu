@@ -692,7 +692,8 @@ static void launch_chunks(const CUtensorMap &tm, const DevOps &ops, const MixedW
     cudaLaunchKernelEx(&cfg, cols_chunk_kernel, tm, ops, w);
 }
 
-void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts) {
+void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts,
+                       cudaEvent_t mark) {
     const ColMaps &m = *w.cmaps;
     // whole block: (J, r); gather: (r, J), the splits of a block side by side
     const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCW) : dim3(ops.np / kCW, ops.col_splits);
@@ -721,6 +722,7 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
                 default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, tm, ops, w); break;
             }
         }
+        if (mark) cudaEventRecord(mark, s);
         cudaStreamWaitEvent(s, m.join, 0);
     }
     if (parts & 2) {
