@@ -59,7 +59,7 @@ constexpr int kPiecePart = 2;      // bundle flags: one part of a cut row (its s
 // share and cutting measured slower, so those plans cut nothing and every
 // form there sums each row the same way.
 constexpr int kPartMax = 256;
-constexpr int kCutMaxWaves = 8;
+constexpr int kCutMaxWaves = 12;
 constexpr int kRPG = 2;            // rows (slots) per 8-lane group of a bundle (4 measured slower: more padding)
 
 // A bundle descriptor is 1 + kRPG int4: {first entry (relative to its

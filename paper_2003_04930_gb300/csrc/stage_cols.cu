@@ -461,7 +461,8 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         int slots_max = 0;
         // rows are cut into parts above the whole-block range when the grid
         // has few waves (many waves absorb a long CTA; measured: N = 2048, 3.4
-        // waves, 15% faster with cuts; N = 8192, 40 waves, 5% slower)
+        // waves, 15% faster with cuts; N = 4096, 10 waves, 3% faster; N = 8192,
+        // 40 waves, 5% slower)
         const bool cut = np > kColMaxNp && (double)s * ncb < kCutMaxWaves * kGatherCtasPerSm * (double)sms;
         for (int k = 0; k < s; ++k) {
             const size_t kb = pl.kh.size();  // even: every split's block starts 16-byte aligned
