@@ -106,14 +106,14 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
  *   keeps its rows' sums in shared memory; the same epilogue. Needs thread
  *   block clusters.
  * COLUMNS_GATHER: the column-block product for any N without staging the
- *   block: each CTA (row split r, block J) stages only its CSR entries and
- *   reads every nonzero's 16 values of block J through L1 and L2; the splits of a
- *   block run side by side, so the block is read from DRAM about once.
+ *   block: each CTA (row split r, block J of 32 columns) stages only its CSR
+ *   entries and reads every nonzero's 32 values of block J through L1 and
+ *   L2 (one 128-byte line per plane); the splits of a block run side by
+ *   side, so the block is read from DRAM about once.
  * AUTO (default): COLUMNS where it applies, else COLUMNS_GATHER, else TILES.
- * COLUMNS, COLUMNS_PERSISTENT and COLUMNS_GATHER give bitwise the same
- * results (each row's products summed in entry order); COLUMNS_CHUNKED (per
- * row: chunk by chunk) and TILES differ from them only in FP32 summation
- * order. */
+ * COLUMNS and COLUMNS_PERSISTENT give bitwise the same results (each row's
+ * products summed in entry order); COLUMNS_GATHER, COLUMNS_CHUNKED (per row:
+ * chunk by chunk) and TILES differ from them only in FP32 summation order. */
 enum {
     QPR_SPARSE_FORM_AUTO = 0,
     QPR_SPARSE_FORM_COLUMNS = 1,

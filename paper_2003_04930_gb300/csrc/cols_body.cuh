@@ -33,6 +33,7 @@ using mixed::NT;
 using mixed::TS;
 
 constexpr int kCW = 16;            // complex columns per block
+constexpr int kCWWide = 32;        // complex columns per block of the gather form (one 128-byte line per plane)
 constexpr int kRowFloats = 2 * kCW; // staged row: kCW real, then kCW imaginary values (128 bytes)
 constexpr int kBoxRows = 32;       // rows of one TMA box
 constexpr int kANT = 512;          // threads of the SpMM kernel
@@ -89,20 +90,26 @@ __device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g 
 // was written by the previous kernel; every load is issued after
 // griddepcontrol.wait, which makes that kernel's writes visible, and no
 // kernel reads the stage inputs through L1 before it.
-template <bool ACC = false, bool GMEM = false>
+template <bool ACC = false, bool GMEM = false, bool WIDE = false>
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
                                              float *__restrict__ X, float *acc_rows = nullptr, int row0 = 0,
                                              float *parts = nullptr) {
+    static_assert(!WIDE || (GMEM && !ACC), "the wide layout is the gather form's");
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
     const size_t plane = (size_t)np * np;
-    const int col = J * kCW + 4 * (p & 3);
-    const float *__restrict__ sDp = GMEM ? sD + (p < 4 ? 0 : plane) + col : sD + 4 * p;
+    // narrow: group g = one row, lanes 0-3 real and 4-7 imaginary values of
+    // 16 columns; wide: group pair h = one row, group 2h + pl its plane pl,
+    // 32 columns (one 128-byte line per plane)
+    const int h = WIDE ? (g >> 1) : g;
+    const int pl = WIDE ? (g & 1) : (p < 4 ? 0 : 1);
+    const int col = WIDE ? J * kCWWide + 4 * p : J * kCW + 4 * (p & 3);
+    const float *__restrict__ sDp = GMEM ? sD + pl * plane + col : sD + 4 * p;
     auto row_of = [&](int q) {
         if (GMEM) return __ldca(reinterpret_cast<const float4 *>(sDp + (size_t)q * np));
         return *reinterpret_cast<const float4 *>(sDp + q * kRowFloats);
     };
-    float *__restrict__ Xp = X + (p < 4 ? 0 : plane) + col;
+    float *__restrict__ Xp = X + pl * plane + col;
     auto put = [&](int row, float4 v) {
         if (ACC) {
             float4 *a = reinterpret_cast<float4 *>(acc_rows + (row - row0) * kRowFloats + 4 * p);
@@ -111,10 +118,14 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = v;
         }
     };
+    // int4 entries per round: kRPG / 2 per group (narrow) or group pair (wide)
+    constexpr int RS = (WIDE ? 2 : 4) * (kRPG / 2);
+    constexpr int RowF = WIDE ? 2 * kRowFloats : kRowFloats;  // floats of a partial row
+    const int part_off = WIDE ? pl * kRowFloats + 4 * p : 4 * p;
     for (int b = b0; b < b1; ++b) {
         const int4 *bd = sP + kBundleInt4 * (b - p_base);
         const int4 d0 = bd[0];
-        const int4 *__restrict__ kh = reinterpret_cast<const int4 *>(sKH + d0.x) + g * (kRPG / 2);
+        const int4 *__restrict__ kh = reinterpret_cast<const int4 *>(sKH + d0.x) + h * (kRPG / 2);
         const int T = d0.y;
         float4 acc[kRPG];
 #pragma unroll
@@ -137,7 +148,7 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
 #pragma unroll
                 for (int u = 0; u < U; ++u)
 #pragma unroll
-                    for (int s2 = 0; s2 < kRPG / 2; ++s2) e[u][s2] = kh[2 * kRPG * (t + u) + s2];
+                    for (int s2 = 0; s2 < kRPG / 2; ++s2) e[u][s2] = kh[RS * (t + u) + s2];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -156,7 +167,7 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             for (; t < T; ++t) {
 #pragma unroll
                 for (int s2 = 0; s2 < kRPG / 2; ++s2) {
-                    const int4 e = kh[2 * kRPG * t + s2];
+                    const int4 e = kh[RS * t + s2];
                     const float4 v0 = fetch(e.x, e.y), v1 = fetch(e.z, e.w);
                     acc[2 * s2] = f4fma(__int_as_float(e.y), v0, acc[2 * s2]);
                     acc[2 * s2 + 1] = f4fma(__int_as_float(e.w), v1, acc[2 * s2 + 1]);
@@ -167,7 +178,7 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             for (int t = 0; t < T; ++t) {
 #pragma unroll
                 for (int s2 = 0; s2 < kRPG / 2; ++s2) {
-                    const int4 e = kh[2 * kRPG * t + s2];
+                    const int4 e = kh[RS * t + s2];
                     acc[2 * s2] = f4fma(__int_as_float(e.y), row_of(e.x), acc[2 * s2]);
                     acc[2 * s2 + 1] = f4fma(__int_as_float(e.w), row_of(e.z), acc[2 * s2 + 1]);
                 }
@@ -177,18 +188,18 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
             float4 a = acc[0];
 #pragma unroll
             for (int s = 1; s < kRPG; ++s) a = f4add(a, acc[s]);
-            a = mixed::f4xor(a, 8);
+            if (!WIDE) a = mixed::f4xor(a, 8);
             a = mixed::f4xor(a, 16);
-            if (g == 0) {
+            if (h == 0) {
                 if (d0.z & kPiecePart)
-                    *reinterpret_cast<float4 *>(parts + bd[1].x * kRowFloats + 4 * p) = a;
+                    *reinterpret_cast<float4 *>(parts + bd[1].x * RowF + part_off) = a;
                 else
                     put(bd[1].x, a);
             }
         } else {
 #pragma unroll
             for (int s = 0; s < kRPG; ++s) {
-                const int row = pick(bd[1 + s], g);
+                const int row = pick(bd[1 + s], h);
                 if (row >= 0) put(row, acc[s]);
             }
         }
@@ -199,20 +210,23 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
 // X[row, J] = the sum of the parts' partial rows in slot order (ACC: added
 // to the row's accumulator). Called by all threads after every warp's
 // bundles (and a barrier).
-template <bool ACC = false>
+template <bool ACC = false, bool WIDE = false>
 __device__ __forceinline__ void combine_cuts(const int4 *__restrict__ cuts, int ncut, const float *parts, int J,
                                              int np, float *__restrict__ X, float *acc_rows = nullptr,
                                              int row0 = 0) {
     const size_t plane = (size_t)np * np;
-    for (int e = threadIdx.x; e < ncut * (kRowFloats / 4); e += blockDim.x) {
-        const int4 c = __ldg(cuts + (e >> 3));
-        const int p = e & 7;
-        float4 s = *reinterpret_cast<const float4 *>(parts + c.y * kRowFloats + 4 * p);
+    constexpr int Q = WIDE ? 2 * kRowFloats / 4 : kRowFloats / 4;  // float4 per partial row
+    for (int e = threadIdx.x; e < ncut * Q; e += blockDim.x) {
+        const int4 c = __ldg(cuts + e / Q);
+        const int p = e % Q;  // wide: plane p / 8, columns 4 (p % 8) ..
+        float4 s = *reinterpret_cast<const float4 *>(parts + c.y * 4 * Q + 4 * p);
         for (int k = 1; k < c.z; ++k)
-            s = f4add(s, *reinterpret_cast<const float4 *>(parts + (c.y + k) * kRowFloats + 4 * p));
+            s = f4add(s, *reinterpret_cast<const float4 *>(parts + (c.y + k) * 4 * Q + 4 * p));
         if (ACC) {
             float4 *a = reinterpret_cast<float4 *>(acc_rows + (c.x - row0) * kRowFloats + 4 * p);
             *a = f4add(*a, s);
+        } else if (WIDE) {
+            *reinterpret_cast<float4 *>(X + (p / 8) * plane + (size_t)c.x * np + J * kCWWide + 4 * (p % 8)) = s;
         } else {
             *reinterpret_cast<float4 *>(X + (p < 4 ? 0 : plane) + (size_t)c.x * np + J * kCW + 4 * (p & 3)) = s;
         }

@@ -85,8 +85,9 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
 
 // Gather form of the SpMM, for N too large to stage a column block: CTA
 // (r, J) stages only its split's entries and bundles and reads each
-// nonzero's 16 values of block J straight from the stage input (two 64-byte
-// segments per row, L1-cached loads). The grid runs the row splits of one
+// nonzero's 32 values of the 32-column block J straight from the stage input
+// (one 128-byte line per plane and row, L1-cached loads; the wide layout of
+// warp_bundles: a group pair per row). The grid runs the row splits of one
 // column block next to each other, so the block's rows (np x 128 bytes) are
 // read from DRAM about once and then served by L2 to the splits.
 template <int STAGE>
@@ -123,11 +124,12 @@ __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(Dev
         return;
     }
     float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-    warp_bundles<false, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, nullptr, 0, parts);
+    warp_bundles<false, true, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, nullptr, 0,
+                                    parts);
     const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
     if (cb1 > cb0) {
         __syncthreads();
-        combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
+        combine_cuts<false, true>(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
     }
 }
 
@@ -306,12 +308,15 @@ using RowEntries = std::vector<std::vector<int2>>;
 // 0: rows longer than part_max are cut into parts (bundles whose sums go to
 // partial slots 0, 1, ... of this block); each cut row appends {row, first
 // slot, parts, 0} to `cuts`. Returns the number of partial slots.
+// groups: row slots per round of a bundle, 4 (one per 8-lane group) or 2 (the
+// wide layout: one per group pair).
 int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::vector<int2> &kh,
                   std::vector<int4> &pieces, std::vector<int> &wb, std::vector<int4> &cuts, int part_max,
-                  bool skip_empty = false) {
-    constexpr int kSlots = 4 * kRPG;
+                  bool skip_empty = false, int groups = 4) {
+    constexpr int kMaxSlots = 4 * kRPG;
+    const int kSlots = groups * kRPG;
     struct Bundle {
-        int rows[kSlots];
+        int rows[kMaxSlots];
         int T;
         bool lng, part;
         int src, e0, e1;  // long rows and parts: the row and its entries [e0, e1)
@@ -323,7 +328,7 @@ int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::ve
     auto row_len = [&](int i) { return (int)ent[i - r0].size(); };
     auto fresh = [&](int T, bool lng) {
         Bundle b;
-        for (int j = 0; j < kSlots; ++j) b.rows[j] = -1;
+        for (int j = 0; j < kMaxSlots; ++j) b.rows[j] = -1;
         b.T = T;
         b.lng = lng;
         b.part = false;
@@ -380,19 +385,21 @@ int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::ve
             const Bundle &b = bs[k];
             pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T,
                                        (b.lng ? kPieceLong : 0) | (b.part ? kPiecePart : 0), 0));
-            // slot s of group g is rows[g + 4 s]
-            for (int s = 0; s < kRPG; ++s)
-                pieces.push_back(make_int4(b.rows[4 * s], b.rows[4 * s + 1], b.rows[4 * s + 2], b.rows[4 * s + 3]));
+            // slot s of group g is rows[g + groups s]
+            for (int s = 0; s < kRPG; ++s) {
+                const int *rw = b.rows + groups * s;
+                pieces.push_back(make_int4(rw[0], rw[1], groups > 2 ? rw[2] : -1, groups > 3 ? rw[3] : -1));
+            }
             // round t, group g, slot s -> position kSlots t + kRPG g + s
             for (int t = 0; t < b.T; ++t)
-                for (int g = 0; g < 4; ++g)
+                for (int g = 0; g < groups; ++g)
                     for (int sl = 0; sl < kRPG; ++sl) {
                         int2 v = make_int2(0, 0);
                         if (b.lng) {
                             const int e = b.e0 + kSlots * t + kRPG * g + sl;
                             if (e < b.e1) v = ent[b.src - r0][e];
                         } else {
-                            const int row = b.rows[g + 4 * sl];
+                            const int row = b.rows[g + groups * sl];
                             if (row >= 0 && t < row_len(row)) v = ent[row - r0][t];
                         }
                         kh.push_back(v);
@@ -428,7 +435,7 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
     }
     const int smem_max = max_smem_optin(device);
     const int n = (int)h.n;
-    const int ncb = np / kCW;
+    const int ncb = np / (gather ? kCWWide : kCW);  // the gather form: 32-column blocks
     // cumulative row cost (nonzeros + a per-row overhead) for the splits
     std::vector<double> cum(np + 1, 0.0);
     for (int i = 0; i < np; ++i) {
@@ -472,7 +479,7 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
             RowEntries ent;
             for (int i = rows[k]; i < rows[k + 1]; ++i) ent.push_back(row_entries(h, i, 0, np));
             slots_max = std::max(slots_max, split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb,
-                                                          pl.cuts, cut ? kPartMax : 0));
+                                                          pl.cuts, cut ? kPartMax : 0, false, gather ? 2 : 4));
             if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
             pl.q.push_back((int)kb);
             pl.q.push_back((int)pl.kh.size());
@@ -482,7 +489,7 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
         pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
         pl.cutb.push_back((int)pl.cuts.size());
-        const size_t part_bytes = (size_t)slots_max * kRowFloats * 4;
+        const size_t part_bytes = (size_t)slots_max * kRowFloats * 4 * (gather ? 2 : 1);
         size_t smem, cap;
         if (gather) {
             // entries, bundles, partial slots; small enough for kGatherCtasPerSm CTAs per SM
@@ -696,8 +703,8 @@ static void launch_chunks(const CUtensorMap &tm, const DevOps &ops, const MixedW
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts,
                        cudaEvent_t mark) {
     const ColMaps &m = *w.cmaps;
-    // whole block: (J, r); gather: (r, J), the splits of a block side by side
-    const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCW) : dim3(ops.np / kCW, ops.col_splits);
+    // whole block: (J, r); gather: (r, J) over 32-column blocks, the splits of a block side by side
+    const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCWWide) : dim3(ops.np / kCW, ops.col_splits);
     const size_t sm = (size_t)ops.col_smem;
     const CUtensorMap &tm = m.d[stage == 1 ? 0 : (stage == 3 ? 2 : 1)];
     if (parts & 1) {

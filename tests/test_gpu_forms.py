@@ -4,13 +4,14 @@ block of steps), its gather form (rows of the block read from L2, for any
 N), its chunked form (clusters streaming the column block in chunks, for any
 N) and the tile-pair form.
 
-The whole-block and gather column forms run the same device arithmetic (row
+The two whole-block column forms run the same device arithmetic (row
 products in entry order, the same gain and epilogue sums, the same stop
 decision), so their states, step counts and residuals are bitwise equal.
 The chunked form sums each row chunk by chunk, so it equals them bitwise
-when the block is one chunk. The chunked and tile-pair forms sum the
-products in other FP32 orders and are held, like every form, to the mixed
-form's tolerances against the FP64 oracle: trajectories (t = 1.5)
+when the block is one chunk. The gather form (32-column blocks, a row's
+long sums dealt over 4 partial sums instead of 8), the chunked and the
+tile-pair forms sum the products in other FP32 orders and are held, like
+every form, to the mixed form's tolerances against the FP64 oracle: trajectories (t = 1.5)
 ||drho||_F <= 1e-6 and max|dp| <= 1e-6 max p, steady states ||drho||_F <= 1e-6
 and max|dp| <= 1e-7 max p. Small chunk_rows make the chunked form stream
 several chunks (both buffers, both barrier phases, a ragged last chunk
@@ -29,7 +30,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 FORMS = (Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_COLUMNS_GATHER,
          Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, Q.QPR_SPARSE_FORM_TILES)
-BITWISE = (Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_COLUMNS_GATHER)  # equal to COLUMNS
+BITWISE = (Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT,)  # equal to COLUMNS
 
 
 def _chunk_rows(n):
