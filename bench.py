@@ -222,6 +222,22 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- ours
+def replica_time(local_total, steps, dist=None, device=None):
+    """Replicas (one independent solve stream per rank): the slowest rank's
+    timed total, max over ranks, and the time per solve over the solves of
+    all ranks. Returns (seconds per solve, max total)."""
+    import torch
+
+    world = 1
+    total = float(local_total)
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total / (steps * world), total
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -279,12 +295,7 @@ def run_ours(a):
         stats.append(st)
     barrier()
     clocks = sampler.stop()
-    total = sum(times)
-    if dist is not None:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = total / (a.steps * world)
+    value, total = replica_time(sum(times), a.steps, dist, dev)
     steps_conv = stats[-1]["steps"]
     rho_solved = rho.clone()  # this form's steady state, compared with the FP64 sparse form's below
 
