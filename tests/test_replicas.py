@@ -30,7 +30,7 @@ def _rank(rank, world, port, totals, steps, out):
 def test_replica_time_is_max_over_ranks(totals):
     steps, world = 3, 2
     port = 29500 + int(totals[0] * 10) % 400
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()  # no fork of this (threaded) process
     mp.spawn(_rank, args=(world, port, totals, steps, out), nprocs=world, join=True)
     want = max(totals)
     for r in range(world):
