@@ -287,7 +287,7 @@ __device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, 
 // the nparts residual-estimate partials in index order, records the
 // estimate and, when the run stops here, sets done so that the kernels of
 // stages 2..4 return at once. A step whose exact residual a refresh already
-// judged is not judged again. Called by every thread after tile_epilogue.
+// decided is not decided again. Called by every thread after tile_epilogue.
 // Stop decision from the stage-1 partials of step `step` (every thread of
 // the CTA calls it; all CTAs that call it compute the same sum in index
 // order). Returns the status; the CTA with `record` writes it to ctl.

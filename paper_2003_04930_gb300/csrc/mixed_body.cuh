@@ -328,8 +328,8 @@ __device__ __forceinline__ void gain_rows(const DevOps &ops, const float *__rest
 // FP32-accurate estimate of ||f(y_n)||_F; a pass is confirmed by an exact
 // FP64 refresh on the host side of the loop). Every CTA sums the partials in
 // the same order and reaches the same decision; the one with `first`
-// records it. A step index whose exact residual a refresh already judged is
-// not judged again. Returns true when the run stops (uniform over the CTA).
+// records it. A step index whose exact residual a refresh already decided is
+// not decided again. Returns true when the run stops (uniform over the CTA).
 __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
     __shared__ float red[32];
     __shared__ int s_status;
