@@ -409,7 +409,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         od[g] = nd;
         nd += qpr::align_up(2 * p2 + 2 * np[g] + nh + ns + npairs[g], 64);
         of[g] = nf;
-        nf += qpr::align_up(8 * p2 + 3 * np[g] + qpr::align_up(nh, 64) + qpr::align_up(ns, 64) + npairs[g], 64) + 64;
+        nf += qpr::align_up(7 * p2 + 3 * np[g] + qpr::align_up(nh, 64) + qpr::align_up(ns, 64) + npairs[g], 64) + 64;
         oi[g] = ni;
         ni += qpr::align_up(2 * (n + 1) + nh + ns, 64) + qpr::align_up((size_t)np[g] + 1, 64) + 2 * segs[g].size();
         ni = qpr::align_up(ni, 64);
@@ -552,11 +552,11 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         std::copy(cg.begin(), cg.end(), hD.begin() + (c - dD));
         std::copy(h.hval.begin(), h.hval.end(), hD.begin() + (hval - dD));
         std::copy(h.sval.begin(), h.sval.end(), hD.begin() + (sval - dD));
-        // float arena: F32 D Dlo da db S Ghi Glo | g32 pv32 c32 | hval32 | sval32 | partials32
+        // float arena: F32 D Dlo da db Ghi Glo | g32 pv32 c32 | hval32 | sval32 | partials32
         // (uploaded from zeros, so the delta D + Dlo starts at 0)
         float *F32 = bf, *Dp = bf + p2, *Dlo = bf + 2 * p2, *da = bf + 3 * p2, *db = bf + 4 * p2;
-        float *S = bf + 5 * p2, *Ghi = bf + 6 * p2, *Glo = bf + 7 * p2;
-        float *g32 = bf + 8 * p2, *pv32 = g32 + p, *c32 = pv32 + p, *hv32 = c32 + p;
+        float *Ghi = bf + 5 * p2, *Glo = bf + 6 * p2;
+        float *g32 = bf + 7 * p2, *pv32 = g32 + p, *c32 = pv32 + p, *hv32 = c32 + p;
         float *sv32 = hv32 + qpr::align_up(nh, 64), *part32 = sv32 + qpr::align_up(ns, 64);
         for (int j = 0; j < p; ++j) hF[(c32 - dF) + j] = (float)cg[j];
         for (size_t q = 0; q < nh; ++q) hF[(hv32 - dF) + q] = (float)h.hval[q];
@@ -619,7 +619,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         d.ops.inv_n32 = (float)(1.0 / (double)n);
         qpr::MixedWork &mw = d.mw;
         mw.R = R; mw.F = F;
-        mw.F32 = F32; mw.D = Dp; mw.Dlo = Dlo; mw.da = da; mw.db = db; mw.S = S; mw.Ghi = Ghi; mw.Glo = Glo;
+        mw.F32 = F32; mw.D = Dp; mw.Dlo = Dlo; mw.da = da; mw.db = db; mw.Ghi = Ghi; mw.Glo = Glo;
         mw.g = g32; mw.pv = pv32; mw.g64 = g64; mw.partials = part; mw.partials32 = part32;
         mw.X = colg[g] ? dXC + oxc[g] : nullptr;
         mw.pairs = nullptr; mw.npairs = npairs[g]; mw.tiles = T[g];

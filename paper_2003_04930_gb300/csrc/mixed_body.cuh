@@ -79,9 +79,8 @@ __device__ __forceinline__ ff ff_mul_f(float ah, float al, float b) {
 }
 
 // Delta update of stage 4 for one real component: delta + dt F + c s4 in
-// float-float, with dt F = (gh, gl) and the step weight c = (ch, cl) (dt for
-// the nested form of the FP32 stages, dt / 6 for the classical form of the
-// tensor-core stage).
+// float-float, with dt F = (gh, gl) and the step weight c = (ch, cl) (dt in
+// the nested RK4 form).
 __device__ __forceinline__ ff delta_update(float dh, float dl, float gh, float gl, float ch, float cl, float s4) {
     const ff u = ff_mul_f(ch, cl, s4);
     const ff t = ff_add(u.hi, u.lo, gh, gl);
@@ -579,10 +578,7 @@ __device__ __forceinline__ void refresh_trace_body(const DevOps &ops, const Mixe
             ctl->status = kCtlNonFinite;
             ctl->done = 1;
         }
-        const double dt6 = ctl->dt / 6.0;
         ctl->dtf = (float)ctl->dt;
-        ctl->dt6h = (float)dt6;
-        ctl->dt6l = (float)(dt6 - (double)ctl->dt6h);
         ctl->dtl = (float)(ctl->dt - (double)ctl->dtf);
         ctl->dt3 = (float)(ctl->dt / 3.0);
     }

@@ -39,7 +39,7 @@ struct qpr_ctx {
     // device work
     double *d_state = nullptr;  // y, z, ya, yb: 2 planes each
     double *d_mix64 = nullptr;  // mixed form: R, F (2 planes each)
-    float *d_mix32 = nullptr;   // mixed form: F32, D, Dlo, da, db, S, Ghi, Glo (2 planes each)
+    float *d_mix32 = nullptr;   // mixed form: F32, D, Dlo, da, db, Ghi, Glo (2 planes each)
     float *d_g32 = nullptr, *d_hval32 = nullptr, *d_c32 = nullptr, *d_sval32 = nullptr, *d_partials32 = nullptr;
     __nv_bfloat16 *d_hsplit = nullptr;  // dense mixed form: H split into 3 BF16 planes
     __nv_bfloat16 *d_dsplit = nullptr;  // dense mixed form: 3 delta-split buffers of 6 planes
@@ -840,8 +840,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
     if (o.precision == QPR_MIXED) {
         CREATE_CUDA(cudaMalloc(&ctx->d_mix64, 4 * plane * sizeof(double)));
         CREATE_CUDA(cudaMemset(ctx->d_mix64, 0, 4 * plane * sizeof(double)));
-        CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 16 * plane * sizeof(float)));
-        CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 16 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&ctx->d_mix32, 14 * plane * sizeof(float)));
+        CREATE_CUDA(cudaMemset(ctx->d_mix32, 0, 14 * plane * sizeof(float)));
         CREATE_CUDA(cudaMalloc(&ctx->d_g32, 2 * np * sizeof(float)));  // g, then the diagonal vector pv
         CREATE_CUDA(cudaMemset(ctx->d_g32, 0, 2 * np * sizeof(float)));
         CREATE_CUDA(cudaMalloc(&ctx->d_partials32, std::max<size_t>(pairs.size(), (size_t)npairs_tc) * sizeof(float)));
@@ -961,9 +961,8 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         mw.Dlo = ctx->d_mix32 + 4 * plane;
         mw.da = ctx->d_mix32 + 6 * plane;
         mw.db = ctx->d_mix32 + 8 * plane;
-        mw.S = ctx->d_mix32 + 10 * plane;
-        mw.Ghi = ctx->d_mix32 + 12 * plane;
-        mw.Glo = ctx->d_mix32 + 14 * plane;
+        mw.Ghi = ctx->d_mix32 + 10 * plane;
+        mw.Glo = ctx->d_mix32 + 12 * plane;
         mw.partials32 = ctx->d_partials32;
         if (cols) {
             const size_t nq = chunked ? kplan.q.size() : cplan.q.size();

@@ -36,9 +36,9 @@ struct Ctl {
     int err_timeout;    // a bounded device-side wait gave up
     int ticket;         // CTAs of the current stage-1 epilogue that finished (column-block form)
     // FP32 forms of dt for the mixed form's delta stages, written by its
-    // refresh: dtf = fl(dt), dt = dtf + dtl and dt / 6 = dt6h + dt6l as
-    // float-float pairs, dt3 = fl(dt / 3)
-    float dtf, dt6h, dt6l, dtl, dt3, pad2_;
+    // refresh: dtf = fl(dt), dt = dtf + dtl as a float-float pair, dt3 =
+    // fl(dt / 3)
+    float dtf, dtl, dt3, pad2_;
     // grid barrier of the persistent column-block kernel: arrivals, generation
     unsigned gb_count, gb_gen;
 };
@@ -125,12 +125,12 @@ struct Work {
 // y = R + delta: FP64 R = y / tr(y) at the last refresh and F = f(R); the
 // delta since that refresh as a float-float pair of FP32 planes, D (high
 // part, the FP32 delta the stages read) and Dlo (low part). FP32 (two np x np
-// planes each): F32 = fl(F), dt F = Ghi + Glo (float-float), the stage
-// deltas da/db and the RK4 sum S.
+// planes each): F32 = fl(F), dt F = Ghi + Glo (float-float) and the stage
+// inputs da/db (the nested RK4 form keeps no running stage sum).
 struct TcMaps;
 struct MixedWork {
     double *R, *F;
-    float *F32, *D, *Dlo, *da, *db, *S, *Ghi, *Glo;
+    float *F32, *D, *Dlo, *da, *db, *Ghi, *Glo;
     float *g;             // gain of the stage delta, np
     float *pv;            // np: diagonal of the next stage input (written by every epilogue, zeroed by a refresh)
     double *g64;          // FP64 gain used by the refresh, np
