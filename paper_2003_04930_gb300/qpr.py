@@ -183,11 +183,20 @@ def _check_rho(rho, n):
 
 
 class Solver:
-    """One problem (graph, alpha, omega) bound to a CUDA device."""
+    """One problem (graph, alpha, omega) bound to a CUDA device.
+
+    The keyword options are the fields of qpr_options (include/qpr.h):
+    precision (QPR_FP64 or QPR_MIXED), backend, h_diag, dangling,
+    graph_steps, ref_refresh, sparse_form (the mixed sparse stage's form),
+    chunk_rows (COLUMNS_CHUNKED), row_splits (COLUMNS, COLUMNS_GATHER) and
+    adaptive_refresh (steady-state solves of the mixed form); stream is a
+    torch stream (or a raw cudaStream_t) the caller's inputs are ordered on.
+    """
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0, row_splits=0, adaptive_refresh=1):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0,
+                 row_splits=0, adaptive_refresh=1):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
