@@ -103,3 +103,13 @@ def test_batch_rejects_invalid_problem_before_cuda(lib):
     assert st == qpr.QPR_E_GRAPH
     assert b"problem 0" in lib.qpr_last_error(None)
     assert lib.qpr_batch_steady_state(0, arr, 0.85, 0.01, 1e-8, 10, None, None) == qpr.QPR_E_ARG
+
+
+def test_injected_allocation_failure_is_reported(lib, monkeypatch):
+    # the library's host-side fault injection: qpr_create fails with QPR_E_OOM,
+    # leaves no context behind and says why
+    monkeypatch.setenv("QPR_FAULT", "oom")
+    st, h = _create(lib, n=4, src=[0, 1, 2], dst=[1, 2, 3], device=0)
+    assert st == qpr.QPR_E_OOM
+    assert not h.value
+    assert b"injected allocation failure" in lib.qpr_last_error(None)
