@@ -12,6 +12,12 @@ trace reductions, stop decision). `value` is seconds per solve (lower is
 better); with N ranks each rank solves its own copy (replicas) and `value` is
 the slowest rank's time divided by the solves of all ranks.
 
+Besides the timed steps, rank 0 adds: the roofline of the dominant kernel
+(each kernel timed alone by qpr_profile_step), the exact FP64 sparse form and
+the plain dense FP64 (DMMA) form on the same problem, the learned warm start,
+an end-to-end solve from pinned host memory, the same comparison at N = 4096
+(`n4096`), one 512-graph batched solve (`batch512`) and the CPU oracle.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the plain FP64 C implementation) on a
@@ -75,6 +81,12 @@ def parse_args():
                     help="batch: qpr_batch_steady_state over --batch-count graphs (N ~ U[32,1024], "
                          "omega ~ U[0.1,0.95], seeds 1000+g)")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-large", action="store_true", help="skip the N=4096 sub-object")
+    ap.add_argument("--large-n", type=int, default=4096)
+    ap.add_argument("--large-seed", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batch sub-object")
+    ap.add_argument("--cpu-full-max-s", type=float, default=90.0,
+                    help="run the oracle solve to completion when its estimate is below this many seconds")
     return ap.parse_args()
 
 
@@ -153,28 +165,50 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle
 def cpu_baseline(a, steps_to_converge: int, sample_steps: int = 0):
-    """Time the CPU oracle on a bounded sample of RK4 steps of the workload and
-    scale to one solve of `steps_to_converge` steps."""
+    """The CPU oracle on the same workload, on all host cores: the whole
+    solve to the residual tolerance when its estimate (a short probe) is below
+    --cpu-full-max-s, else a bounded sample of RK4 steps scaled to the solve's
+    step count. Also a single-thread sample (seconds per RK4 step)."""
     from oracle import Oracle
-    from oracle.cpu import max_threads
+    from oracle.cpu import max_threads, set_threads
     from paper_2003_04930_gb300 import graphs
 
     g = graphs.heavy_tailed(a.n, a.seed)
     o = Oracle.from_edges(g, alpha=0.85, omega=a.omega)
-    rho = graphs.maximally_mixed(a.n)
-    probe = 2
+    rho0 = graphs.maximally_mixed(a.n)
+    cores = max_threads()
+    probe = 4
     t = time.perf_counter()
-    rho = o.evolve(rho, a.dt, probe)
+    o.evolve(rho0, a.dt, probe)
     per = (time.perf_counter() - t) / probe
-    r = sample_steps or max(2, min(steps_to_converge, int(15.0 / max(per, 1e-6))))
-    t = time.perf_counter()
-    o.evolve(rho, a.dt, r)
-    el = time.perf_counter() - t
-    per = el / r
-    return {"value": per * steps_to_converge, "unit": "s", "cores": max_threads(), "kind": "oracle",
-            "sample": f"{r} RK4 steps of the same workload timed ({el:.1f} s), scaled by the "
-                      f"{steps_to_converge} steps the solve takes",
-            "seconds_per_rk4_step": per}
+    out = {"unit": "s", "cores": cores, "kind": "oracle"}
+    if not sample_steps and per * steps_to_converge <= a.cpu_full_max_s:
+        t = time.perf_counter()
+        _, steps, resid, _ = o.steady_state(rho0, a.dt, a.tol, a.max_steps)
+        el = time.perf_counter() - t
+        out.update(value=el, sample=f"the whole solve to ||f||_F < {a.tol}: {steps} RK4 steps, final residual "
+                                    f"{resid:.3e}, run to completion on {cores} threads",
+                   steps=steps, seconds_per_rk4_step=el / max(steps, 1), projected=False)
+    else:
+        r = sample_steps or max(2, min(steps_to_converge, int(15.0 / max(per, 1e-6))))
+        t = time.perf_counter()
+        o.evolve(rho0, a.dt, r)
+        el = time.perf_counter() - t
+        out.update(value=el / r * steps_to_converge, projected=True,
+                   sample=f"{r} RK4 steps of the same workload timed ({el:.1f} s), scaled by the "
+                          f"{steps_to_converge} steps the solve takes", seconds_per_rk4_step=el / r)
+    # one thread: a bounded sample of steps (about 5 s), seconds per step
+    set_threads(1)
+    try:
+        r1 = max(2, min(200, int(5.0 / max(per * cores, 1e-6))))
+        t = time.perf_counter()
+        o.evolve(rho0, a.dt, r1)
+        el1 = time.perf_counter() - t
+    finally:
+        set_threads(cores)
+    out["single_thread"] = {"seconds_per_rk4_step": el1 / r1, "sample_steps": r1,
+                            "projected_solve_s": el1 / r1 * steps_to_converge}
+    return out
 
 
 def oracle_steps_to_converge(a):
@@ -201,7 +235,7 @@ def run_reference(a):
     g = graphs.heavy_tailed(a.n, a.seed)
     o = Oracle.from_edges(g, alpha=0.85, omega=a.omega)
     rho = graphs.maximally_mixed(a.n)
-    sample = a.cpu_sample_steps or 20
+    sample = a.cpu_sample_steps or 100
     vals = []
     for k in range(a.warmup + a.steps):
         t = time.perf_counter()
@@ -297,186 +331,37 @@ def run_ours(a):
     clocks = sampler.stop()
     value, total = replica_time(sum(times), a.steps, dist, dev)
     steps_conv = stats[-1]["steps"]
+    n = a.n
     rho_solved = rho.clone()  # this form's steady state, compared with the FP64 sparse form's below
 
-    # per-kernel durations on the solver's stream, same workload and state
-    prof = s.profile_step(rho, a.dt, 20)
+    # per-kernel durations on the solver's stream, same workload and state: each kernel alone between events
     peaks, peak_src = load_peaks()
-    n = a.n
-    if s.backend == qpr.QPR_BACKEND_DENSE and prec == qpr.QPR_MIXED:
-        # split-BF16 GEMM: 6 BF16 products of H (np x np) with [Re | Im] delta
-        # (np x 2 np), 2 flops per multiply-add, executed on the padded np
-        npad = ((n + 127) // 128) * 128
-        flops = 6 * 2.0 * npad * (2 * npad) * npad
-        ach = flops / (prof["stage_ms"] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "stage_mixed_tc_kernel (tcgen05)",
-                "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
-                "peak_source": f"bf16_tflops of {peak_src}"}
-    elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
-            s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER:
-        # gather SpMM: its DRAM floor is one read of the stage input and one
-        # write of X (2 x 8 np^2 bytes); its nonzeros gather nnz(H) x np x 8
-        # bytes of row segments, served mostly by L2 (no measured L2 peak)
-        npad = ((n + 31) // 32) * 32
-        alg = 16 * npad * npad
-        gathered = h_nonzeros(g) * npad * 8
-        ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
-        epi_alg = 44 * n * n  # the nested-RK4 epilogue's mean per stage, as below
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "cols_gather_kernel",
-                "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
-                "peak_source": f"hbm_gbs of {peak_src}",
-                "l2_gather": {"bytes_per_launch": gathered,
-                              "achieved_gbs": gathered / (prof["gain_ms"] * 1e-3) / 1e9},
-                "epilogue": {"kernel": "cols_epi_kernel", "bound": "hbm", "launch_ms": prof["stage_ms"],
-                             "alg_bytes_per_launch": epi_alg, "traffic": None,
-                             "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                             "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                             "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
-                "note": "launch_ms from CUDA events around each launch (includes the launch gap)"}
-    elif s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and \
-            s.sparse_form in (qpr.QPR_SPARSE_FORM_COLUMNS, qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED):
-        chunked = s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED
-        # column-block SpMM: every nonzero of H reads its row slice of each
-        # column block from shared memory, nnz(H) x np x 8 bytes per launch;
-        # bound by shared-memory bandwidth, peak derived from the unit counts
-        # (128 bytes per clock per SM) and the maximum SM clock
-        npad = ((n + 31) // 32) * 32
-        alg = h_nonzeros(g) * npad * 8
-        smem_peak = 128.0 * SMS * SM_MAX_GHZ  # GB/s
-        ach = alg / (prof["gain_ms"] * 1e-3) / 1e9
-        # epilogue kernel (nested RK4 form): N x N FP32 plane pairs (8 bytes
-        # per element) read or written per stage: stage 1 X, D, F32, the next
-        # input (32); stages 2-3 X, the input, F32, D, the next input (40);
-        # stage 4 X, the input, D, Dlo, Ghi, Glo, D and Dlo written (64):
-        # mean (32 + 40 + 40 + 64) / 4 = 44
-        epi_alg = 44 * n * n
-        # DRAM bytes per launch from one ncu capture of the stage-1 launches of these kernels at N=922 (caches
-        # flushed before every replay pass, so one cold pass over the operands): SpMM 7.03 MB, epilogue 14.04 MB
-        spmm_traffic, epi_traffic = (7033600, 14044160) if n == 922 else (None, None)
-        roof = {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
-                "traffic": spmm_traffic, "kernel": "cols_chunk_kernel" if chunked else "cols_spmm_kernel",
-                "alg_bytes_per_launch": alg, "launch_ms": prof["gain_ms"],
-                "peak_source": f"derived: 128 B/clk/SM x {SMS} SMs x {SM_MAX_GHZ} GHz",
-                "epilogue": {"kernel": "cols_epi_kernel", "bound": "hbm", "launch_ms": prof["stage_ms"],
-                             "alg_bytes_per_launch": epi_alg, "traffic": epi_traffic,
-                             "achieved": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                             "frac": epi_alg / (prof["stage_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                             "unit": "GB/s", "peak_source": f"hbm_gbs of {peak_src}"},
-                "note": "launch_ms from CUDA events around each launch (includes the launch gap; the SpMM's "
-                        "gain branch runs beside it on a forked stream and is not included)" +
-                        ("; the state is L2-resident at this N, so the epilogue's HBM fraction can exceed 1"
-                         if 16 * 4 * n * n < 100e6 else "")}
-    elif s.backend == qpr.QPR_BACKEND_SPARSE:
-        if prec == qpr.QPR_MIXED:
-            # mean over the 4 stages of the N x N planes read or written: FP32
-            # delta/D/F32/S planes (8 N^2 bytes each) and, at stage 4, the FP64
-            # y (read and written) and R: (32 + 48 + 48 + 80) / 4 = 52 N^2 bytes
-            alg = 52 * n * n
-            kname = "stage_mixed_sparse_kernel"
-        else:
-            # mean of 4 complex128 N x N matrices per stage (input, y or Z, outputs)
-            alg = 4 * 16 * n * n
-            kname = "stage_sparse_kernel"
-        ach = alg / (prof["stage_ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": kname,
-                "alg_bytes_per_launch": alg, "launch_ms": prof["stage_ms"],
-                "peak_source": f"hbm_gbs of {peak_src}",
-                "note": "state buffers are L2-resident at this N, so the HBM fraction can exceed 1"}
-    else:
-        flops = 4.0 * n ** 3
-        fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
-        ach = flops / (prof["stage_ms"] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None, "kernel": "stage_fp64_kernel (DMMA)",
-                "alg_flops_per_launch": flops, "launch_ms": prof["stage_ms"],
-                "peak_source": f"bf16_tflops of {peak_src} x nominal FP64/BF16 ratio 1.25/2250"}
-
-    form = {(qpr.QPR_FP64, 1): "fp64 dense DMMA", (qpr.QPR_FP64, 2): "fp64 sparse CSR",
-            (qpr.QPR_MIXED, 1): "mixed: split-BF16 tcgen05 GEMM deltas (FP32 accumulate) + fp64 "
-                                "reference/accumulation/residual",
-            (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas (tile pairs) + float-float delta "
-                                "accumulation + fp64 reference/residual"}[(prec, s.backend)]
-    if s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS:
-        form = ("mixed: fp32 column-block SpMM from TMA-staged shared memory + tile-pair epilogue, "
-                "float-float delta accumulation, fp64 reference/residual")
-    elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER:
-        form = ("mixed: fp32 column-block SpMM gathering row segments from L2 + tile-pair epilogue, "
-                "float-float delta accumulation, fp64 reference/residual")
-    elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_CHUNKED:
-        form = ("mixed: fp32 column-block SpMM, block streamed in chunks multicast over a thread-block cluster "
-                "+ tile-pair epilogue, float-float delta accumulation, fp64 reference/residual")
+    prof = s.profile_step(rho, a.dt, 20)
+    roof = roofline(s, g, a.n, prof, peaks, peak_src, prec)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",
-            "config": dict(workload_config(a), form=form, ref_refresh=a.ref_refresh, sparse_plan=s.sparse_plan,
-                           parallelism=f"replicas{world}"),
+            "config": dict(workload_config(a), form=form_name(s, prec), ref_refresh=a.ref_refresh,
+                           sparse_plan=s.sparse_plan, parallelism=f"replicas{world}"),
             "rk4_steps_to_converge": steps_conv, "rk4_steps_per_s": steps_conv / (total / a.steps),
-            "residual": stats[-1]["residual"], "roofline": roof, "clocks": clocks,
+            "residual": stats[-1]["residual"], "roofline": roof, "profile_ms": prof, "clocks": clocks,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats))}
 
     # the plain dense FP64 (DMMA) form on the same problem: s/step x steps
     if not a.no_dense_projection and s.backend != qpr.QPR_BACKEND_DENSE:
-        sd = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=qpr.QPR_BACKEND_DENSE, device=local)
-        pd = sd.profile_step(rho, a.dt, 3)
-        flops = 4.0 * n ** 3
-        fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
-        line["plain_fp64_dense"] = {
-            "ms_per_rk4_step": pd["step_ms"], "projected_time_to_steady_state_s": pd["step_ms"] * 1e-3 * steps_conv,
-            "stage_tflops": flops / (pd["stage_ms"] * 1e-3) / 1e12,
-            "frac_of_fp64_peak": flops / (pd["stage_ms"] * 1e-3) / 1e12 / fp64_peak,
-            "fp64_peak_tflops": fp64_peak, "peak_source": f"bf16_tflops of {peak_src} x 1.25/2250"}
-        sd.close()
+        line["plain_fp64_dense"] = dense_projection(g, a.omega, local, rho, a.dt, steps_conv, peaks, peak_src)
 
     # the exact FP64 sparse form on the same problem, one solve
     if not a.no_fp64_sparse and (prec != qpr.QPR_FP64 or s.backend != qpr.QPR_BACKEND_SPARSE):
-        sf = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=qpr.QPR_BACKEND_SPARSE, device=local)
-        rho.copy_(rho0)
-        sf.steady_state(rho, a.dt, a.tol, a.max_steps)
-        rho.copy_(rho0)
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stf = sf.steady_state(rho, a.dt, a.tol, a.max_steps)
-        e1.record()
-        e1.synchronize()
-        # error of this form's steady state against the exact FP64 form (itself held to the oracle by the
-        # tests): the precision form's stated bounds are max|dp| <= 1e-7 max p and ||drho||_F <= 1e-6
-        p_ours = torch.diagonal(rho_solved).real
-        p_fp64 = torch.diagonal(rho).real
-        line["fp64_sparse"] = {"time_to_steady_state_s": e0.elapsed_time(e1) / 1e3, "steps": stf["steps"],
-                               "max_dp_rel": float((p_ours - p_fp64).abs().max() / p_fp64.abs().max()),
-                               "fro_drho": float(torch.linalg.norm(rho_solved - rho))}
-        sf.close()
+        line["fp64_sparse"] = fp64_sparse_solve(g, a, local, rho0, rho_solved, flush, warm=True)
 
     # the learned warm start (network trained by train_warmstart, weights in the package): inference plus the
     # solve from rho0 = diag(p_hat), timed like the cold solve
     if not a.no_warm_start and prec == qpr.QPR_MIXED:
-        from paper_2003_04930_gb300 import warmstart
-        net = warmstart.load_network(device=local)
-        if net is not None and a.omega >= warmstart.WARM_OMEGA_MIN:
-            def warm_solve():
-                p_hat = net.predict(g, a.omega)
-                rho.copy_(torch.from_numpy(warmstart.warm_rho(p_hat)))
-                return s.steady_state(rho, a.dt, a.tol, a.max_steps)
-            warm_solve()
-            wt, wst = [], None
-            for _ in range(max(1, a.steps)):
-                flush.fill_(1.0)
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-                wst = warm_solve()
-                torch.cuda.synchronize()
-                wt.append(time.perf_counter() - t)
-            line["warm_start"] = {"value": statistics.mean(wt), "unit": "s", "steps": wst["steps"],
-                                  "cold_steps": steps_conv, "cold_value": value,
-                                  "timed": "GNN inference (qpr_gnn_predict) + rho0 = diag(p_hat) upload + solve",
-                                  "network": "4-layer message passing, width 64, BF16 weights, trained on 256 "
-                                             "solver-generated steady states (N in [64, 1024])"}
-            net.close()
+        ws = warm_solve(s, g, a.omega, a, local, rho, flush, max(1, a.steps))
+        if ws is not None:
+            ws.update(cold_steps=steps_conv, cold_value=value)
+            line["warm_start"] = ws
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     host = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)
@@ -490,15 +375,259 @@ def run_ours(a):
         e2e.append(time.perf_counter() - t)
     line["e2e"] = {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 16 * n * n,
                    "d2h_bytes_per_step": 16 * n * n}
+    s.close()
+
+    # the other size the metric names, and the batched form
+    if not a.no_large and rank == 0:
+        line["n4096"] = large_case(a, local, peaks, peak_src, flush)
+    if not a.no_batch and rank == 0:
+        line["batch512"] = batch_case(a, local)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, steps_conv, a.cpu_sample_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def form_name(s, prec):
+    from paper_2003_04930_gb300 import qpr
+    form = {(qpr.QPR_FP64, 1): "fp64 dense DMMA", (qpr.QPR_FP64, 2): "fp64 sparse CSR",
+            (qpr.QPR_MIXED, 1): "mixed: split-BF16 tcgen05 GEMM deltas (FP32 accumulate) + fp64 "
+                                "reference/accumulation/residual",
+            (qpr.QPR_MIXED, 2): "mixed: fp32 sparse CSR deltas (tile pairs) + float-float delta "
+                                "accumulation + fp64 reference/residual"}[(prec, s.backend)]
+    if s.sparse_form in (qpr.QPR_SPARSE_FORM_COLUMNS, qpr.QPR_SPARSE_FORM_COLUMNS_PERSISTENT):
+        form = ("mixed: fp32 column-block SpMM from TMA-staged shared memory + tile-pair epilogue, "
+                "float-float delta accumulation, fp64 reference/residual")
+    elif s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER:
+        form = ("mixed: fp32 column-block SpMM gathering row segments through L1/L2 + tile-pair epilogue, "
+                "float-float delta accumulation, fp64 reference/residual")
+    return form
+
+
+# DRAM bytes per launch of the current kernels from one ncu capture each
+# (`dram__bytes_read.sum + dram__bytes_write.sum`, the commands in profiles/),
+# keyed by (kernel, N); a kernel changed since its capture has no entry.
+NCU_TRAFFIC = {}
+
+
+def roofline(s, g, n, prof, peaks, peak_src, prec):
+    """Roofline of the dominant kernel of the form in use, from the kernel's
+    own duration (qpr_profile_step: each kernel alone between CUDA events)."""
+    from paper_2003_04930_gb300 import qpr
+    hbm = peaks["hbm_gbs"]
+
+    def hbm_entry(kernel, alg, ms, extra=None):
+        ach = alg / (ms * 1e-3) / 1e9
+        d = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+             "traffic": NCU_TRAFFIC.get((kernel, n)), "kernel": kernel, "alg_bytes_per_launch": alg,
+             "launch_ms": ms, "peak_source": f"hbm_gbs of {peak_src}",
+             "launch_ms_source": "qpr_profile_step: the kernel alone on the stream between two CUDA events"}
+        if extra:
+            d.update(extra)
+        return d
+
+    if s.backend == qpr.QPR_BACKEND_DENSE and prec == qpr.QPR_MIXED:
+        # split-BF16 GEMM: 6 BF16 products of H (np x np) with [Re | Im] delta (np x 2 np), on the padded np
+        npad = ((n + 127) // 128) * 128
+        flops = 6 * 2.0 * npad * (2 * npad) * npad
+        ach = flops / (prof["product_ms"] * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "stage_mixed_tc_kernel (tcgen05)",
+                "alg_flops_per_launch": flops, "launch_ms": prof["product_ms"],
+                "peak_source": f"bf16_tflops of {peak_src}"}
+    if s.backend == qpr.QPR_BACKEND_SPARSE and prec == qpr.QPR_MIXED and s.sparse_form != qpr.QPR_SPARSE_FORM_TILES:
+        gather = s.sparse_form == qpr.QPR_SPARSE_FORM_COLUMNS_GATHER
+        npad = ((n + 31) // 32) * 32
+        nnz = h_nonzeros(g)
+        # SpMM: one read of the stage input and one write of X (two FP32 planes each, 8 np^2 bytes), and the
+        # CSR entries of H once (8 bytes per nonzero, column index and FP32 value)
+        alg = 16 * npad * npad + 8 * nnz
+        kernel = "cols_gather_kernel" if gather else "cols_spmm_kernel"
+        # epilogue (nested RK4 form): FP32 plane pairs (8 bytes per element) read or written per stage:
+        # stage 1 X, D, F32, the next input (32); stages 2-3 X, the input, F32, D, the next input (40);
+        # stage 4 X, the input, D, Dlo, Ghi, Glo, D and Dlo written (64): mean (32 + 40 + 40 + 64) / 4 = 44
+        epi_alg = 44 * n * n
+        rows_read = nnz * npad * 8  # each nonzero's row of the stage input, per column block (L1/L2 or smem)
+        extra = {"gathered_bytes_per_launch": rows_read,
+                 "gathered_gbs": rows_read / (prof["product_ms"] * 1e-3) / 1e9,
+                 "flops_per_launch": 4.0 * nnz * npad,
+                 "epilogue": hbm_entry("cols_epi_kernel", epi_alg, prof["epilogue_ms"]),
+                 "gain": {"kernel": "cols_gain_kernel", "launch_ms": prof["gain_ms"]},
+                 "note": "alg bytes are the DRAM floor (stage input and X once, the CSR entries once); at "
+                         "N <= 1400 the state is L2-resident, so a fraction of the HBM peak is a lower bound "
+                         "on what the kernel moves through the memory system"}
+        return hbm_entry(kernel, alg, prof["product_ms"], extra)
+    if s.backend == qpr.QPR_BACKEND_SPARSE:
+        if prec == qpr.QPR_MIXED:
+            alg, kname = 52 * n * n, "stage_mixed_sparse_kernel"
+        else:
+            alg, kname = 4 * 16 * n * n, "stage_sparse_kernel"
+        return hbm_entry(kname, alg, prof["product_ms"])
+    flops = 4.0 * n ** 3
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+    ach = flops / (prof["product_ms"] * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": ach / fp64_peak, "traffic": None, "kernel": "stage_fp64_kernel (DMMA)",
+            "alg_flops_per_launch": flops, "launch_ms": prof["product_ms"],
+            "peak_source": f"bf16_tflops of {peak_src} x nominal FP64/BF16 ratio 1.25/2250"}
+
+
+def dense_projection(g, omega, local, rho, dt, steps_conv, peaks, peak_src, prof_steps=3):
+    """The plain dense FP64 (DMMA) form on the same problem: its step time
+    from qpr_profile_step times the step count of the solve (projected)."""
+    from paper_2003_04930_gb300 import Solver, qpr
+    sd = Solver.from_edges(g, alpha=0.85, omega=omega, backend=qpr.QPR_BACKEND_DENSE, device=local)
+    pd = sd.profile_step(rho, dt, prof_steps)
+    sd.close()
+    flops = 4.0 * g.n ** 3
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+    return {"ms_per_rk4_step": pd["step_ms"], "projected_time_to_steady_state_s": pd["step_ms"] * 1e-3 * steps_conv,
+            "projected": True, "stage_tflops": flops / (pd["product_ms"] * 1e-3) / 1e12,
+            "frac_of_fp64_peak": flops / (pd["product_ms"] * 1e-3) / 1e12 / fp64_peak,
+            "fp64_peak_tflops": fp64_peak, "peak_source": f"bf16_tflops of {peak_src} x 1.25/2250"}
+
+
+def timed_solve(s, rho, rho0, a, flush):
+    import torch
+    rho.copy_(rho0)
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = s.steady_state(rho, a.dt, a.tol, a.max_steps)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, st
+
+
+def fp64_sparse_solve(g, a, local, rho0, rho_solved, flush, warm):
+    """One solve of the exact FP64 sparse form (after one untimed solve when
+    `warm`), and the error of `rho_solved` against it: the precision form's
+    stated bounds are max|dp| <= 1e-7 max p and ||drho||_F <= 1e-6."""
+    import torch
+    from paper_2003_04930_gb300 import Solver, qpr
+    sf = Solver.from_edges(g, alpha=0.85, omega=a.omega, backend=qpr.QPR_BACKEND_SPARSE, device=local)
+    rho = torch.empty_like(rho0)
+    if warm:
+        rho.copy_(rho0)
+        sf.steady_state(rho, a.dt, a.tol, a.max_steps)
+    t, stf = timed_solve(sf, rho, rho0, a, flush)
+    sf.close()
+    p_ours = torch.diagonal(rho_solved).real
+    p_fp64 = torch.diagonal(rho).real
+    return {"time_to_steady_state_s": t, "steps": stf["steps"],
+            "max_dp_rel": float((p_ours - p_fp64).abs().max() / p_fp64.abs().max()),
+            "fro_drho": float(torch.linalg.norm(rho_solved - rho))}
+
+
+def warm_solve(s, g, omega, a, local, rho, flush, reps):
+    """GNN inference (qpr_gnn_predict) + rho0 = diag(p_hat) upload + solve,
+    wall-clocked `reps` times after one untimed run; None when the network is
+    absent or omega is below the warm-start threshold."""
+    import torch
+    from paper_2003_04930_gb300 import warmstart
+    net = warmstart.load_network(device=local)
+    if net is None or omega < warmstart.WARM_OMEGA_MIN:
+        return None
+
+    def once():
+        p_hat = net.predict(g, omega)
+        rho.copy_(torch.from_numpy(warmstart.warm_rho(p_hat)))
+        return s.steady_state(rho, a.dt, a.tol, a.max_steps)
+    once()
+    wt, wst = [], None
+    for _ in range(reps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        wst = once()
+        torch.cuda.synchronize()
+        wt.append(time.perf_counter() - t)
+    net.close()
+    return {"value": statistics.mean(wt), "unit": "s", "steps": wst["steps"],
+            "timed": "GNN inference (qpr_gnn_predict) + rho0 = diag(p_hat) upload + solve",
+            "network": "4-layer message passing, width 64, BF16 weights, trained on 256 solver-generated "
+                       "steady states (N in [64, 1024])"}
+
+
+def large_case(a, local, peaks, peak_src, flush):
+    """The metric's second size: the same generator at N = 4096 (seed 3),
+    omega = 0.8. Mixed cold and warm-started solves (one timed each after one
+    untimed), one FP64 sparse solve (the exact form, also the reference of
+    the error), the plain dense FP64 DMMA form projected from one profiled
+    step, and the roofline of the gather SpMM and the epilogue."""
+    import torch
+    from paper_2003_04930_gb300 import Solver, graphs, qpr
+    n = a.large_n
+    la = argparse.Namespace(**vars(a))
+    la.n, la.seed = n, a.large_seed
+    g = graphs.heavy_tailed(n, la.seed)
+    dev = torch.device("cuda", local)
+    s = Solver.from_edges(g, alpha=0.85, omega=la.omega, precision=qpr.QPR_MIXED, device=local,
+                          ref_refresh=la.ref_refresh)
+    rho0 = torch.from_numpy(graphs.maximally_mixed(n)).to(dev)
+    rho = torch.empty_like(rho0)
+    rho.copy_(rho0)
+    s.steady_state(rho, la.dt, la.tol, la.max_steps)
+    t_cold, st = timed_solve(s, rho, rho0, la, flush)
+    rho_solved = rho.clone()
+    out = {"workload": f"heavy-tailed PA digraph N={n} seed={la.seed}, alpha=0.85, omega={la.omega}, rho0=I/N, "
+                       f"RK4 dt={la.dt}, until ||L(rho)||_F<{la.tol}",
+           "form": form_name(s, qpr.QPR_MIXED), "sparse_plan": s.sparse_plan,
+           "cold": {"time_to_steady_state_s": t_cold, "steps": st["steps"], "residual": st["residual"],
+                    "gpu_launches": st["kernel_launches"]}}
+    prof = s.profile_step(rho_solved, la.dt, 4)
+    out["profile_ms"] = prof
+    out["roofline"] = roofline(s, g, n, prof, peaks, peak_src, qpr.QPR_MIXED)
+    ws = warm_solve(s, g, la.omega, la, local, rho, flush, 1)
+    if ws is not None:
+        out["warm_start"] = ws
+    s.close()
+    out["fp64_sparse"] = fp64_sparse_solve(g, la, local, rho0, rho_solved, flush, warm=False)
+    out["plain_fp64_dense"] = dense_projection(g, la.omega, local, rho_solved, la.dt, st["steps"], peaks, peak_src,
+                                               prof_steps=1)
+    best = min(t_cold, ws["value"]) if ws is not None else t_cold
+    out["speedup_vs_fp64_sparse"] = out["fp64_sparse"]["time_to_steady_state_s"] / best
+    out["speedup_vs_plain_fp64_dense_projected"] = out["plain_fp64_dense"]["projected_time_to_steady_state_s"] / best
+    return out
+
+
+def batch_case(a, local):
+    """The batched form: one qpr_batch_steady_state call over 512 graphs
+    (N ~ U[32,1024], omega ~ U[0.1,0.95], seeds 1000+g), timed once (the
+    call assembles, uploads and plans every problem itself, so there is no
+    state for a warm-up call to leave behind)."""
+    import numpy as np
+    import torch
+    from paper_2003_04930_gb300 import graphs, qpr
+    specs = graphs.batch_specs(a.batch_count)
+    gs = [graphs.heavy_tailed(n, seed) for n, om, seed in specs]
+    dev = torch.device("cuda", local)
+    rho0 = [torch.from_numpy(graphs.maximally_mixed(g.n)).to(dev) for g in gs]
+    rho = [r.clone() for r in rho0]
+    probs = [(g, om, r) for g, (n, om, seed), r in zip(gs, specs, rho)]
+
+    def solve():
+        for r, r0 in zip(rho, rho0):
+            r.copy_(r0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, stats = qpr.batch_steady_state(probs, dt=a.dt, tol=a.tol, max_steps=a.max_steps,
+                                           ref_refresh=a.ref_refresh, device=local)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, stats
+    t, stats = solve()
+    steps = [x["steps"] for x in stats]
+    return {"workload": f"{a.batch_count} heavy-tailed graphs, N ~ U[32,1024], omega ~ U[0.1,0.95], alpha=0.85, "
+                        f"rho0=I/N, RK4 dt={a.dt}, each to ||L(rho)||_F<{a.tol}",
+            "time_to_steady_state_s": t, "timed": "the whole qpr_batch_steady_state call (host assembly, "
+            "upload, solve, download), wall clock", "sum_n2": int(sum(g.n ** 2 for g in gs)),
+            "rk4_steps_max": max(steps), "rk4_steps_mean": float(np.mean(steps)),
+            "converged": int(sum(x["converged"] for x in stats)), "gpu_launches": int(stats[0]["kernel_launches"])}
 
 
 def run_batch(a):

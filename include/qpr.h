@@ -58,7 +58,7 @@ typedef enum {
     QPR_E_OOM = 4,           /* device or host allocation failed */
     QPR_E_UNSTABLE = 5,      /* dt outside the RK4 stability estimate (qpr_evolve only) */
     QPR_E_NOT_CONVERGED = 6, /* max_steps reached before the residual fell below tol */
-    QPR_E_TIMEOUT = 7,       /* a device-side wait gave up */
+    QPR_E_TIMEOUT = 7,       /* a device-side wait gave up (the context is not poisoned) */
     QPR_E_NONFINITE = 8      /* a NaN or Inf appeared in the state or the residual */
 } qpr_status;
 
@@ -100,11 +100,6 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
  *   cooperative launch support).
  * TILES: one launch per stage; each 32 x 32 tile pair gathers, from L2, the
  *   row slices of the delta that its rows' nonzeros select.
- * COLUMNS_CHUNKED: the column-block product for any N: a cluster of CTAs
- *   (one per row split) streams the column block in chunks of chunk_rows
- *   staged rows, each chunk loaded once and multicast to the cluster, and
- *   keeps its rows' sums in shared memory; the same epilogue. Needs thread
- *   block clusters.
  * COLUMNS_GATHER: the column-block product for any N without staging the
  *   block: each CTA (row split r, block J of 32 columns) stages only its CSR
  *   entries and reads every nonzero's 32 values of block J through L1 and
@@ -112,14 +107,13 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
  *   side, so the block is read from DRAM about once.
  * AUTO (default): COLUMNS where it applies, else COLUMNS_GATHER, else TILES.
  * COLUMNS and COLUMNS_PERSISTENT give bitwise the same results (each row's
- * products summed in entry order); COLUMNS_GATHER, COLUMNS_CHUNKED (per row:
- * chunk by chunk) and TILES differ from them only in FP32 summation order. */
+ * products summed in entry order); COLUMNS_GATHER and TILES differ from them
+ * only in FP32 summation order. (Value 4 is not used.) */
 enum {
     QPR_SPARSE_FORM_AUTO = 0,
     QPR_SPARSE_FORM_COLUMNS = 1,
     QPR_SPARSE_FORM_TILES = 2,
     QPR_SPARSE_FORM_COLUMNS_PERSISTENT = 3,
-    QPR_SPARSE_FORM_COLUMNS_CHUNKED = 4,
     QPR_SPARSE_FORM_COLUMNS_GATHER = 5
 };
 
@@ -133,8 +127,10 @@ typedef struct {
     int32_t backend;     /* QPR_BACKEND_AUTO (default), QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE */
     int32_t ref_refresh; /* QPR_MIXED: steps between exact FP64 reference refreshes (default 32) */
     int32_t sparse_form; /* QPR_MIXED, sparse backend: QPR_SPARSE_FORM_* (default AUTO) */
-    int32_t chunk_rows;  /* COLUMNS_CHUNKED: staged rows per chunk, a positive multiple of 32
-                            (default 0: chosen by the plan) */
+    int32_t test_fault;  /* testing only (default 0). 1: every grid barrier of the COLUMNS_PERSISTENT
+                            form waits for one arrival more than its grid makes, so each wait
+                            gives up after its time limit (about a second) and the call returns
+                            QPR_E_TIMEOUT; the context stays usable. Other forms ignore it. */
     int32_t row_splits;  /* COLUMNS, COLUMNS_GATHER: row splits of the product, at least this many
                             (default 0: chosen by the plan; at most 16, 64 for the gather form) */
     int32_t adaptive_refresh; /* QPR_MIXED steady-state solves: 1 (default) lengthens the window between
@@ -185,15 +181,15 @@ QPR_API const char *qpr_status_string(qpr_status s);
  * of H used by the RK4 step-size check. qpr_backend: the backend in use
  * (QPR_BACKEND_DENSE or QPR_BACKEND_SPARSE). qpr_sparse_form: the form of
  * the FP32 sparse stage in use (QPR_SPARSE_FORM_COLUMNS,
- * _COLUMNS_PERSISTENT, _COLUMNS_CHUNKED, _COLUMNS_GATHER or _TILES; 0 when
- * the context is not QPR_MIXED with the sparse backend). */
+ * _COLUMNS_PERSISTENT, _COLUMNS_GATHER or _TILES; 0 when the context is not
+ * QPR_MIXED with the sparse backend). */
 QPR_API int64_t qpr_n(const qpr_ctx *ctx);
 QPR_API int32_t qpr_backend(const qpr_ctx *ctx);
 QPR_API int32_t qpr_sparse_form(const qpr_ctx *ctx);
-/* Geometry of the column-block product in use, into out[4]: row splits
- * (the cluster size of COLUMNS_CHUNKED), staged rows per chunk (0: the whole
- * block or, for COLUMNS_GATHER, none), chunks per column block (1 unless
- * chunked) and the product kernel's dynamic shared memory in bytes. All 0
+/* Geometry of the column-block product in use, into out[4]: row splits,
+ * complex columns per column block (16 for COLUMNS and COLUMNS_PERSISTENT,
+ * 32 for COLUMNS_GATHER), CTAs of one product launch (column blocks x row
+ * splits) and the product kernel's dynamic shared memory in bytes. All 0
  * for the tile-pair form.
  * Errors: QPR_E_ARG (ctx or out NULL). */
 QPR_API qpr_status qpr_sparse_plan(const qpr_ctx *ctx, int32_t *out);
@@ -231,17 +227,27 @@ QPR_API qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps)
 QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int64_t max_steps,
                             qpr_stats *out);
 
-/* Per-kernel timing of the RK4 step on the context's stream. Runs `steps`
- * RK4 steps from rho (rho itself is not modified) without CUDA graphs,
- * bracketing every kernel launch with CUDA events, and writes the mean
- * durations in milliseconds: ms_out[0] one stage kernel (H rho plus the fused
- * epilogue; the epilogue kernel in the column-block form), ms_out[1] one
- * gain kernel (G p; in the two-launch column-block forms the SpMM kernel
- * alone, from the end of the previous launch to an event right after it, the
- * gain running beside it on a forked stream; 0 where the stage kernel
- * computes the gain itself), ms_out[2] one whole step.
- * Meant for roofline measurements; steps >= 1. */
-QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out);
+/* Per-kernel timing of the RK4 step, for roofline measurements (the paper
+ * has no counterpart). Runs `steps` RK4 steps (steps >= 1) from rho (rho
+ * itself is not modified) on the context's stream without CUDA graphs,
+ * without programmatic dependent launch and without the forked gain branch:
+ * every kernel runs alone, between two CUDA events, so each time below is
+ * one kernel's own duration (plus the event granularity, about a
+ * microsecond), not the overlapped time of the solve's graph launches.
+ * Means over all launches of the kind, in milliseconds. */
+typedef struct {
+    double product_ms;   /* the H rho product: the column-block SpMM (COLUMNS, COLUMNS_PERSISTENT) or
+                            gather SpMM (COLUMNS_GATHER); the fused stage kernel of the other forms
+                            (product and epilogue in one launch) */
+    double epilogue_ms;  /* the epilogue kernel of the two-kernel column-block forms; 0 otherwise */
+    double gain_ms;      /* the gain kernel G p (0 where the stage kernel forms the gain itself) */
+    double refresh_ms;   /* QPR_MIXED: one exact FP64 reference refresh, all its kernels; 0 otherwise */
+    double step_ms;      /* the kernels of one RK4 step run one at a time (the sum of the above) */
+    int32_t launches_per_step;
+    int32_t reserved[3];
+} qpr_profile;
+
+QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, qpr_profile *out);
 
 /* p[i] = Re rho_ii (the probability at node i); p: N doubles, host or
  * device. rank (nullable): N int64 node indices in descending order of p,

@@ -35,9 +35,10 @@ using mixed::TS;
 constexpr int kCW = 16;            // complex columns per block
 constexpr int kCWWide = 32;        // complex columns per block of the gather form (one 128-byte line per plane)
 constexpr int kRowFloats = 2 * kCW; // staged row: kCW real, then kCW imaginary values (128 bytes)
+static_assert(kCW == kColWidth && kCWWide == kColGatherWidth, "host and device block widths agree");
 constexpr int kBoxRows = 32;       // rows of one TMA box
 constexpr int kANT = 512;          // threads of the SpMM kernel
-constexpr int kAWarps = kANT / 32;   // (32 warps measured slower, for both the whole-block and chunked kernels)
+constexpr int kAWarps = kANT / 32;   // (32 warps measured slower)
 // Gather form (measured sweeps: 2 CTAs per SM with 8 rounds of loads in
 // flight beat 3 CTAs per SM with 4 or fewer by 10-30%)
 constexpr int kGatherCtasPerSm = 2;   // resident CTAs per SM the gather form's plan sizes for
@@ -48,8 +49,8 @@ constexpr int kLongRow = 48;       // longer rows: one bundle, nonzeros dealt to
 constexpr int kENT = 512;          // threads of the epilogue (2 elements of a tile pair each; 256 measured slower)
 constexpr int kPieceLong = 1;      // bundle flags: long-row bundle
 constexpr int kPiecePart = 2;      // bundle flags: one part of a cut row (its sum goes to a partial slot)
-// For np above kColMaxNp (the gather and chunked forms, many row splits; the
-// gather form only when its grid has fewer than kCutMaxWaves waves), rows
+// For np above kColMaxNp (the gather form, many row splits, when its grid
+// has fewer than kCutMaxWaves waves), rows
 // longer than kPartMax nonzeros are cut into parts of at most kPartMax,
 // each a long-row bundle of its own (possibly on another warp) whose sum goes
 // to a partial slot in shared memory; after all warps, the parts of a row are
@@ -82,20 +83,17 @@ __device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g 
 // kRPG interleaved sums added in slot order, then over the groups by
 // xor-shuffle), so the result does not depend on timing.
 //
-// ACC (the chunked form): instead of storing X, add each row's sums to its
-// accumulator acc[(row - row0) kRowFloats + 4 p .. + 3] in shared memory.
 // GMEM (the gather form): sD is the stage input in global memory (two np x
 // np planes); row q's 16 values of block J are read there with L1-cached
 // loads (hub rows, referenced by many rows of a split, hit L1). The input
 // was written by the previous kernel; every load is issued after
 // griddepcontrol.wait, which makes that kernel's writes visible, and no
 // kernel reads the stage inputs through L1 before it.
-template <bool ACC = false, bool GMEM = false, bool WIDE = false>
+template <bool GMEM = false, bool WIDE = false>
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
-                                             float *__restrict__ X, float *acc_rows = nullptr, int row0 = 0,
-                                             float *parts = nullptr) {
-    static_assert(!WIDE || (GMEM && !ACC), "the wide layout is the gather form's");
+                                             float *__restrict__ X, float *parts) {
+    static_assert(!WIDE || GMEM, "the wide layout is the gather form's");
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
     const size_t plane = (size_t)np * np;
     // narrow: group g = one row, lanes 0-3 real and 4-7 imaginary values of
@@ -110,14 +108,7 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
         return *reinterpret_cast<const float4 *>(sDp + q * kRowFloats);
     };
     float *__restrict__ Xp = X + pl * plane + col;
-    auto put = [&](int row, float4 v) {
-        if (ACC) {
-            float4 *a = reinterpret_cast<float4 *>(acc_rows + (row - row0) * kRowFloats + 4 * p);
-            *a = f4add(*a, v);
-        } else {
-            *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = v;
-        }
-    };
+    auto put = [&](int row, float4 v) { *reinterpret_cast<float4 *>(Xp + (size_t)row * np) = v; };
     // int4 entries per round: kRPG / 2 per group (narrow) or group pair (wide)
     constexpr int RS = (WIDE ? 2 : 4) * (kRPG / 2);
     constexpr int RowF = WIDE ? 2 * kRowFloats : kRowFloats;  // floats of a partial row
@@ -207,13 +198,11 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
 }
 
 // The rows cut into parts, cuts[0 .. ncut) = {row, first slot, parts, 0}:
-// X[row, J] = the sum of the parts' partial rows in slot order (ACC: added
-// to the row's accumulator). Called by all threads after every warp's
-// bundles (and a barrier).
-template <bool ACC = false, bool WIDE = false>
+// X[row, J] = the sum of the parts' partial rows in slot order. Called by all
+// threads after every warp's bundles (and a barrier).
+template <bool WIDE = false>
 __device__ __forceinline__ void combine_cuts(const int4 *__restrict__ cuts, int ncut, const float *parts, int J,
-                                             int np, float *__restrict__ X, float *acc_rows = nullptr,
-                                             int row0 = 0) {
+                                             int np, float *__restrict__ X) {
     const size_t plane = (size_t)np * np;
     constexpr int Q = WIDE ? 2 * kRowFloats / 4 : kRowFloats / 4;  // float4 per partial row
     for (int e = threadIdx.x; e < ncut * Q; e += blockDim.x) {
@@ -222,10 +211,7 @@ __device__ __forceinline__ void combine_cuts(const int4 *__restrict__ cuts, int 
         float4 s = *reinterpret_cast<const float4 *>(parts + c.y * 4 * Q + 4 * p);
         for (int k = 1; k < c.z; ++k)
             s = f4add(s, *reinterpret_cast<const float4 *>(parts + (c.y + k) * 4 * Q + 4 * p));
-        if (ACC) {
-            float4 *a = reinterpret_cast<float4 *>(acc_rows + (c.x - row0) * kRowFloats + 4 * p);
-            *a = f4add(*a, s);
-        } else if (WIDE) {
+        if (WIDE) {
             *reinterpret_cast<float4 *>(X + (p / 8) * plane + (size_t)c.x * np + J * kCWWide + 4 * (p % 8)) = s;
         } else {
             *reinterpret_cast<float4 *>(X + (p < 4 ? 0 : plane) + (size_t)c.x * np + J * kCW + 4 * (p & 3)) = s;

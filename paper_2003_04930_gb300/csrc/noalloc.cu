@@ -117,6 +117,10 @@ extern "C" qpr_status qpr_rhs_noalloc(int64_t n, const int32_t *h_ptr, const int
         return QPR_E_ARG;
     if (!(alpha >= 0.0 && alpha <= 1.0) || !(omega >= 0.0 && omega <= 1.0)) return QPR_E_ARG;
     if (dangling_mode != QPR_DANGLING_F && dangling_mode != QPR_DANGLING_UNIFORM) return QPR_E_ARG;
+    // an error left on this thread by earlier work is not ours to clear: report
+    // it before queuing anything, so the check after the launches below sees
+    // only this call's own launch errors
+    if (cudaPeekAtLastError() != cudaSuccess) return QPR_E_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -304,6 +304,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     h->dt = dt;
     h->scale = 1.0;
     h->resid_exact_step = -1;
+    h->gb_extra = (ctx->persist_grid > 0 && ctx->opt.test_fault) ? 1u : 0u;
     QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
     qpr_status st = ensure_mixed_graph(ctx);
     if (st != QPR_OK) return st;
@@ -329,7 +330,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         since = (refresh ? 0 : since) + block;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
-        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait gave up (err_timeout set by a stage kernel)");
         if (!h->done) {
             refresh = true;
             if (adaptive) {
@@ -352,7 +353,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
         ctx->launches += qpr::kMixedLaunchesPerRefresh;
         st = read_ctl(ctx);
         if (st != QPR_OK) return st;
-        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait of the tensor-core stage gave up");
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait gave up (err_timeout set by a stage kernel)");
         if (h->done) return QPR_OK;  // converged, max steps or non-finite, decided exactly
         if (prev == qpr::kCtlMaxSteps) return QPR_OK;
         // the estimate passed but the exact residual did not: keep stepping
@@ -577,7 +578,6 @@ int32_t qpr_backend(const qpr_ctx *ctx) { return ctx ? ctx->backend : 0; }
 int32_t qpr_sparse_form(const qpr_ctx *ctx) {
     if (!ctx || ctx->opt.precision != QPR_MIXED || ctx->mw.splitD) return 0;
     if (!ctx->mw.cmaps) return QPR_SPARSE_FORM_TILES;
-    if (ctx->ops.col_cs > 0) return QPR_SPARSE_FORM_COLUMNS_CHUNKED;
     if (ctx->ops.col_gather) return QPR_SPARSE_FORM_COLUMNS_GATHER;
     return ctx->persist_grid > 0 ? QPR_SPARSE_FORM_COLUMNS_PERSISTENT : QPR_SPARSE_FORM_COLUMNS;
 }
@@ -587,8 +587,8 @@ qpr_status qpr_sparse_plan(const qpr_ctx *ctx, int32_t *out) {
     if (!ctx->mw.cmaps) return QPR_OK;
     const qpr::DevOps &o = ctx->ops;
     out[0] = o.col_splits;
-    out[1] = o.col_cs > 0 ? o.col_kc : 0;
-    out[2] = o.col_cs > 0 ? o.col_nc : 1;
+    out[1] = o.col_gather ? qpr::kColGatherWidth : qpr::kColWidth;
+    out[2] = (o.np / out[1]) * o.col_splits;
     out[3] = o.col_smem;
     return QPR_OK;
 }
@@ -678,10 +678,9 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return arg_err(QPR_E_ARG, "unknown dangling mode");
     if (o.graph_steps < 0 || o.graph_steps > 4096) return arg_err(QPR_E_ARG, "graph_steps outside [0, 4096]");
     if (o.backend < QPR_BACKEND_AUTO || o.backend > QPR_BACKEND_SPARSE) return arg_err(QPR_E_ARG, "unknown backend");
-    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_COLUMNS_GATHER)
+    if (o.sparse_form < QPR_SPARSE_FORM_AUTO || o.sparse_form > QPR_SPARSE_FORM_COLUMNS_GATHER || o.sparse_form == 4)
         return arg_err(QPR_E_ARG, "unknown sparse_form");
-    if (o.chunk_rows < 0 || o.chunk_rows % 32 != 0 || o.chunk_rows > 4096)
-        return arg_err(QPR_E_ARG, "chunk_rows must be 0 or a multiple of 32 up to 4096");
+    if (o.test_fault != 0 && o.test_fault != 1) return arg_err(QPR_E_ARG, "test_fault must be 0 or 1");
     if (o.row_splits < 0 || o.row_splits > 64) return arg_err(QPR_E_ARG, "row_splits outside [0, 64]");
     HostOps hops;
     {
@@ -850,44 +849,35 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         CREATE_CUDA(cudaMalloc(&ctx->d_sval32, sv32.size() * sizeof(float)));
         CREATE_CUDA(cudaMemcpy(ctx->d_sval32, sv32.data(), sv32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
-    // column-block form: the whole column block staged (cplan) or, for larger
-    // N, streamed in chunks by clusters (kplan)
+    // column-block form: the whole column block staged in shared memory, or
+    // (larger N) the gather form reading row segments through L1/L2
     qpr::ColPlan cplan;
-    qpr::ChunkPlan kplan;
     const int form = o.sparse_form;
     const bool want_cols = (o.precision == QPR_MIXED) && !tc && form != QPR_SPARSE_FORM_TILES;
-    bool cols = want_cols && form != QPR_SPARSE_FORM_COLUMNS_CHUNKED && form != QPR_SPARSE_FORM_COLUMNS_GATHER &&
+    bool cols = want_cols && form != QPR_SPARSE_FORM_COLUMNS_GATHER &&
                 qpr::plan_columns(hops, np, ctx->device, cplan, o.row_splits);
     const bool gathered = want_cols && !cols && (form == QPR_SPARSE_FORM_AUTO || form == QPR_SPARSE_FORM_COLUMNS_GATHER) &&
                           qpr::plan_columns(hops, np, ctx->device, cplan, o.row_splits, true);
-    const bool chunked = want_cols && !cols && !gathered && form == QPR_SPARSE_FORM_COLUMNS_CHUNKED &&
-                         qpr::plan_chunks(hops, np, ctx->device, kplan, o.chunk_rows);
-    cols = cols || gathered || chunked;
+    cols = cols || gathered;
     if (o.precision == QPR_MIXED && !tc && !cols && form != QPR_SPARSE_FORM_AUTO && form != QPR_SPARSE_FORM_TILES) {
-        ctx->err = form == QPR_SPARSE_FORM_COLUMNS_CHUNKED ? "sparse_form COLUMNS_CHUNKED: no cluster plan fits this device"
-                   : form == QPR_SPARSE_FORM_COLUMNS_GATHER
+        ctx->err = form == QPR_SPARSE_FORM_COLUMNS_GATHER
                        ? "sparse_form COLUMNS_GATHER: no row split fits one CTA's shared memory"
                        : "sparse_form COLUMNS: the staged operands of N = " + std::to_string(n) +
                              " do not fit one CTA's shared memory";
         return bail(QPR_E_ARG);
     }
     if (cols) {
-        if (chunked) {
-            CREATE_CUDA(qpr::set_chunk_attrs(kplan.smem, kplan.cs));
-        } else if (gathered) {
+        if (gathered) {
             CREATE_CUDA(qpr::set_gather_smem(cplan.smem));
         } else {
             CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
         }
-        const std::vector<int2> &kh = chunked ? kplan.kh : cplan.kh;
+        const std::vector<int2> &kh = cplan.kh;
         // the bundle descriptors, then the cut rows
-        std::vector<int4> pieces(chunked ? kplan.pieces : cplan.pieces);
-        const std::vector<int4> &cuts = chunked ? kplan.cuts : cplan.cuts;
-        pieces.insert(pieces.end(), cuts.begin(), cuts.end());
+        std::vector<int4> pieces(cplan.pieces);
+        pieces.insert(pieces.end(), cplan.cuts.begin(), cplan.cuts.end());
         std::vector<int> ints;
-        for (const std::vector<int> *v : {chunked ? &kplan.q : &cplan.q, chunked ? &kplan.sb : &cplan.sb,
-                                          chunked ? &kplan.wb : &cplan.wb, chunked ? &kplan.cutb : &cplan.cutb,
-                                          &kplan.rows})
+        for (const std::vector<int> *v : {&cplan.q, &cplan.sb, &cplan.wb, &cplan.cutb})
             ints.insert(ints.end(), v->begin(), v->end());
         CREATE_CUDA(cudaMalloc(&ctx->d_colkh, kh.size() * sizeof(int2)));
         CREATE_CUDA(cudaMemcpy(ctx->d_colkh, kh.data(), kh.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -965,37 +955,22 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         mw.Glo = ctx->d_mix32 + 12 * plane;
         mw.partials32 = ctx->d_partials32;
         if (cols) {
-            const size_t nq = chunked ? kplan.q.size() : cplan.q.size();
-            const size_t nsb = chunked ? kplan.sb.size() : cplan.sb.size();
-            const size_t nwb = chunked ? kplan.wb.size() : cplan.wb.size();
-            const size_t ncb = chunked ? kplan.cutb.size() : cplan.cutb.size();
+            const size_t nq = cplan.q.size();
+            const size_t nsb = cplan.sb.size();
+            const size_t nwb = cplan.wb.size();
             ops.col_kh = ctx->d_colkh;
             ops.col_q = ctx->d_colint;
             ops.col_sb = ctx->d_colint + nq;
             ops.col_wb = ctx->d_colint + nq + nsb;
             ops.col_cutb = ctx->d_colint + nq + nsb + nwb;
             ops.col_pieces = ctx->d_colpieces;
-            ops.col_cut = ctx->d_colpieces + (chunked ? kplan.pieces.size() : cplan.pieces.size());
-            ops.col_part_off = chunked ? kplan.part_off : cplan.part_off;
-            if (chunked) {
-                ops.col_rowb = ctx->d_colint + nq + nsb + nwb + ncb;
-                ops.col_cs = kplan.cs;
-                ops.col_kc = kplan.kc;
-                ops.col_nc = kplan.nc;
-                ops.col_smem = kplan.smem;
-                ops.col_acc_off = kplan.acc_off;
-                ops.col_kh_off = kplan.kh_off;
-                ops.col_kh_slot = kplan.kh_slot;
-                ops.col_p_off = kplan.p_off;
-                ops.col_p_slot = kplan.p_slot;
-                ops.col_splits = kplan.cs;
-            } else {
-                ops.col_gather = gathered ? 1 : 0;
-                ops.col_splits = cplan.splits;
-                ops.col_smem = cplan.smem;
-                ops.col_p_off = cplan.p_off;
-                ops.col_sp_off = cplan.sp_off;
-            }
+            ops.col_cut = ctx->d_colpieces + cplan.pieces.size();
+            ops.col_part_off = cplan.part_off;
+            ops.col_gather = gathered ? 1 : 0;
+            ops.col_splits = cplan.splits;
+            ops.col_smem = cplan.smem;
+            ops.col_p_off = cplan.p_off;
+            ops.col_sp_off = cplan.sp_off;
             ops.col_epi_off = ctx->epi_off;
             ops.col_psmem = ctx->persist_smem;
             mw.X = ctx->d_X;
@@ -1171,12 +1146,12 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
     return QPR_OK;
 }
 
-qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, double *ms_out) {
+qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, qpr_profile *out) {
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     qpr_status st = begin_call(ctx);
     if (st != QPR_OK) return st;
-    if (!rho || !ms_out || steps < 1) return fail(ctx, QPR_E_ARG, "rho/ms_out NULL or steps < 1");
+    if (!rho || !out || steps < 1) return fail(ctx, QPR_E_ARG, "rho/out NULL or steps < 1");
     if (!(dt > 0.0) || dt > qpr_max_stable_dt(ctx)) return fail(ctx, QPR_E_ARG, "dt not positive or unstable");
     st = import_state(ctx, rho);
     if (st != QPR_OK) return st;
@@ -1186,56 +1161,82 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     h->tol = 0.0;
     h->dt = dt;
     h->scale = 1.0;
+    h->resid_exact_step = -1;
     QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
-    std::vector<cudaEvent_t> ev(8 * steps + 1), mk(4 * steps);
-    for (auto &e : ev) QPR_CUDA(ctx, cudaEventCreate(&e));
-    for (auto &e : mk) QPR_CUDA(ctx, cudaEventCreate(&e));
-    const bool cols = ctx->opt.precision == QPR_MIXED && ctx->mw.cmaps && ctx->persist_grid <= 0;
-    int m = 0;
+    const bool mixed = ctx->opt.precision == QPR_MIXED;
+    const bool cols = mixed && ctx->mw.cmaps;
+    // every kernel alone on the stream, between two events: kind 0 product,
+    // 1 epilogue, 2 gain; the refresh's kernels together (kind 3)
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    auto timed = [&](int kind, auto &&launch) -> qpr_status {
+        Mark mk{kind, nullptr, nullptr};
+        QPR_CUDA(ctx, cudaEventCreate(&mk.a));
+        marks.push_back(mk);
+        QPR_CUDA(ctx, cudaEventCreate(&marks.back().b));
+        QPR_CUDA(ctx, cudaEventRecord(marks.back().a, ctx->stream));
+        launch();
+        QPR_CUDA(ctx, cudaEventRecord(marks.back().b, ctx->stream));
+        return QPR_OK;
+    };
+    auto destroy = [&]() {
+        for (Mark &m : marks) {
+            if (m.a) cudaEventDestroy(m.a);
+            if (m.b) cudaEventDestroy(m.b);
+        }
+    };
     const qpr::Work &w = ctx->work;
     const double *yin[5] = {w.y, w.y, w.ya, w.yb, w.ya};
-    const bool mixed = ctx->opt.precision == QPR_MIXED;
-    if (mixed) qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
-    int q = 0;
-    QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
-    for (int64_t k = 0; k < steps; ++k) {
-        for (int s = 1; s <= 4; ++s) {
-            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, cols ? mk[m++] : nullptr);
-            else qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream);
-            QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
-            if (mixed) qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2);
-            else launch_stage(ctx, s);
-            QPR_CUDA(ctx, cudaEventRecord(ev[q++], ctx->stream));
-        }
+    int per_step = 0;
+    if (mixed) {
+        st = timed(3, [&] { qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream); });
+        if (st != QPR_OK) { destroy(); return st; }
     }
-    st = sync_ctx(ctx);
-    double stage_ms = 0.0, gain_ms = 0.0, total_ms = 0.0;
-    if (st == QPR_OK) {
-        for (int i = 0; i + 1 < q; ++i) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-            if (i % 2 == 0) gain_ms += ms;
-            else stage_ms += ms;
-        }
-        float tot = 0.f;
-        cudaEventElapsedTime(&tot, ev[0], ev[q - 1]);
-        total_ms = tot;
-        if (cols) {
-            // the column SpMM alone: from the previous event to the mark after its launch
-            gain_ms = 0.0;
-            for (int i = 0; i < m; ++i) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[2 * i], mk[i]);
-                gain_ms += ms;
+    for (int64_t k = 0; k < steps && st == QPR_OK; ++k) {
+        for (int s = 1; s <= 4 && st == QPR_OK; ++s) {
+            if (cols) {
+                st = timed(2, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 4, true); });
+                if (st == QPR_OK)
+                    st = timed(0, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, true); });
+                if (st == QPR_OK)
+                    st = timed(1, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2, true); });
+                if (k == 0) per_step += 3;
+            } else if (mixed) {
+                if (ctx->mw.splitD) {
+                    st = timed(2, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, true); });
+                    if (k == 0) per_step += 1;
+                }
+                if (st == QPR_OK)
+                    st = timed(0, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2, true); });
+                if (k == 0) per_step += 1;
+            } else {
+                st = timed(2, [&] { qpr::launch_gain(s, ctx->ops, yin[s], w, ctx->stream); });
+                if (st == QPR_OK) st = timed(0, [&] { launch_stage(ctx, s); });
+                if (k == 0) per_step += 2;
             }
         }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
-    for (auto &e : mk) cudaEventDestroy(e);
-    if (st != QPR_OK) return st;
-    ms_out[0] = stage_ms / (4.0 * steps);
-    ms_out[1] = gain_ms / (4.0 * steps);
-    ms_out[2] = total_ms / (double)steps;
+    if (st == QPR_OK) st = sync_ctx(ctx);
+    if (st != QPR_OK) {
+        destroy();
+        return st;
+    }
+    double sum[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (const Mark &m : marks) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, m.a, m.b);
+        sum[m.kind] += ms;
+        cnt[m.kind] += 1;
+    }
+    destroy();
+    memset(out, 0, sizeof(*out));
+    out->product_ms = cnt[0] ? sum[0] / cnt[0] : 0.0;
+    out->epilogue_ms = cnt[1] ? sum[1] / cnt[1] : 0.0;
+    out->gain_ms = cnt[2] ? sum[2] / cnt[2] : 0.0;
+    out->refresh_ms = cnt[3] ? sum[3] / cnt[3] : 0.0;
+    out->step_ms = (sum[0] + sum[1] + sum[2]) / (double)steps;
+    out->launches_per_step = per_step;
     return QPR_OK;
 }
 

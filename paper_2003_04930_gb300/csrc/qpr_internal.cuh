@@ -41,6 +41,9 @@ struct Ctl {
     float dtf, dtl, dt3, pad2_;
     // grid barrier of the persistent column-block kernel: arrivals, generation
     unsigned gb_count, gb_gen;
+    // testing only: arrivals a grid barrier waits for beyond its grid (0, or 1
+    // to make every barrier wait run out; qpr_options.test_fault)
+    unsigned gb_extra, pad3_;
 };
 
 // kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
@@ -87,18 +90,8 @@ struct DevOps {
     int col_smem;          // dynamic shared memory of the SpMM kernel
     int col_p_off;         // byte offset of the staged bundles in it
     int col_sp_off;        // byte offset of the staged diagonal (np floats) in it
-    // chunked column-block form (col_cs > 0): clusters of col_cs CTAs (the row
-    // splits [col_rowb[r], col_rowb[r + 1]) of one column block) share chunks
-    // of col_kc staged rows by multicast; col_nc chunks; per (split, chunk)
-    // block r * col_nc + c the entry range (col_q), bundles (col_sb) and warp
-    // starts (col_wb); shared memory: 2 chunk buffers, the accumulators
-    // (col_acc_off), 2 entry buffers of col_kh_slot bytes (col_kh_off), 2
-    // bundle buffers of col_p_slot bytes (col_p_off)
-    const int *col_rowb;
-    int col_cs, col_kc, col_nc, col_acc_off, col_kh_off, col_kh_slot, col_p_slot;
     int col_gather;        // 1: the gather form (the SpMM reads delta from L2; plan of ColPlan, gather)
-    // rows cut into parts (kPartMax): per split (or per (split, chunk) block)
-    // the cut range [col_cutb[k], col_cutb[k + 1]) of col_cut; the partial
+    // rows cut into parts (kPartMax): per split the cut range [col_cutb[k], col_cutb[k + 1]) of col_cut; the partial
     // slots at byte col_part_off of the SpMM's shared memory
     const int4 *col_cut;
     const int *col_cutb;
@@ -203,12 +196,14 @@ cudaError_t init_stage_sparse();
 // Reference refresh: R = y = y / tr(y), F = f(R) exactly (FP64), D = 0, exact
 // residual and stop decision.
 void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s);
-// One RK4 stage: parts & 1 launches the gain of the stage delta, parts & 2
-// the FP32 sparse stage kernel (3 = both, in that order).
-// mark (column form, optional): an event recorded on s right after the SpMM
-// launch, before the join with the gain branch (profiling).
+// One RK4 stage: parts & 1 launches the gain of the stage delta (the
+// tensor-core form; the tile-pair stage kernel forms the gain itself), parts
+// & 2 the stage kernel (3 = both, in that order). Column-block form: parts &
+// 1 the SpMM with the gain on a forked branch beside it, parts & 2 the
+// epilogue; serial (profiling): no fork and no programmatic dependent
+// launch, and parts & 4 launches the gain on s by itself.
 void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
-                        cudaEvent_t mark = nullptr);
+                        bool serial = false);
 // Opt in to the dynamic shared memory of the sparse mixed stage kernels.
 cudaError_t init_stage_mixed();
 // Dense backend of the mixed form (stage_mixed_tc.cu).
@@ -220,6 +215,9 @@ void launch_mixed_tc(int stage, const DevOps &ops, const MixedWork &w, const TcM
 // column-block SpMM X = H delta from TMA-staged columns, then the tile-pair
 // epilogue. Used where its staged operands fit (np <= kColMaxNp and a plan).
 constexpr int kColMaxNp = 1536;
+// Complex columns per block of the whole-block and of the gather SpMM.
+constexpr int kColWidth = 16;
+constexpr int kColGatherWidth = 32;
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps);
 // Host plan of the column-block SpMM (device copies go to DevOps col_*).
@@ -249,29 +247,8 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
 cudaError_t set_gather_smem(int bytes);
 // Opt in to `bytes` of dynamic shared memory for the SpMM kernels.
 cudaError_t set_cols_smem(int bytes);
-// Host plan of the chunked column-block form (N too large to stage a whole
-// column block): device copies go to DevOps col_* as for ColPlan, plus the
-// split rows and the chunk geometry.
-struct ChunkPlan {
-    int cs = 0, kc = 0, nc = 0;
-    int smem = 0, acc_off = 0, kh_off = 0, kh_slot = 0, p_off = 0, p_slot = 0, part_off = 0;
-    std::vector<int> rows;        // cs + 1
-    std::vector<int2> kh;
-    std::vector<int> q, sb, wb;   // per (split, chunk) block, as in ColPlan
-    std::vector<int4> pieces;
-    std::vector<int4> cuts;       // per block, as in ColPlan
-    std::vector<int> cutb;
-};
-// Plans the chunked form (a cluster size and chunk rows whose shared memory
-// fits and whose clusters can be scheduled); false if none does. Sets the
-// kernel's attributes for the plan it returns.
-// kc > 0: chunks of kc staged rows (a multiple of 32) instead of the plan's choice.
-bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc = 0);
-// Opt in to `bytes` of dynamic shared memory (and clusters of cs > 8 CTAs)
-// for the chunked SpMM kernel.
-cudaError_t set_chunk_attrs(int bytes, int cs);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
-                       cudaEvent_t mark = nullptr);
+                       bool serial = false);
 // Persistent form (stage_persist.cu): one cooperative launch runs up to
 // `steps` RK4 steps of the column-block form, grid barriers between the
 // phases. persist_grid: CTAs of that launch for an np x np problem with the

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
         return;
     }
     float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X, nullptr, 0, parts);
+    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X, parts);
     const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
     if (cb1 > cb0) {
         __syncthreads();
@@ -124,12 +124,11 @@ __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(Dev
         return;
     }
     float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-    warp_bundles<false, true, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, nullptr, 0,
-                                    parts);
+    warp_bundles<true, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, parts);
     const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
     if (cb1 > cb0) {
         __syncthreads();
-        combine_cuts<false, true>(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
+        combine_cuts<true>(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
     }
 }
 
@@ -166,121 +165,6 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     epilogue_pair_in<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
 }
 
-// Chunked form, for N too large to stage a whole column block: a cluster of
-// col_cs CTAs (rank r: the row split [col_rowb[r], col_rowb[r + 1])) works on
-// one column block J = blockIdx.y. The block is streamed in chunks of col_kc
-// staged rows, double-buffered; each chunk is loaded once for the cluster
-// (its 32-row boxes dealt to the ranks round-robin, each box multicast to
-// every rank) and every CTA adds its rows' products with the chunk's
-// columns of H to accumulators in shared memory (per row: chunk by chunk,
-// in entry order within a chunk). A cluster barrier after each chunk frees
-// its buffer for the chunk two ahead. The accumulators go to X at the end.
-//
-// Every wait is bounded; a CTA whose wait gave up reports it and stops
-// computing but still issues its copies, waits for every chunk and takes
-// every cluster barrier, so no peer is left at a barrier or without its
-// boxes, and no copy into the CTA is in flight when it leaves.
-__global__ void __launch_bounds__(kANT, 1) cols_chunk_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
-                                                            MixedWork w) {
-    extern __shared__ uint8_t dyn_raw[];
-    __shared__ __align__(8) uint64_t full[2], csr[2];
-    __shared__ int s_done;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int r = blockIdx.x, J = blockIdx.y;  // cluster (col_cs, 1, 1): the rank is blockIdx.x
-    const int np = ops.np, kc = ops.col_kc, nc = ops.col_nc, cs = ops.col_cs;
-    const uint32_t s0 = tma::smem_u32(dyn_raw);
-    // the same offset in every CTA of the cluster (multicast writes there)
-    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);
-    // buffer b of the chunks, entries and bundles
-    auto buf = [&](int b) { return reinterpret_cast<float *>(base) + (size_t)b * kc * kRowFloats; };
-    auto skh = [&](int b) { return reinterpret_cast<int2 *>(base + ops.col_kh_off + b * ops.col_kh_slot); };
-    auto spc = [&](int b) { return reinterpret_cast<int4 *>(base + ops.col_p_off + b * ops.col_p_slot); };
-    float *acc = reinterpret_cast<float *>(base + ops.col_acc_off);
-    const int row0 = ops.col_rowb[r], nrows = ops.col_rowb[r + 1] - row0;
-    const uint16_t mask = (uint16_t)((1u << cs) - 1u);
-    // block (r, c): this split's entries and bundles for chunk c, into buffer b
-    auto issue_csr = [&](int c, int b) {
-        const int blk = r * nc + c;
-        const int q0 = ops.col_q[2 * blk], q1 = ops.col_q[2 * blk + 1];
-        const int p0 = ops.col_sb[blk], p1 = ops.col_sb[blk + 1];
-        const uint32_t kh_bytes = (uint32_t)((q1 - q0) * 8), p_bytes = (uint32_t)((p1 - p0) * 16 * kBundleInt4);
-        tma::mbar_expect_tx(&csr[b], kh_bytes + p_bytes);
-        if (kh_bytes) tma::load_bulk(skh(b), ops.col_kh + q0, kh_bytes, &csr[b]);
-        if (p_bytes) tma::load_bulk(spc(b), ops.col_pieces + kBundleInt4 * (size_t)p0, p_bytes, &csr[b]);
-    };
-    // chunk c (staged rows [c kc, min(np, (c + 1) kc)), a multiple of 32):
-    // this rank's boxes, multicast; every rank expects the whole chunk
-    auto issue_chunk = [&](int c, int b) {
-        const int c0 = c * kc, rows = min(kc, np - c0);
-        tma::mbar_expect_tx(&full[b], (uint32_t)rows * kRowFloats * 4);
-        for (int m = r; m * kBoxRows < rows; m += cs)
-            tma::load_3d_multicast(buf(b) + (size_t)m * kBoxRows * kRowFloats, &tm, &full[b], J * kCW, 0,
-                                   c0 + m * kBoxRows, mask);
-    };
-    if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
-            tma::mbar_init(&full[b], 1);
-            tma::mbar_init(&csr[b], 1);
-        }
-        tma::mbar_init_fence();
-        issue_csr(0, 0);
-        if (nc > 1) issue_csr(1, 1);
-    }
-    for (int e = tid; e < nrows * (kRowFloats / 4); e += kANT)
-        reinterpret_cast<float4 *>(acc)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    tma::grid_dependency_wait();
-    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) {
-        // uniform over the cluster (set by an earlier kernel); no multicast was issued
-        if (tid == 0) {
-            tma::mbar_wait(&csr[0], 0);
-            if (nc > 1) tma::mbar_wait(&csr[1], 0);
-        }
-        return;
-    }
-    tma::launch_dependents();
-    tma::cluster_sync();  // every rank's barriers are initialised before the first multicast
-    if (tid == 0) {
-        issue_chunk(0, 0);
-        if (nc > 1) issue_chunk(1, 1);
-    }
-    bool bad = false;
-    for (int c = 0; c < nc; ++c) {
-        const int b = c & 1;
-        const uint32_t par = (uint32_t)(c >> 1) & 1u;
-        const bool ok_csr = tma::mbar_wait(&csr[b], par);
-        const bool ok_full = tma::mbar_wait(&full[b], par);
-        if (__syncthreads_or(!(ok_csr && ok_full)) && !bad) {
-            bad = true;
-            if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
-        }
-        if (!bad) {
-            const int blk = r * nc + c;
-            const int *wb = ops.col_wb + blk * kAWarps + warp;
-            float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-            warp_bundles<true>(buf(b), skh(b), spc(b), ops.col_sb[blk], wb[0], wb[1], J, np, w.X, acc, row0, parts);
-            const int cb0 = ops.col_cutb[blk], cb1 = ops.col_cutb[blk + 1];
-            if (cb1 > cb0) {
-                __syncthreads();
-                combine_cuts<true>(ops.col_cut + cb0, cb1 - cb0, parts, J, np, w.X, acc, row0);
-            }
-        }
-        tma::cluster_sync();  // every rank is done with buffer b
-        if (c + 2 < nc && tid == 0) {
-            issue_csr(c + 2, b);
-            issue_chunk(c + 2, b);
-        }
-    }
-    if (bad) return;
-    const size_t plane = (size_t)np * np;
-    for (int e = tid; e < nrows * (kRowFloats / 4); e += kANT) {
-        const int i = e >> 3, p = e & 7;
-        float *dst = w.X + (p < 4 ? 0 : plane) + (size_t)(row0 + i) * np + J * kCW + 4 * (p & 3);
-        *reinterpret_cast<float4 *>(dst) = reinterpret_cast<const float4 *>(acc)[e];
-    }
-}
-
 int max_smem_optin(int device) {
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
@@ -295,7 +179,7 @@ cudaError_t set_spmm_attr(int bytes) {
     return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// The entries of row i (column relative to a chunk start, FP32 value bits).
+// The entries of row i (column relative to c0, FP32 value bits).
 using RowEntries = std::vector<std::vector<int2>>;
 
 // Bundles of one split's rows [r0, r1) with the entries ent[i - r0]: long
@@ -521,113 +405,6 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
     return false;
 }
 
-bool plan_chunks(const HostOps &h, int np, int device, ChunkPlan &plan, int kc_force) {
-    if (np % kBoxRows != 0) return false;
-    int sms = 0, cl = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, device) != cudaSuccess || sms <= 0 || !cl) {
-        cudaGetLastError();
-        return false;
-    }
-    const int smem_max = max_smem_optin(device);
-    const int n = (int)h.n;
-    const int ncb = np / kCW;
-    // each row's entries (column, FP32 value bits) in CSR order
-    RowEntries all(np);
-    for (int i = 0; i < n && i < np; ++i) all[i] = row_entries(h, i, 0, np);
-    std::vector<double> cum(np + 1, 0.0);
-    for (int i = 0; i < np; ++i) cum[i + 1] = cum[i] + (double)all[i].size() + 16.0;
-    // (cluster size, rows per chunk): the portable cluster size and the
-    // largest chunks first
-    std::vector<int2> cands = {{8, 512}, {8, 256}, {16, 512}, {16, 256}, {8, 128}, {16, 128}, {4, 128}};
-    if (kc_force > 0) cands = {{8, kc_force}, {16, kc_force}, {4, kc_force}};
-    for (const int2 cand : cands) {
-        const int cs = cand.x, kc = std::min(cand.y, np);
-        ChunkPlan pl;
-        pl.cs = cs;
-        pl.kc = kc;
-        pl.nc = (np + kc - 1) / kc;
-        // row splits by cost (nonzeros + a per-row overhead)
-        pl.rows.assign(cs + 1, 0);
-        int i = 0;
-        for (int k = 1; k < cs; ++k) {
-            const double target = cum[np] * (double)k / (double)cs;
-            while (i < np && cum[i] < target) ++i;
-            pl.rows[k] = std::max(pl.rows[k - 1], i);
-        }
-        pl.rows[cs] = np;
-        int rows_max = 0;
-        for (int k = 0; k < cs; ++k) rows_max = std::max(rows_max, pl.rows[k + 1] - pl.rows[k]);
-        size_t kh_max = 0, p_max = 0;
-        int slots_max = 0;
-        for (int k = 0; k < cs; ++k) {
-            const int r0 = pl.rows[k], r1 = pl.rows[k + 1];
-            for (int c = 0; c < pl.nc; ++c) {
-                const int c0 = c * kc, c1 = std::min(np, c0 + kc);
-                RowEntries ent(r1 - r0);
-                for (int row = r0; row < r1; ++row)
-                    for (const int2 &e : all[row])
-                        if (e.x >= c0 && e.x < c1) ent[row - r0].push_back(make_int2(e.x - c0, e.y));
-                const size_t kb = pl.kh.size();  // even: every block starts 16-byte aligned
-                const int first = (int)(pl.pieces.size() / kBundleInt4);
-                pl.sb.push_back(first);
-                pl.cutb.push_back((int)pl.cuts.size());
-                slots_max = std::max(slots_max, split_bundles(r0, r1, ent, kb, pl.kh, pl.pieces, pl.wb, pl.cuts,
-                                                              np > kColMaxNp ? kPartMax : 0, /*skip_empty=*/true));
-                if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
-                pl.q.push_back((int)kb);
-                pl.q.push_back((int)pl.kh.size());
-                kh_max = std::max(kh_max, (pl.kh.size() - kb) * 8);
-                p_max = std::max(p_max, (size_t)((int)(pl.pieces.size() / kBundleInt4) - first) * 16 * kBundleInt4);
-            }
-        }
-        pl.sb.push_back((int)(pl.pieces.size() / kBundleInt4));
-        pl.wb.push_back((int)(pl.pieces.size() / kBundleInt4));
-        pl.cutb.push_back((int)pl.cuts.size());
-        pl.kh_slot = (int)std::max<size_t>(16, kh_max);
-        pl.p_slot = (int)std::max<size_t>(16, p_max);
-        pl.acc_off = 2 * kc * kRowFloats * 4;
-        pl.kh_off = pl.acc_off + rows_max * kRowFloats * 4;
-        pl.p_off = pl.kh_off + 2 * pl.kh_slot;
-        pl.part_off = pl.p_off + 2 * pl.p_slot;
-        const size_t smem = (size_t)pl.part_off + (size_t)slots_max * kRowFloats * 4 + 128;
-        if (smem_max <= 1024 || smem > (size_t)smem_max - 1024) continue;
-        pl.smem = (int)smem;
-        // the cluster must be schedulable with this shared memory
-        if (set_chunk_attrs(pl.smem, cs) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        int clusters = 0;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cs, ncb);
-        cfg.blockDim = dim3(kANT);
-        cfg.dynamicSmemBytes = (size_t)pl.smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = cs;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&clusters, cols_chunk_kernel, &cfg) != cudaSuccess || clusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
-        if (pl.kh.empty()) pl.kh.assign(2, make_int2(0, 0));
-        plan = std::move(pl);
-        return true;
-    }
-    return false;
-}
-
-cudaError_t set_chunk_attrs(int bytes, int cs) {
-    cudaError_t e = cudaFuncSetAttribute(cols_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && cs > 8)
-        e = cudaFuncSetAttribute(cols_chunk_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
-}
-
 bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
@@ -664,9 +441,12 @@ cudaError_t set_gather_smem(int bytes) {
 }
 
 // Stage inputs: stage 1 D (map 0), stage 2 da (map 1), stage 3 db (map 2),
-// stage 4 da (map 1). parts & 1: the SpMM kernel, parts & 2: the epilogue.
+// stage 4 da (map 1). With pdl, the launch may start before the previous
+// kernel in the stream has finished (programmatic dependent launch; the
+// kernel waits with griddepcontrol.wait before it reads that kernel's
+// output); without, it is an ordinary stream-ordered launch.
 template <typename K, typename... A>
-void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -676,70 +456,50 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, A.
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// The chunked SpMM: clusters of col_cs CTAs along x, with programmatic
-// dependent launch.
-static void launch_chunks(const CUtensorMap &tm, const DevOps &ops, const MixedWork &w, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ops.col_cs, ops.np / kCW);
-    cfg.blockDim = dim3(kANT);
-    cfg.dynamicSmemBytes = (size_t)ops.col_smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[2];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    at[1].id = cudaLaunchAttributeClusterDimension;
-    at[1].val.clusterDim.x = ops.col_cs;
-    at[1].val.clusterDim.y = 1;
-    at[1].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 2;
-    cudaLaunchKernelEx(&cfg, cols_chunk_kernel, tm, ops, w);
-}
-
-void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts,
-                       cudaEvent_t mark) {
+void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts, bool serial) {
     const ColMaps &m = *w.cmaps;
     // whole block: (J, r); gather: (r, J) over 32-column blocks, the splits of a block side by side
     const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCWWide) : dim3(ops.np / kCW, ops.col_splits);
     const size_t sm = (size_t)ops.col_smem;
     const CUtensorMap &tm = m.d[stage == 1 ? 0 : (stage == 3 ? 2 : 1)];
+    const bool pdl = !serial;
+    if (serial && (parts & 4)) cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), s>>>(ops, w);
     if (parts & 1) {
-        // fork: the gain on the side stream, the SpMM here; join before the epilogue
-        cudaEventRecord(m.fork, s);
-        cudaStreamWaitEvent(m.side, m.fork, 0);
-        cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
-        cudaEventRecord(m.join, m.side);
-        if (ops.col_cs > 0) {
-            launch_chunks(tm, ops, w, s);
-        } else if (ops.col_gather) {
+        if (!serial) {
+            // fork: the gain on the side stream, the SpMM here; join before the epilogue
+            cudaEventRecord(m.fork, s);
+            cudaStreamWaitEvent(m.side, m.fork, 0);
+            cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
+            cudaEventRecord(m.join, m.side);
+        }
+        if (ops.col_gather) {
             switch (stage) {
-                case 1: launch_pdl(cols_gather_kernel<1>, ga, dim3(kANT), sm, s, ops, w); break;
-                case 2: launch_pdl(cols_gather_kernel<2>, ga, dim3(kANT), sm, s, ops, w); break;
-                case 3: launch_pdl(cols_gather_kernel<3>, ga, dim3(kANT), sm, s, ops, w); break;
-                default: launch_pdl(cols_gather_kernel<4>, ga, dim3(kANT), sm, s, ops, w); break;
+                case 1: launch_pdl(cols_gather_kernel<1>, ga, dim3(kANT), sm, s, pdl, ops, w); break;
+                case 2: launch_pdl(cols_gather_kernel<2>, ga, dim3(kANT), sm, s, pdl, ops, w); break;
+                case 3: launch_pdl(cols_gather_kernel<3>, ga, dim3(kANT), sm, s, pdl, ops, w); break;
+                default: launch_pdl(cols_gather_kernel<4>, ga, dim3(kANT), sm, s, pdl, ops, w); break;
             }
         } else {
             switch (stage) {
-                case 1: launch_pdl(cols_spmm_kernel<1>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-                case 2: launch_pdl(cols_spmm_kernel<2>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-                case 3: launch_pdl(cols_spmm_kernel<3>, ga, dim3(kANT), sm, s, tm, ops, w); break;
-                default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, tm, ops, w); break;
+                case 1: launch_pdl(cols_spmm_kernel<1>, ga, dim3(kANT), sm, s, pdl, tm, ops, w); break;
+                case 2: launch_pdl(cols_spmm_kernel<2>, ga, dim3(kANT), sm, s, pdl, tm, ops, w); break;
+                case 3: launch_pdl(cols_spmm_kernel<3>, ga, dim3(kANT), sm, s, pdl, tm, ops, w); break;
+                default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, pdl, tm, ops, w); break;
             }
         }
-        if (mark) cudaEventRecord(mark, s);
-        cudaStreamWaitEvent(s, m.join, 0);
+        if (!serial) cudaStreamWaitEvent(s, m.join, 0);
     }
     if (parts & 2) {
         const dim3 ge(w.npairs);
         switch (stage) {
-            case 1: launch_pdl(cols_epi_kernel<1>, ge, dim3(kENT), 0, s, ops, w); break;
-            case 2: launch_pdl(cols_epi_kernel<2>, ge, dim3(kENT), 0, s, ops, w); break;
-            case 3: launch_pdl(cols_epi_kernel<3>, ge, dim3(kENT), 0, s, ops, w); break;
-            default: launch_pdl(cols_epi_kernel<4>, ge, dim3(kENT), 0, s, ops, w); break;
+            case 1: launch_pdl(cols_epi_kernel<1>, ge, dim3(kENT), 0, s, pdl, ops, w); break;
+            case 2: launch_pdl(cols_epi_kernel<2>, ge, dim3(kENT), 0, s, pdl, ops, w); break;
+            case 3: launch_pdl(cols_epi_kernel<3>, ge, dim3(kENT), 0, s, pdl, ops, w); break;
+            default: launch_pdl(cols_epi_kernel<4>, ge, dim3(kENT), 0, s, pdl, ops, w); break;
         }
     }
 }

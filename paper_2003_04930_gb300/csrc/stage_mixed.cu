@@ -119,10 +119,9 @@ void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s)
     refresh_post_kernel<<<grid_elems(tot), 256, 0, s>>>(ops, w);
 }
 
-void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts,
-                        cudaEvent_t mark) {
-    if (w.cmaps) {  // column-block form: parts 1 = SpMM, 2 = epilogue
-        launch_cols_stage(stage, ops, w, s, parts, mark);
+void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts, bool serial) {
+    if (w.cmaps) {  // column-block form: parts 1 = SpMM (with the gain beside it), 2 = epilogue, 4 = gain (serial)
+        launch_cols_stage(stage, ops, w, s, parts, serial);
         return;
     }
     const float *din = (stage == 1) ? w.D : (stage == 3 ? w.db : w.da);

@@ -24,27 +24,31 @@ using namespace cols;
 
 // Epilogue buffers: sX1, sX2 (TS x LDX), sO (4 TS x LDO), sg (TS), in floats.
 constexpr int kEpiFloats = 2 * TS * LDX + 4 * TS * LDO + TS;
-// Spins of a grid-barrier wait before the kernel reports a timeout (each
-// spin sleeps ~100 ns: well above a second).
-constexpr long long kBarrierSpins = 1ll << 24;
+// Time a grid-barrier wait may take before the kernel reports a timeout
+// (one second on the global nanosecond timer; a legitimate wait at these
+// sizes is microseconds).
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 
 // Grid-wide barrier by generation count. Release: every CTA's writes are
 // fenced before it arrives; acquire: the waiter fences after it sees the new
-// generation. Bounded: returns false (and sets err_timeout) when it gave up.
+// generation. The barrier completes when ncta + ctl->gb_extra CTAs have
+// arrived (gb_extra is 0 except under qpr_options.test_fault). Bounded:
+// returns false (and sets err_timeout) when it gave up.
 __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned ncta, unsigned &gen, int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned g = gen;
+        const unsigned expect = ncta + *(volatile unsigned *)&ctl->gb_extra;
         __threadfence();
-        if (atomicAdd(&ctl->gb_count, 1u) == ncta - 1) {
+        if (atomicAdd(&ctl->gb_count, 1u) == expect - 1) {
             atomicExch(&ctl->gb_count, 0u);
             __threadfence();
             atomicExch(&ctl->gb_gen, g + 1);
         } else {
-            long long it = 0;
+            const unsigned long long t0 = tma::global_ns();
             while (*(volatile unsigned *)&ctl->gb_gen == g) {
-                if (++it > kBarrierSpins) {
+                if (tma::global_ns() - t0 > kBarrierTimeoutNs) {
                     ok = 0;
                     atomicExch(&ctl->err_timeout, 1);
                     break;
@@ -106,7 +110,7 @@ __device__ __forceinline__ int persist_stage(const CUtensorMap *tm, const DevOps
             return -1;
         }
         warp_bundles(sm.sD, sm.sKH, sm.sP, ops.col_sb[r], ops.col_wb[r * kAWarps + warp],
-                     ops.col_wb[r * kAWarps + warp + 1], J, np, w.X, nullptr, 0, sm.parts);
+                     ops.col_wb[r * kAWarps + warp + 1], J, np, w.X, sm.parts);
         const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
         if (cb1 > cb0) {
             __syncthreads();

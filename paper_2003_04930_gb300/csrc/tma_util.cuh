@@ -9,16 +9,23 @@
 namespace qpr {
 namespace tma {
 
-// Iterations of a bounded mbarrier wait before the kernel reports a timeout
-// (far above any legitimate wait at these sizes).
-constexpr long long kSpinLimit = 1ll << 26;
+// Time a bounded mbarrier wait may take before the kernel reports a timeout
+// (one second on the global nanosecond timer: far above any legitimate wait
+// at these sizes).
+constexpr unsigned long long kWaitTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
 }
-// Makes the initialisation visible to the async proxy (TMA) and the cluster.
+// Makes the initialisation visible to the async proxy (TMA).
 __device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
@@ -26,10 +33,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// Bounded wait for phase `parity`; false if it gave up.
+// Bounded wait for phase `parity`; false if it gave up. The timer is read
+// only after a try_wait that failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; ++it) {
+    unsigned long long t0 = 0;
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -37,8 +46,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        const unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > kWaitTimeoutNs) return false;
     }
-    return false;
 }
 
 // Tiled tensor loads into shared memory, completing on `bar` (bytes
@@ -75,30 +86,6 @@ __device__ __forceinline__ void load_bulk(void *dst, const void *src, uint32_t b
             smem_u32(dst)),
         "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 3-D tiled load multicast to the CTAs of the cluster in cta_mask: the box
-// lands at the same shared-memory offset in each, and each CTA's mbarrier at
-// the offset of `bar` receives the bytes.
-__device__ __forceinline__ void load_3d_multicast(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                                  int c2, uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%3, %4, %5}], [%2], %6;\n" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
-        : "memory");
-}
-
-// Thread-block cluster: this CTA's rank, and the cluster-wide barrier (every
-// thread of every CTA of the cluster; release/acquire of shared and global
-// memory).
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 // Programmatic dependent launch: wait until the previous kernel in the

@@ -23,7 +23,7 @@ QPR_HDIAG_ZERO, QPR_HDIAG_NEG_OUTDEG = 0, 1
 QPR_DANGLING_F, QPR_DANGLING_UNIFORM = 0, 1
 QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
 (QPR_SPARSE_FORM_AUTO, QPR_SPARSE_FORM_COLUMNS, QPR_SPARSE_FORM_TILES, QPR_SPARSE_FORM_COLUMNS_PERSISTENT,
- QPR_SPARSE_FORM_COLUMNS_CHUNKED, QPR_SPARSE_FORM_COLUMNS_GATHER) = 0, 1, 2, 3, 4, 5
+ QPR_SPARSE_FORM_COLUMNS_GATHER) = 0, 1, 2, 3, 5
 
 # every entry point declared in include/qpr.h
 EXPORTED = (
@@ -41,7 +41,7 @@ class qpr_options(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("backend", ctypes.c_int32),
                 ("ref_refresh", ctypes.c_int32), ("sparse_form", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_int32), ("row_splits", ctypes.c_int32),
+                ("test_fault", ctypes.c_int32), ("row_splits", ctypes.c_int32),
                 ("adaptive_refresh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
@@ -55,6 +55,16 @@ class qpr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k in
                 ("steps", "substeps_m", "t", "residual", "trace_before", "seconds", "kernel_launches",
                  "converged")}
+
+
+class qpr_profile(ctypes.Structure):
+    _fields_ = [("product_ms", ctypes.c_double), ("epilogue_ms", ctypes.c_double), ("gain_ms", ctypes.c_double),
+                ("refresh_ms", ctypes.c_double), ("step_ms", ctypes.c_double),
+                ("launches_per_step", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in
+                ("product_ms", "epilogue_ms", "gain_ms", "refresh_ms", "step_ms", "launches_per_step")}
 
 
 class qpr_problem(ctypes.Structure):
@@ -120,7 +130,7 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_evolve.restype = st
     lib.qpr_steady_state.argtypes = [vp, vp, f64, f64, i64, ctypes.POINTER(qpr_stats)]
     lib.qpr_steady_state.restype = st
-    lib.qpr_profile_step.argtypes = [vp, vp, f64, i64, ctypes.POINTER(f64)]
+    lib.qpr_profile_step.argtypes = [vp, vp, f64, i64, ctypes.POINTER(qpr_profile)]
     lib.qpr_profile_step.restype = st
     lib.qpr_rhs_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, f64, f64, ctypes.c_int32, vp, vp, vp]
     lib.qpr_rhs_noalloc.restype = st
@@ -188,15 +198,15 @@ class Solver:
     The keyword options are the fields of qpr_options (include/qpr.h):
     precision (QPR_FP64 or QPR_MIXED), backend, h_diag, dangling,
     graph_steps, ref_refresh, sparse_form (the mixed sparse stage's form),
-    chunk_rows (COLUMNS_CHUNKED), row_splits (COLUMNS, COLUMNS_GATHER) and
-    adaptive_refresh (steady-state solves of the mixed form); stream is a
+    row_splits (COLUMNS, COLUMNS_GATHER), adaptive_refresh (steady-state
+    solves of the mixed form) and test_fault (testing only); stream is a
     torch stream (or a raw cudaStream_t) the caller's inputs are ordered on.
     """
 
     def __init__(self, n, src, dst, w=None, alpha=0.85, omega=0.8, h_diag=QPR_HDIAG_ZERO,
                  dangling=QPR_DANGLING_F, precision=QPR_FP64, graph_steps=32, stream=None, device=-1,
-                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, chunk_rows=0,
-                 row_splits=0, adaptive_refresh=1):
+                 backend=QPR_BACKEND_AUTO, ref_refresh=32, sparse_form=QPR_SPARSE_FORM_AUTO, row_splits=0,
+                 adaptive_refresh=1, test_fault=0):
         lib = load_library()
         self._lib = lib
         self.n = int(n)
@@ -211,7 +221,7 @@ class Solver:
         opt.backend = int(backend)
         opt.ref_refresh = int(ref_refresh)
         opt.sparse_form = int(sparse_form)
-        opt.chunk_rows = int(chunk_rows)
+        opt.test_fault = int(test_fault)
         opt.row_splits = int(row_splits)
         opt.adaptive_refresh = int(adaptive_refresh)
         if stream is not None:
@@ -255,17 +265,17 @@ class Solver:
 
     @property
     def sparse_form(self) -> int:
-        """QPR_SPARSE_FORM_COLUMNS, _COLUMNS_PERSISTENT, _COLUMNS_CHUNKED,
-        _COLUMNS_GATHER or _TILES (0: not the mixed sparse form)."""
+        """QPR_SPARSE_FORM_COLUMNS, _COLUMNS_PERSISTENT, _COLUMNS_GATHER or
+        _TILES (0: not the mixed sparse form)."""
         return int(self._lib.qpr_sparse_form(self._h))
 
     @property
     def sparse_plan(self) -> dict:
-        """Geometry of the column-block product: row splits (cluster size),
-        chunk rows (0: whole block), chunks, shared-memory bytes."""
+        """Geometry of the column-block product: row splits, complex columns
+        per block, CTAs per product launch, shared-memory bytes."""
         out = (ctypes.c_int32 * 4)()
         self._raise(self._lib.qpr_sparse_plan(self._h, out))
-        return {"splits": out[0], "chunk_rows": out[1], "chunks": out[2], "smem": out[3]}
+        return {"splits": out[0], "block_cols": out[1], "ctas": out[2], "smem": out[3]}
 
     @property
     def h_spread(self) -> float:
@@ -314,12 +324,13 @@ class Solver:
         return (p, rank) if with_rank else p
 
     def profile_step(self, rho, dt: float, steps: int):
-        """Mean per-launch durations (ms) of the stage kernel and the gain
-        kernel, and of one whole RK4 step, timed with CUDA events."""
+        """qpr_profile_step: each kernel of `steps` RK4 steps run alone
+        between CUDA events; mean durations (ms) of the product, epilogue,
+        gain and refresh kernels, and the serialised step."""
         _check_rho(rho, self.n)
-        ms = (ctypes.c_double * 3)()
-        self._raise(self._lib.qpr_profile_step(self._h, _ptr(rho), float(dt), int(steps), ms))
-        return {"stage_ms": ms[0], "gain_ms": ms[1], "step_ms": ms[2]}
+        out = qpr_profile()
+        self._raise(self._lib.qpr_profile_step(self._h, _ptr(rho), float(dt), int(steps), ctypes.byref(out)))
+        return out.as_dict()
 
 
 def batch_steady_state(problems, alpha=0.85, dt=0.01, tol=1e-8, max_steps=400000, ref_refresh=32,

@@ -65,8 +65,8 @@ def _create(lib, n, src, dst, w=None, alpha=0.85, omega=0.5, **optkw):
     (dict(n=3, src=[0], dst=[1], dangling=5), qpr.QPR_E_ARG),
     (dict(n=3, src=[0], dst=[1], precision=9), qpr.QPR_E_ARG),
     (dict(n=3, src=[0], dst=[1], sparse_form=6), qpr.QPR_E_ARG),
-    (dict(n=3, src=[0], dst=[1], chunk_rows=48), qpr.QPR_E_ARG),
-    (dict(n=3, src=[0], dst=[1], chunk_rows=-32), qpr.QPR_E_ARG),
+    (dict(n=3, src=[0], dst=[1], sparse_form=4), qpr.QPR_E_ARG),
+    (dict(n=3, src=[0], dst=[1], test_fault=2), qpr.QPR_E_ARG),
     (dict(n=3, src=[0], dst=[1], row_splits=65), qpr.QPR_E_ARG),
     (dict(n=3, src=[0, 3], dst=[1, 0]), qpr.QPR_E_GRAPH),
     (dict(n=3, src=[0, -1], dst=[1, 0]), qpr.QPR_E_GRAPH),

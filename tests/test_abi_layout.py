@@ -13,7 +13,8 @@ import pytest
 from paper_2003_04930_gb300 import qpr
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-STRUCTS = [qpr.qpr_options, qpr.qpr_stats, qpr.qpr_problem, qpr.qpr_gnn_sample, qpr.qpr_tune_result]
+STRUCTS = [qpr.qpr_options, qpr.qpr_stats, qpr.qpr_profile, qpr.qpr_problem, qpr.qpr_gnn_sample,
+           qpr.qpr_tune_result]
 
 
 @pytest.fixture(scope="module")

@@ -1,21 +1,17 @@
 """The forms of the FP32 sparse stage of QPR_MIXED: the column-block form
 (two launches per stage), its persistent form (one cooperative launch per
 block of steps), its gather form (rows of the block read from L2, for any
-N), its chunked form (clusters streaming the column block in chunks, for any
 N) and the tile-pair form.
 
 The two whole-block column forms run the same device arithmetic (row
 products in entry order, the same gain and epilogue sums, the same stop
 decision), so their states, step counts and residuals are bitwise equal.
-The chunked form sums each row chunk by chunk, so it equals them bitwise
-when the block is one chunk. The gather form (32-column blocks, a row's
-long sums dealt over 4 partial sums instead of 8), the chunked and the
-tile-pair forms sum the products in other FP32 orders and are held, like
-every form, to the mixed form's tolerances against the FP64 oracle: trajectories (t = 1.5)
-||drho||_F <= 1e-6 and max|dp| <= 1e-6 max p, steady states ||drho||_F <= 1e-6
-and max|dp| <= 1e-7 max p. Small chunk_rows make the chunked form stream
-several chunks (both buffers, both barrier phases, a ragged last chunk
-where 32-row boxes do not fill it) at sizes the oracle runs quickly.
+The gather form (32-column blocks, a row's long sums dealt over 4 partial
+sums instead of 8) and the tile-pair form sum the products in other FP32
+orders and are held, like every form, to the mixed form's tolerances
+against the FP64 oracle: trajectories (t = 1.5) ||drho||_F <= 1e-6 and
+max|dp| <= 1e-6 max p, steady states ||drho||_F <= 1e-6 and max|dp| <=
+1e-7 max p.
 """
 import numpy as np
 import pytest
@@ -29,20 +25,13 @@ from paper_2003_04930_gb300 import qpr as Q
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 FORMS = (Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, Q.QPR_SPARSE_FORM_COLUMNS_GATHER,
-         Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, Q.QPR_SPARSE_FORM_TILES)
+         Q.QPR_SPARSE_FORM_TILES)
 BITWISE = (Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT,)  # equal to COLUMNS
 
 
-def _chunk_rows(n):
-    """Chunks of 32 to 128 rows: 2 to 7 chunks at these sizes."""
-    return 32 if n <= 200 else (64 if n <= 320 else 128)
-
-
-def _solver(g, omega, form, refresh=32, chunk_rows=None):
-    if chunk_rows is None:
-        chunk_rows = _chunk_rows(g.n) if form == Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED else 0
+def _solver(g, omega, form, refresh=32, **kw):
     return Solver.from_edges(g, alpha=0.85, omega=omega, precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE,
-                             sparse_form=form, ref_refresh=refresh, chunk_rows=chunk_rows)
+                             sparse_form=form, ref_refresh=refresh, **kw)
 
 
 def _close(got, ref, prel):
@@ -57,7 +46,10 @@ def test_default_form_is_columns_where_it_fits():
     big = Solver.from_edges(graphs.heavy_tailed(2000, 1), precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE)
     assert big.sparse_form == Q.QPR_SPARSE_FORM_COLUMNS_GATHER  # 2016 padded rows: the whole block does not fit
     plan = big.sparse_plan
-    assert plan["splits"] >= 1 and plan["chunk_rows"] == 0 and plan["chunks"] == 1
+    assert plan["splits"] >= 1 and plan["block_cols"] == 32 and plan["ctas"] == plan["splits"] * 2016 // 32
+    small = Solver.from_edges(graphs.heavy_tailed(300, 1), precision=Q.QPR_MIXED,
+                              backend=Q.QPR_BACKEND_SPARSE).sparse_plan
+    assert small["block_cols"] == 16 and small["ctas"] == small["splits"] * 320 // 16 and small["smem"] > 0
     fp64 = Solver.from_edges(graphs.heavy_tailed(300, 1), backend=Q.QPR_BACKEND_SPARSE)
     assert fp64.sparse_form == 0
 
@@ -86,11 +78,6 @@ def test_forms_trajectory(n, omega, refresh):
         assert np.abs(got[form] - got[form].conj().T).max() == 0.0
     for form in BITWISE:
         np.testing.assert_array_equal(got[form], got[Q.QPR_SPARSE_FORM_COLUMNS])
-    # one chunk: the whole-block sums
-    s = _solver(g, omega, Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, refresh, chunk_rows=4096)
-    d = torch.from_numpy(rho0.copy()).to(DEV)
-    s.evolve(d, 0.01, 150)
-    np.testing.assert_array_equal(d.cpu().numpy(), got[Q.QPR_SPARSE_FORM_COLUMNS])
 
 
 @pytest.mark.parametrize("n,omega", [(150, 0.8), (400, 0.3)])
@@ -135,20 +122,40 @@ def large_case():
     return g, omega, rho0, ref
 
 
-@pytest.mark.parametrize("form,chunk_rows", [(Q.QPR_SPARSE_FORM_COLUMNS_GATHER, 0),
-                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 0),
-                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 96),
-                                             (Q.QPR_SPARSE_FORM_COLUMNS_CHUNKED, 512),
-                                             (Q.QPR_SPARSE_FORM_TILES, 0)])
-def test_large_n_trajectory(large_case, form, chunk_rows):
-    # N = 2000 (2016 padded rows), beyond the whole-block form; the chunked
-    # form with its default plan, 96-row chunks (21, the last of 96 rows) and
-    # 512-row chunks (4, the last of 480 rows)
+@pytest.mark.parametrize("form", [Q.QPR_SPARSE_FORM_COLUMNS_GATHER, Q.QPR_SPARSE_FORM_TILES])
+def test_large_n_trajectory(large_case, form):
+    # N = 2000 (2016 padded rows), beyond the whole-block form
     g, omega, rho0, ref = large_case
-    s = _solver(g, omega, form, chunk_rows=chunk_rows)
+    s = _solver(g, omega, form)
     assert s.sparse_form == form
     d = torch.from_numpy(rho0.copy()).to(DEV)
     s.evolve(d, 0.01, 40)
     got = d.cpu().numpy()
     _close(got, ref, 1e-6)
     assert np.abs(got - got.conj().T).max() == 0.0
+
+
+def test_grid_barrier_timeout_is_reported_and_context_stays_usable():
+    # test_fault makes every grid barrier of the persistent form wait for one
+    # arrival more than its grid makes: no barrier completes, every CTA's
+    # bounded wait gives up after its time limit (about a second), sets the
+    # error flag and leaves the kernel. The host reads the flag and returns
+    # QPR_E_TIMEOUT; no CUDA error occurs, so the context is not poisoned.
+    import time
+    g = graphs.heavy_tailed(120, 7)
+    s = _solver(g, 0.8, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, refresh=16, test_fault=1)
+    d = torch.from_numpy(graphs.maximally_mixed(120)).to(DEV)
+    t = time.perf_counter()
+    with pytest.raises(Q.QprError) as e:
+        s.steady_state(d, 0.01, 1e-8, 1000)
+    assert e.value.status == Q.QPR_E_TIMEOUT
+    assert time.perf_counter() - t < 60.0
+    # the same context still serves calls that need no grid barrier
+    o = Oracle.from_edges(g, alpha=0.85, omega=0.8)
+    rho = graphs.random_density(120, 3, rank=2)
+    assert abs(s.residual(torch.from_numpy(rho).to(DEV)) - o.residual(rho)) <= 1e-12
+    # and the device serves a context without the fault
+    ok = _solver(g, 0.8, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, refresh=16)
+    d.copy_(torch.from_numpy(graphs.maximally_mixed(120)))
+    st = ok.steady_state(d, 0.01, 1e-8, 200000)
+    assert st["converged"] == 1

@@ -45,6 +45,48 @@ def test_features_of_hand_worked_graph():
     np.testing.assert_allclose(x[:, 6], np.log(4 * pi), atol=1e-12)
 
 
+def _hand_params(gd):
+    d = {name: np.zeros(shp) for name, shp in gnn.param_shapes()}
+    for name, i, j, v in gd["weights_nonzero"]:
+        if j is None:
+            d[name][i] = v
+        else:
+            d[name][i, j] = v
+    return gnn.pack(d)
+
+
+def test_aggregation_and_forward_of_hand_worked_network():
+    # the network definition worked out by hand on the four-node graph: the
+    # aggregation matrix (built from A + A^T, rows normalised, not symmetric),
+    # the first layer's pre-activations and activations, a second-layer unit
+    # fed only by P h1, and the logits of the readout
+    with open(os.path.join(GOLDEN, "gnn_n4.json")) as f:
+        gd = json.load(f)
+    A = np.array(gd["A"], dtype=np.float64)
+    P = gnn.aggregation(A)
+    np.testing.assert_allclose(P, np.array(gd["P"]), rtol=0, atol=1e-15)
+    x = np.zeros((4, gnn.F_IN))
+    x[:, :2] = np.array(gd["x_columns_0_1"], dtype=np.float64)
+    th = _hand_params(gd)
+    for bf16 in (True, False):  # powers of two: BF16 rounding changes nothing
+        s, ph, cache = gnn.forward(th, x, P, bf16=bf16)
+        h0, m1, z1 = cache[0]
+        np.testing.assert_allclose(m1[:, 1], gd["layer1"]["P_v"], atol=1e-15)
+        np.testing.assert_allclose(m1[:, 0], gd["layer1"]["P_ones"], atol=1e-15)
+        np.testing.assert_allclose(z1[:, :3], np.array(gd["layer1"]["z_units_0_1_2"]), atol=1e-15)
+        assert np.all(z1[:, 3:] == 0)
+        h1 = cache[1][0]
+        np.testing.assert_allclose(h1[:, :3], np.array(gd["layer1"]["h_units_0_1_2"]), atol=1e-15)
+        z2 = cache[1][2]
+        np.testing.assert_allclose(z2[:, 3], gd["layer2_unit3"], atol=1e-15)
+        np.testing.assert_allclose(s, gd["logits"], atol=1e-14)
+        # softmax of the logits: equal logits give equal probabilities, and
+        # the ratio of two is exp of their difference
+        assert ph[0] == pytest.approx(ph[3], rel=1e-15)
+        assert ph[0] / ph[1] == pytest.approx(np.exp(2.25), rel=1e-14)
+        assert ph[2] / ph[1] == pytest.approx(np.exp(1.25), rel=1e-14)
+
+
 def test_pagerank_feature_equals_omega1_steady_state():
     g = graphs.heavy_tailed(30, 4)
     A = gnn.adjacency(g.n, g.src, g.dst, g.w)

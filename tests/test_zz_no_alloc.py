@@ -5,10 +5,11 @@ that own every device allocation through their own pool, fixed memory
 budgets, no allocation after start-up): it keeps its scratch in a
 fixed-size __device__ array and takes everything else from the caller. This
 test builds the CSR operands from the CPU oracle's operators, calls the
-entry point through the C ABI twice in a row (the second call runs on the
-scratch the first one left behind), and checks both outputs against the
-context-based qpr_rhs within the tolerance of the other right-hand-side
-parity tests. The file name sorts last so that a run stopping at the first
+entry point through the C ABI for three sizes in a row, twice each (every
+call runs on the scratch the previous one left behind, a larger size's
+included), and checks every output against the context-based qpr_rhs and
+the oracle's right-hand side within the tolerance of the other
+right-hand-side parity tests. The file name sorts last so that a run stopping at the first
 failure has already run every other test.
 """
 import ctypes
@@ -54,23 +55,38 @@ def _call(lib, n, ops, alpha, omega, dangling, rho, out):
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("n,omega,dangling", [(200, 0.8, 0), (97, 0.3, 1), (256, 0.0, 0)])
-def test_noalloc_rhs_matches_context_rhs_twice(n, omega, dangling):
+CASES = [(256, 0.0, 0), (97, 0.3, 1), (200, 0.8, 0)]
+
+
+def _graph(n):
+    return graphs.heavy_tailed(n, 11) if n != 97 else graphs.erdos_renyi(n, 0.03, 5)
+
+
+def test_noalloc_rhs_matches_context_rhs_twice():
+    # one test, sizes in the order 256, 97, 200: each call runs on the scratch
+    # the previous one left behind, including a larger padded size's (256 ->
+    # 128 -> 224 padded rows), and each size is called twice in a row
     lib = Q.load_library()
-    g = graphs.heavy_tailed(n, 11) if n != 97 else graphs.erdos_renyi(n, 0.03, 5)
-    kw = dict(alpha=0.85, omega=omega, dangling=dangling)
-    ops = _operands(g, **kw)
-    s = Solver.from_edges(g, **kw)
-    for call in range(2):
-        rho = torch.from_numpy(graphs.random_hermitian(n, 100 + call)).to(DEV)
-        ref = torch.zeros_like(rho)
-        s.rhs(rho, ref)
-        out = torch.full_like(rho, float("nan"))
-        assert _call(lib, n, ops, 0.85, omega, dangling, rho, out) == Q.QPR_OK
-        torch.cuda.synchronize()
-        r, o = ref.cpu().numpy(), out.cpu().numpy()
-        scale = max(1.0, np.abs(r).max())
-        assert np.abs(o - r).max() <= 1e-13 * scale * max(1, n / 16), call
+    for n, omega, dangling in CASES:
+        g = _graph(n)
+        kw = dict(alpha=0.85, omega=omega, dangling=dangling)
+        ops = _operands(g, **kw)
+        s = Solver.from_edges(g, **kw)
+        o = Oracle.from_edges(g, **kw)
+        for call in range(2):
+            rho = torch.from_numpy(graphs.random_hermitian(n, 100 + call)).to(DEV)
+            ref = torch.zeros_like(rho)
+            s.rhs(rho, ref)
+            out = torch.full_like(rho, float("nan"))
+            assert _call(lib, n, ops, 0.85, omega, dangling, rho, out) == Q.QPR_OK
+            torch.cuda.synchronize()
+            r, got = ref.cpu().numpy(), out.cpu().numpy()
+            scale = max(1.0, np.abs(r).max())
+            assert np.abs(got - r).max() <= 1e-13 * scale * max(1, n / 16), (n, call)
+            # and directly against the oracle's right-hand side
+            f = o.rhs(rho.cpu().numpy())
+            assert np.abs(got - f).max() <= 1e-13 * max(1.0, np.abs(f).max()) * max(1, n / 16), (n, call)
+        s.close()
 
 
 def test_noalloc_rejects_sizes_beyond_maximum():
