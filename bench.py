@@ -347,6 +347,10 @@ def run_ours(a):
             "residual": stats[-1]["residual"], "roofline": roof, "profile_ms": prof, "clocks": clocks,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats))}
 
+    # the main text's comparison of the quantum and the classical ranking: hub classes (c = 10) of the
+    # steady-state populations and of the classical PageRank vector, both on the GPU
+    line["hubs"] = hub_report(s, rho_solved)
+
     # the plain dense FP64 (DMMA) form on the same problem: s/step x steps
     if not a.no_dense_projection and s.backend != qpr.QPR_BACKEND_DENSE:
         line["plain_fp64_dense"] = dense_projection(g, a.omega, local, rho, a.dt, steps_conv, peaks, peak_src)
@@ -390,6 +394,28 @@ def run_ours(a):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def hub_report(s, rho_ss, c=10.0, top=10):
+    """QPR against classical PageRank on the solved graph: hub counts (main
+    p > c/N, secondary 1/N < p <= c/N) of both vectors, the overlap of their
+    hub sets and of their top-`top` nodes (qpr_populations, qpr_pagerank,
+    qpr_hub_classes)."""
+    import numpy as np
+    p, rank = s.populations(rho_ss, with_rank=True)
+    t = time.perf_counter()
+    pi = s.pagerank(tol=1e-14)
+    t_pr = time.perf_counter() - t
+    cq, nq = s.hub_classes(p, c)
+    cp, npr = s.hub_classes(pi, c)
+    rank_pr = np.argsort(-pi, kind="stable")
+    return {"c": c, "qpr_counts": {"main": int(nq[2]), "secondary": int(nq[1])},
+            "pagerank_counts": {"main": int(npr[2]), "secondary": int(npr[1])},
+            "main_hubs_in_both": int(np.sum((cq == 2) & (cp == 2))),
+            "hubs_in_both": int(np.sum((cq >= 1) & (cp >= 1))),
+            f"top{top}_overlap": len(set(rank[:top].tolist()) & set(rank_pr[:top].tolist())),
+            "qpr_top": rank[:top].tolist(), "pagerank_top": rank_pr[:top].tolist(),
+            "pagerank_iters": s.last_pagerank_iters, "pagerank_s": t_pr}
 
 
 def form_name(s, prec):

@@ -254,6 +254,32 @@ QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, in
  * ties to the lower index (the ranking of the main text's airline study). */
 QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank);
 
+/* ---- classical PageRank and hub classes ----
+ * The main text compares the quantum PageRank ranking of the airline network
+ * with the classical PageRank and sorts nodes into hubs (its airline-ranking
+ * paragraph: main hubs above c/N, secondary hubs between 1/N and c/N, with
+ * c = 10).
+ *
+ * qpr_pagerank: the classical PageRank pi of the context's graph, the
+ * stationary vector of G = alpha S + (1 - alpha) F (Eq. S4, Eq. S2): G pi =
+ * pi, sum pi = 1 (also the populations of the omega = 1 steady state). Power
+ * iteration in FP64 on the device from the uniform vector, each iterate
+ * divided by its sum, until the L1 change of one iteration is below tol
+ * (checked every 8 iterations) or max_iter iterations. pi: N doubles, host or
+ * device; iters (nullable): the iterations run. Returns QPR_OK,
+ * QPR_E_NOT_CONVERGED (pi then holds the last iterate), QPR_E_NONFINITE,
+ * QPR_E_ARG (tol <= 0, max_iter < 1, pi NULL), QPR_E_CUDA.
+ *
+ * qpr_hub_classes: classes[i] = 2 for a main hub (p_i > c/N), 1 for a
+ * secondary hub (1/N < p_i <= c/N; the text leaves the side of the
+ * equalities open), 0 otherwise, for any probability vector p of the
+ * context's N nodes (the populations from qpr_populations, or pi). p: N
+ * doubles, host or device; classes (nullable): N int32, host or device;
+ * counts (nullable, host): the number of nodes in classes 0, 1, 2. c >= 1.
+ * Returns QPR_OK, QPR_E_ARG, QPR_E_CUDA. */
+QPR_API qpr_status qpr_pagerank(qpr_ctx *ctx, double tol, int64_t max_iter, double *pi, int64_t *iters);
+QPR_API qpr_status qpr_hub_classes(qpr_ctx *ctx, const double *p, double c, int32_t *classes, int64_t *counts);
+
 /* ---- many problems in one batched run ----
  * One problem of a batch: a weighted edge list (as in qpr_create), its own
  * omega, and its density matrix rho (N x N complex128, host or device),

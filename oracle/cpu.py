@@ -71,6 +71,12 @@ def _load():
         lib.oracle_steady_state.restype = ip
         lib.oracle_steady_state.argtypes = [vp, vp, f64, f64, i64, ctypes.POINTER(i64),
                                             ctypes.POINTER(f64), vp]
+        lib.oracle_rkf45.restype = ip
+        lib.oracle_rkf45.argtypes = [vp, vp, f64, f64, f64, f64, f64, i64, ctypes.POINTER(i64),
+                                     ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64),
+                                     ctypes.POINTER(f64), vp, i64]
+        lib.oracle_rkf45_step.restype = f64
+        lib.oracle_rkf45_step.argtypes = [vp, vp, f64, vp, vp]
         lib.oracle_set_threads.argtypes = [ip]
         lib.oracle_max_threads.restype = ip
         _lib = lib
@@ -170,6 +176,37 @@ class Oracle:
         if history:
             out = out + (hist[: int(steps.value) + 1],)
         return out
+
+    def rkf45(self, rho0: np.ndarray, h0: float, step_tol: float, h_max: float, resid_tol: float = 0.0,
+              t_end: float = float("inf"), max_steps: int = 10**7, history: bool = False, hist_cap: int = 200000):
+        """Adaptive RKF45 (Supplementary Note 2, Eq. S10 - S13; readings in
+        qpr_oracle.c). Returns a dict: rho, accepted, rejected, t, h (the next
+        attempt's step), residual, status, and with ``history`` an array of
+        (t, h, discrepancy, s, accepted) per attempt."""
+        y = np.array(rho0, dtype=np.complex128, order="C", copy=True)
+        acc, rej = ctypes.c_int64(0), ctypes.c_int64(0)
+        t, h, r = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        hist = np.zeros((hist_cap, 5)) if history else None
+        st = self._lib.oracle_rkf45(self._h, _ptr(y), float(h0), float(step_tol), float(h_max), float(resid_tol),
+                                    float(t_end), int(max_steps), ctypes.byref(acc), ctypes.byref(rej),
+                                    ctypes.byref(t), ctypes.byref(h), ctypes.byref(r),
+                                    _ptr(hist) if history else None, int(hist_cap) if history else 0)
+        if st not in (OR_OK, OR_E_NOT_CONVERGED):
+            raise OracleError(st, "rkf45")
+        out = {"rho": y, "accepted": int(acc.value), "rejected": int(rej.value), "t": float(t.value),
+               "h": float(h.value), "residual": float(r.value), "status": int(st)}
+        if history:
+            out["history"] = hist[: min(hist_cap, out["accepted"] + out["rejected"])]
+        return out
+
+    def rkf45_step(self, rho: np.ndarray, h: float):
+        """One RKF45 attempt without step-size control from rho (used as
+        given): (y_{k+1} of Eq. S11, z_{k+1} of Eq. S12, |z - y|)."""
+        rho = np.ascontiguousarray(rho, dtype=np.complex128)
+        y4 = np.empty_like(rho)
+        z5 = np.empty_like(rho)
+        err = self._lib.oracle_rkf45_step(self._h, _ptr(rho), float(h), _ptr(y4), _ptr(z5))
+        return y4, z5, float(err)
 
 
 def prepare(rho: np.ndarray) -> np.ndarray:

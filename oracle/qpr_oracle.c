@@ -29,6 +29,13 @@
  *     followed by division by Re tr y;
  *   - residual r = ||f(y)||_F over all N^2 complex entries; the steady-state
  *     loop stops at the first step index n whose r_n < tol.
+ *   - the adaptive RKF45 scheme of Supplementary Note 2 (oracle_rkf45): the
+ *     six stages of Eq. S10, the fourth-order solution y of Eq. S11 and the
+ *     fifth-order solution z of Eq. S12 (the printed 845/4101 and 2197/4101
+ *     read as 845/4104 and 2197/4104, the values that make the stage rows sum
+ *     to their nodes and the weights of Eq. S11 sum to one), and the step
+ *     factor s of Eq. S13. Readings where the note is silent are listed at
+ *     oracle_rkf45.
  *
  * The initial state is first made exactly Hermitian, (rho + rho^dag)/2,
  * and divided by its real trace.
@@ -64,6 +71,9 @@ typedef struct {
     int64_t self_loops, zero_weights;
     /* work buffers for RK4 (n*n complex each) */
     cplx *k, *acc, *tmp;
+    /* work buffers for RKF45, allocated on first use: k1..k6, the stage
+     * input, the fourth- and fifth-order solutions (n*n complex each) */
+    cplx *rk[6], *rin, *ry, *rz;
 } oracle_t;
 
 void oracle_set_threads(int t) {
@@ -87,6 +97,8 @@ void oracle_free(oracle_t *o) {
     free(o->A); free(o->H); free(o->G); free(o->c);
     free(o->h_ptr); free(o->h_col); free(o->h_val);
     free(o->k); free(o->acc); free(o->tmp);
+    for (int i = 0; i < 6; ++i) free(o->rk[i]);
+    free(o->rin); free(o->ry); free(o->rz);
     free(o);
 }
 
@@ -316,4 +328,161 @@ int oracle_steady_state(oracle_t *o, cplx *rho, double dt, double tol, int64_t m
         if (s == max_steps) return OR_E_NOT_CONVERGED;
         rk4_finish(o, rho, dt);
     }
+}
+
+/* ---- RKF45, Supplementary Note 2 (Eq. S10 - S13) ----
+ *
+ * The coefficients of Eq. S10 (stage inputs), Eq. S11 (fourth order) and
+ * Eq. S12 (fifth order), written as the note prints them, with the two
+ * garbled 4101 denominators read as 4104. */
+static const double RKF_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+static const double RKF_Y[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+static const double RKF_Z[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+static int rkf_alloc(oracle_t *o) {
+    if (o->rin) return 1;
+    const size_t nn = (size_t)o->n * (size_t)o->n;
+    for (int i = 0; i < 6; ++i) o->rk[i] = (cplx *)malloc(nn * sizeof(cplx));
+    o->rin = (cplx *)malloc(nn * sizeof(cplx));
+    o->ry = (cplx *)malloc(nn * sizeof(cplx));
+    o->rz = (cplx *)malloc(nn * sizeof(cplx));
+    int ok = o->rin && o->ry && o->rz;
+    for (int i = 0; i < 6; ++i) ok = ok && o->rk[i];
+    if (!ok) {
+        for (int i = 0; i < 6; ++i) { free(o->rk[i]); o->rk[i] = NULL; }
+        free(o->rin); free(o->ry); free(o->rz);
+        o->rin = o->ry = o->rz = NULL;
+    }
+    return ok;
+}
+
+/* One attempt of step h from y_k (Eq. S10 - S12), with f(y_k) already in
+ * o->k: k1 = h f(y_k), k_s = h f(y_k + sum_j a_sj k_j), then y_{k+1} into
+ * o->ry, z_{k+1} into o->rz. Returns the discrepancy |z_{k+1} - y_{k+1}|,
+ * read as the largest modulus over the N^2 entries. */
+static double rkf_attempt(oracle_t *o, const cplx *y, double h) {
+    const size_t nn = (size_t)o->n * (size_t)o->n;
+    for (size_t q = 0; q < nn; ++q) o->rk[0][q] = h * o->k[q];
+    for (int s = 1; s < 6; ++s) {
+        for (size_t q = 0; q < nn; ++q) {
+            cplx v = y[q];
+            for (int j = 0; j < s; ++j) v += RKF_A[s][j] * o->rk[j][q];
+            o->rin[q] = v;
+        }
+        oracle_rhs(o, o->rin, o->rk[s]);
+        for (size_t q = 0; q < nn; ++q) o->rk[s][q] *= h;
+    }
+    double err = 0.0;
+    for (size_t q = 0; q < nn; ++q) {
+        cplx yv = y[q], zv = y[q];
+        for (int j = 0; j < 6; ++j) {
+            yv += RKF_Y[j] * o->rk[j][q];
+            zv += RKF_Z[j] * o->rk[j][q];
+        }
+        o->ry[q] = yv;
+        o->rz[q] = zv;
+        const double d = cabs(zv - yv);
+        if (d > err || isnan(d)) err = d;
+    }
+    return err;
+}
+
+/* Adaptive RKF45 on rho in place (Supplementary Note 2, Eq. S10 - S13).
+ *
+ * Each attempt from the current state y_k with step h forms k1..k6, the
+ * fourth-order y_{k+1} and the fifth-order z_{k+1}, and the factor
+ * s = (step_tol h / (2 |z_{k+1} - y_{k+1}|))^(1/4) of Eq. S13; the next
+ * attempt uses s h. Readings where the note is silent:
+ *   - |.| is the largest modulus of the N^2 complex entries of z - y;
+ *   - an attempt is accepted when |z_{k+1} - y_{k+1}| <= step_tol h (a
+ *     discrepancy within the tolerance per unit time), and then y_{k+1}, the
+ *     fourth-order solution that Eq. S11 defines as the approximation, is
+ *     the new state; otherwise the state is kept and the attempt is repeated
+ *     with s h;
+ *   - s is clipped to [1/10, 4] and s h to h_max (a discrepancy of zero
+ *     gives the largest factor), and in a trajectory the last step is
+ *     shortened to end exactly at t_end;
+ *   - after every accepted step the state is divided by its real trace, as
+ *     in the fixed-step RK4 of this file.
+ * Stops at the first accepted state y_k with ||f(y_k)||_F < resid_tol
+ * (steady state; resid_tol = 0 never stops this way), when the integrated
+ * time reaches t_end (trajectory; INFINITY for none), or after max_steps
+ * accepted steps (OR_E_NOT_CONVERGED in steady-state mode). The initial
+ * state is prepared as in oracle_evolve. Outputs (nullable): accepted and
+ * rejected attempts, the time reached, the step size the next attempt would
+ * use, the residual of the returned state; hist (nullable, 5 doubles per
+ * attempt, at most hist_cap attempts): t, h, discrepancy, s, accepted. */
+int oracle_rkf45(oracle_t *o, cplx *rho, double h0, double step_tol, double h_max, double resid_tol, double t_end,
+                 int64_t max_steps, int64_t *accepted_out, int64_t *rejected_out, double *t_out, double *h_out,
+                 double *resid_out, double *hist, int64_t hist_cap) {
+    if (!(h0 > 0.0) || !(step_tol > 0.0) || !(h_max > 0.0) || !(resid_tol >= 0.0) || max_steps < 0 ||
+        !(t_end > 0.0))
+        return OR_E_ARG;
+    double tr = oracle_prepare(o->n, rho);
+    if (!(tr > 0.0) || !isfinite(tr)) return OR_E_ARG;
+    if (!rkf_alloc(o)) return OR_E_OOM;
+    const int64_t n = o->n;
+    const size_t nn = (size_t)n * (size_t)n;
+    double h = h0 < h_max ? h0 : h_max, t = 0.0, r = 0.0;
+    int64_t acc = 0, rej = 0, na = 0;
+    int status = OR_OK;
+    oracle_rhs(o, rho, o->k);
+    r = oracle_frobenius(n, o->k);
+    for (;;) {
+        if (!isfinite(r)) { status = OR_E_NONFINITE; break; }
+        if (resid_tol > 0.0 && r < resid_tol) break;
+        if (t >= t_end) break;
+        if (acc >= max_steps) { status = (resid_tol > 0.0) ? OR_E_NOT_CONVERGED : OR_OK; break; }
+        const double hs = (t + h > t_end) ? t_end - t : h;
+        const double err = rkf_attempt(o, rho, hs);
+        if (!isfinite(err)) { status = OR_E_NONFINITE; break; }
+        double sfac = (err > 0.0) ? pow(step_tol * hs / (2.0 * err), 0.25) : 4.0;
+        if (sfac < 0.1) sfac = 0.1;
+        if (sfac > 4.0) sfac = 4.0;
+        const int ok = err <= step_tol * hs;
+        if (hist && na < hist_cap) {
+            double *e = hist + 5 * na;
+            e[0] = t; e[1] = hs; e[2] = err; e[3] = sfac; e[4] = ok ? 1.0 : 0.0;
+        }
+        ++na;
+        if (ok) {
+            memcpy(rho, o->ry, nn * sizeof(cplx));
+            double trc = 0.0;
+            for (int64_t a = 0; a < n; ++a) trc += creal(rho[a * n + a]);
+            for (size_t q = 0; q < nn; ++q) rho[q] /= trc;
+            t = (t + hs > t_end) ? t_end : t + hs;
+            ++acc;
+            oracle_rhs(o, rho, o->k);
+            r = oracle_frobenius(n, o->k);
+        } else {
+            ++rej;
+        }
+        h = sfac * hs;
+        if (h > h_max) h = h_max;
+    }
+    if (accepted_out) *accepted_out = acc;
+    if (rejected_out) *rejected_out = rej;
+    if (t_out) *t_out = t;
+    if (h_out) *h_out = h;
+    if (resid_out) *resid_out = r;
+    return status;
+}
+
+/* One RKF45 attempt of step h from rho (prepared as in oracle_evolve) with
+ * no step-size control: y_{k+1} (Eq. S11) into y4 and z_{k+1} (Eq. S12)
+ * into z5 (each nullable); returns the discrepancy |z - y| (largest modulus). */
+double oracle_rkf45_step(oracle_t *o, const cplx *rho, double h, cplx *y4, cplx *z5) {
+    if (!rkf_alloc(o)) return NAN;
+    const size_t nn = (size_t)o->n * (size_t)o->n;
+    oracle_rhs(o, rho, o->k);
+    const double err = rkf_attempt(o, rho, h);
+    if (y4) memcpy(y4, o->ry, nn * sizeof(cplx));
+    if (z5) memcpy(z5, o->rz, nn * sizeof(cplx));
+    return err;
 }

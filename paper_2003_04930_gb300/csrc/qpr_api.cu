@@ -1275,4 +1275,64 @@ qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *ra
     return QPR_OK;
 }
 
+qpr_status qpr_pagerank(qpr_ctx *ctx, double tol, int64_t max_iter, double *pi, int64_t *iters) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!pi) return fail(ctx, QPR_E_ARG, "pi is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return fail(ctx, QPR_E_ARG, "tol must be positive and max_iter >= 1");
+    const int64_t n = ctx->n;
+    // scratch: the host staging buffer (2 n^2 doubles >= 2 n + grid for n >= 2)
+    if ((size_t)2 * n * n < (size_t)(2 * n + qpr::pagerank_grid((int)n)))
+        return fail(ctx, QPR_E_ARG, "n too small for the staging buffer");
+    int64_t it = 0;
+    double delta = 0.0;
+    QPR_CUDA(ctx, qpr::pagerank(ctx->ops, tol, max_iter, ctx->d_io, ctx->d_p, &it, &delta, ctx->stream));
+    ctx->launches += 2 + it;
+    if (is_device_ptr(pi)) {
+        QPR_CUDA(ctx, cudaMemcpyAsync(pi, ctx->d_p, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        QPR_CUDA(ctx, cudaMemcpyAsync(pi, ctx->d_p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (iters) *iters = it;
+    if (!std::isfinite(delta)) return fail(ctx, QPR_E_NONFINITE, "non-finite PageRank iterate");
+    if (delta >= tol)
+        return fail(ctx, QPR_E_NOT_CONVERGED, "max_iter reached with L1 change " + std::to_string(delta));
+    return QPR_OK;
+}
+
+qpr_status qpr_hub_classes(qpr_ctx *ctx, const double *p, double c, int32_t *classes, int64_t *counts) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!p) return fail(ctx, QPR_E_ARG, "p is NULL");
+    if (!(c >= 1.0) || !std::isfinite(c)) return fail(ctx, QPR_E_ARG, "c must be finite and at least 1");
+    const int64_t n = ctx->n;
+    const double *src = p;
+    if (!is_device_ptr(p)) {
+        QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_p, p, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->d_p;
+    }
+    // the classes and the counts in the staging buffer (2 n^2 doubles)
+    int *d_cls = reinterpret_cast<int *>(ctx->d_io);
+    unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(ctx->d_io + (n + 1) / 2 + 1);
+    QPR_CUDA(ctx, qpr::hub_classes(src, (int)n, c, d_cls, d_cnt, ctx->stream));
+    ctx->launches += 1;
+    unsigned long long cnt[3] = {0, 0, 0};
+    QPR_CUDA(ctx, cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
+    if (classes) {
+        const cudaMemcpyKind kind = is_device_ptr(classes) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        QPR_CUDA(ctx, cudaMemcpyAsync(classes, d_cls, n * sizeof(int32_t), kind, ctx->stream));
+    }
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (counts)
+        for (int k = 0; k < 3; ++k) counts[k] = (int64_t)cnt[k];
+    return QPR_OK;
+}
+
 }  // extern "C"

@@ -266,6 +266,21 @@ constexpr int kMixedLaunchesPerRefresh = 5;
 // refreshes, in multiples of ref_refresh.
 constexpr int kMaxRefreshGrowth = 8;
 
+// ---- classical PageRank and hub classes (pagerank.cu) ----
+// CTAs of one power-iteration kernel for n nodes.
+int pagerank_grid(int n);
+// Power iteration pi <- G pi / sum(pi) from the uniform vector until the L1
+// change of an iteration (checked every 8) is below tol or after max_iter
+// iterations; pi (normalised) into pi_out_dev (n doubles). scratch: device,
+// 2 n + pagerank_grid(n) doubles. Synchronises the stream.
+cudaError_t pagerank(const DevOps &ops, double tol, int64_t max_iter, double *scratch, double *pi_out_dev,
+                     int64_t *iters, double *delta_out, cudaStream_t s);
+// classes_dev[i] in {0, 1, 2} (rest, secondary hub, main hub) of the
+// probabilities p (device, n doubles) with threshold factor c; counts_dev
+// (3 values) receives the class sizes.
+cudaError_t hub_classes(const double *p, int n, double c, int *classes_dev, unsigned long long *counts_dev,
+                        cudaStream_t s);
+
 // ---- host assembly (qpr_api.cu) ----
 struct HostOps {
     int64_t n = 0;

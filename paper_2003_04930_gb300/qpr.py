@@ -31,7 +31,7 @@ EXPORTED = (
     "qpr_n", "qpr_backend", "qpr_sparse_form", "qpr_sparse_plan", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
-    "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune",
+    "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune", "qpr_pagerank", "qpr_hub_classes",
 )
 QPR_NOALLOC_MAX_N = 256
 
@@ -159,6 +159,10 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_autotune.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
+    lib.qpr_pagerank.argtypes = [vp, f64, i64, vp, ctypes.POINTER(i64)]
+    lib.qpr_pagerank.restype = st
+    lib.qpr_hub_classes.argtypes = [vp, vp, f64, vp, vp]
+    lib.qpr_hub_classes.restype = st
     _lib = lib
     return lib
 
@@ -322,6 +326,23 @@ class Solver:
         rank = np.zeros(self.n, dtype=np.int64) if with_rank else None
         self._raise(self._lib.qpr_populations(self._h, _ptr(rho), _ptr(p), _ptr(rank)))
         return (p, rank) if with_rank else p
+
+    def pagerank(self, tol: float = 1e-14, max_iter: int = 100000, out=None):
+        """qpr_pagerank: the classical PageRank vector of the graph (NumPy
+        array, or `out` if given: a float64 tensor or array of N entries)."""
+        pi = np.zeros(self.n) if out is None else out
+        it = ctypes.c_int64(0)
+        self._raise(self._lib.qpr_pagerank(self._h, float(tol), int(max_iter), _ptr(pi), ctypes.byref(it)))
+        self.last_pagerank_iters = int(it.value)
+        return pi
+
+    def hub_classes(self, p, c: float = 10.0):
+        """qpr_hub_classes: (classes, counts) of a probability vector p (host
+        array or device tensor of N float64); classes is an int32 array."""
+        cls = np.zeros(self.n, dtype=np.int32)
+        counts = np.zeros(3, dtype=np.int64)
+        self._raise(self._lib.qpr_hub_classes(self._h, _ptr(p), float(c), _ptr(cls), _ptr(counts)))
+        return cls, counts
 
     def profile_step(self, rho, dt: float, steps: int):
         """qpr_profile_step: each kernel of `steps` RK4 steps run alone
