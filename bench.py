@@ -435,9 +435,11 @@ def form_name(s, prec):
 
 
 # DRAM bytes per launch of the current kernels from one ncu capture each
-# (`dram__bytes_read.sum + dram__bytes_write.sum`, the commands in profiles/),
-# keyed by (kernel, N); a kernel changed since its capture has no entry.
-NCU_TRAFFIC = {}
+# (`dram__bytes_read.sum + dram__bytes_write.sum` of the stage-1 launch,
+# profiles/traffic_cols_n922_n4096.md), keyed by (kernel, N); a kernel
+# changed since its capture has no entry.
+NCU_TRAFFIC = {("cols_spmm_kernel", 922): 7033000, ("cols_epi_kernel", 922): 14043000,
+               ("cols_gather_kernel", 4096): 135267000 + 99186000, ("cols_epi_kernel", 4096): 269651000 + 101275000}
 
 
 def roofline(s, g, n, prof, peaks, peak_src, prec):

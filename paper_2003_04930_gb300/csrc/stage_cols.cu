@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "cols_body.cuh"
+#include "cols_spmm.cuh"
 #include "qpr_internal.cuh"
 #include "tma_util.cuh"
 
@@ -24,112 +25,15 @@ namespace {
 
 using namespace cols;
 
-// Launched with programmatic dependent launch: the prologue (barriers, this
-// CTA's CSR entries and bundles, which no kernel writes) overlaps the end of
-// the previous kernel; the stage input is read after grid_dependency_wait.
 template <int STAGE>
 __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
                                                          MixedWork w) {
-    extern __shared__ uint8_t dyn_raw[];
-    __shared__ __align__(8) uint64_t bar_csr, bar_d;
-    __shared__ int s_done;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int J = blockIdx.x, r = blockIdx.y, np = ops.np;
-    const uint32_t s0 = tma::smem_u32(dyn_raw);
-    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);  // 128-byte aligned, shared provenance kept
-    float *sD = reinterpret_cast<float *>(base);
-    int2 *sKH = reinterpret_cast<int2 *>(base + (size_t)np * kRowFloats * 4);
-    int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
-    const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
-    const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
-    const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);  // an even count of entries
-    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * kBundleInt4);
-    if (tid == 0) {
-        tma::mbar_init(&bar_csr, 1);
-        tma::mbar_init(&bar_d, 1);
-        tma::mbar_init_fence();
-        tma::mbar_expect_tx(&bar_csr, kh_bytes + p_bytes);
-        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar_csr);
-        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + kBundleInt4 * (size_t)p_base, p_bytes, &bar_csr);
-    }
-    const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
-    tma::grid_dependency_wait();
-    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) {
-        tma::mbar_wait(&bar_csr, 0);  // the copies in flight land before the CTA leaves (bounded)
-        return;
-    }
-    tma::launch_dependents();
-    if (tid == 0) {
-        tma::mbar_expect_tx(&bar_d, (uint32_t)np * kRowFloats * 4);
-        for (int b = 0; b < np; b += kBoxRows)
-            tma::load_3d(sD + (size_t)b * kRowFloats, &tm, &bar_d, J * kCW, 0, b);
-    }
-    const bool ok = tma::mbar_wait(&bar_csr, 0) && tma::mbar_wait(&bar_d, 0);
-    if (__syncthreads_or(!ok)) {
-        // bounded wait gave up: report, give the copies one more bounded wait, return
-        if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
-        tma::mbar_wait(&bar_csr, 0);
-        tma::mbar_wait(&bar_d, 0);
-        return;
-    }
-    float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-    warp_bundles(sD, sKH, sP, p_base, wb0, wb1, J, np, w.X, parts);
-    const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
-    if (cb1 > cb0) {
-        __syncthreads();
-        combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, np, w.X);
-    }
+    spmm_block_body([&] { return &tm; }, ops, w, blockIdx.x, blockIdx.y);
 }
 
-// Gather form of the SpMM, for N too large to stage a column block: CTA
-// (r, J) stages only its split's entries and bundles and reads each
-// nonzero's 32 values of the 32-column block J straight from the stage input
-// (one 128-byte line per plane and row, L1-cached loads; the wide layout of
-// warp_bundles: a group pair per row). The grid runs the row splits of one
-// column block next to each other, so the block's rows (np x 128 bytes) are
-// read from DRAM about once and then served by L2 to the splits.
 template <int STAGE>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(DevOps ops, MixedWork w) {
-    extern __shared__ uint8_t dyn_raw[];
-    __shared__ __align__(8) uint64_t bar_csr;
-    __shared__ int s_done;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int r = blockIdx.x, J = blockIdx.y;
-    const uint32_t s0 = tma::smem_u32(dyn_raw);
-    uint8_t *base = dyn_raw + (((s0 + 127) & ~127u) - s0);
-    int2 *sKH = reinterpret_cast<int2 *>(base);
-    int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
-    const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
-    const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
-    const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);
-    const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * kBundleInt4);
-    if (tid == 0) {
-        tma::mbar_init(&bar_csr, 1);
-        tma::mbar_init_fence();
-        tma::mbar_expect_tx(&bar_csr, kh_bytes + p_bytes);
-        if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar_csr);
-        if (p_bytes) tma::load_bulk(sP, ops.col_pieces + kBundleInt4 * (size_t)p_base, p_bytes, &bar_csr);
-    }
-    const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
-    tma::grid_dependency_wait();
-    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    const bool ok = tma::mbar_wait(&bar_csr, 0);  // also before leaving: the copies land first (bounded)
-    if (s_done) return;
-    tma::launch_dependents();
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
-        return;
-    }
-    float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
-    warp_bundles<true, true>(stage_input<STAGE>(w), sKH, sP, p_base, wb0, wb1, J, ops.np, w.X, parts);
-    const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
-    if (cb1 > cb0) {
-        __syncthreads();
-        combine_cuts<true>(ops.col_cut + cb0, cb1 - cb0, parts, J, ops.np, w.X);
-    }
+    spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, blockIdx.x, blockIdx.y);
 }
 
 // The gain of the stage input, rows shared over the grid; runs beside the
