@@ -347,6 +347,10 @@ def run_ours(a):
             "residual": stats[-1]["residual"], "roofline": roof, "profile_ms": prof, "clocks": clocks,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats))}
 
+    # the paper's own integrator: adaptive RKF45 (Supplementary Note 2) on the same problem and stop rule
+    if prec == qpr.QPR_MIXED and s.sparse_form in (qpr.QPR_SPARSE_FORM_COLUMNS, qpr.QPR_SPARSE_FORM_COLUMNS_GATHER):
+        line["rkf45"] = rkf45_solve(s, a, rho0, rho_solved, flush, max(1, a.steps), value, steps_conv)
+
     # the main text's comparison of the quantum and the classical ranking: hub classes (c = 10) of the
     # steady-state populations and of the classical PageRank vector, both on the GPU
     line["hubs"] = hub_report(s, rho_solved)
@@ -394,6 +398,37 @@ def run_ours(a):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def rkf45_solve(s, a, rho0, rho_ref, flush, reps, rk4_value, rk4_steps, step_tol=1e-6):
+    """qpr_rkf45 to the same residual tolerance from the same start (h0 =
+    dt, Tol = 1e-6, h_max = the RK4 stability estimate), one untimed solve
+    then `reps` timed with CUDA events; the difference of its steady state
+    from the fixed-step RK4 one (both stop at ||f||_F < tol, so they differ by
+    up to about tol over the spectral gap)."""
+    import torch
+    rho = torch.empty_like(rho0)
+    rho.copy_(rho0)
+    s.rkf45(rho, tol=a.tol, max_steps=a.max_steps, h0=a.dt, step_tol=step_tol)
+    ts, st = [], None
+    for _ in range(reps):
+        rho.copy_(rho0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = s.rkf45(rho, tol=a.tol, max_steps=a.max_steps, h0=a.dt, step_tol=step_tol)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.mean(ts)
+    p, pr = torch.diagonal(rho).real, torch.diagonal(rho_ref).real
+    return {"time_to_steady_state_s": t, "accepted_steps": st["accepted"], "rejected": st["rejected"],
+            "t": st["t"], "h_final": st["h_next"], "h_max": s.max_stable_dt, "step_tol": step_tol,
+            "residual": st["residual"], "gpu_launches": st["kernel_launches"],
+            "rk4_steps": rk4_steps, "rk4_time_s": rk4_value, "speedup_vs_rk4": rk4_value / t,
+            "max_dp_rel_vs_rk4": float((p - pr).abs().max() / pr.abs().max()),
+            "form": "mixed column-block form, six powers of h L per attempt, controller on the device"}
 
 
 def hub_report(s, rho_ss, c=10.0, top=10):
@@ -614,6 +649,7 @@ def large_case(a, local, peaks, peak_src, flush):
     ws = warm_solve(s, g, la.omega, la, local, rho, flush, 1)
     if ws is not None:
         out["warm_start"] = ws
+    out["rkf45"] = rkf45_solve(s, la, rho0, rho_solved, flush, 1, t_cold, st["steps"])
     s.close()
     out["fp64_sparse"] = fp64_sparse_solve(g, la, local, rho0, rho_solved, flush, warm=False)
     out["plain_fp64_dense"] = dense_projection(g, la.omega, local, rho_solved, la.dt, st["steps"], peaks, peak_src,

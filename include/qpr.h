@@ -254,6 +254,58 @@ QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, in
  * ties to the lower index (the ranking of the main text's airline study). */
 QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *rank);
 
+/* ---- adaptive RKF45 (the paper's own integrator) ----
+ * The RKF45 scheme of Supplementary Note 2: per attempt of step h the six
+ * stages of Eq. S10, the fourth-order solution y_{k+1} (Eq. S11) and the
+ * fifth-order solution z_{k+1} (Eq. S12), with the printed 845/4101 and
+ * 2197/4101 read as 845/4104 and 2197/4104 (the values for which each stage
+ * row sums to its node and the weights of Eq. S11 sum to one), and the step
+ * factor s = (Tol h / (2 |z_{k+1} - y_{k+1}|))^(1/4) of Eq. S13. Readings
+ * where the note is silent: |.| is the largest modulus over the N^2 entries;
+ * an attempt is accepted when |z - y| <= Tol h, and y_{k+1} becomes the
+ * state; after every attempt h <- min(s h, h_max) with s clipped to
+ * [1/10, 4]; a trajectory's last step ends exactly at t_end.
+ * Computed in the mixed delta form of QPR_MIXED on the column-block sparse
+ * stage (COLUMNS, COLUMNS_PERSISTENT or COLUMNS_GATHER; else QPR_E_ARG): f is
+ * linear, so an attempt is the polynomial P4(hL) (y) and the discrepancy
+ * (P5 - P4)(hL) y, formed from the six powers (hL)^k y in FP32 with the
+ * state in float-float against the exact FP64 reference; the step-size
+ * controller runs on the device; the state is renormalised at every exact
+ * refresh (each block of ref_refresh attempts). The paper has no
+ * tolerance; Tol and h_max are the caller's. */
+typedef struct {
+    double h0;       /* first step (<= 0: 0.01; clipped to h_max) */
+    double step_tol; /* Tol of Eq. S13 (<= 0: 1e-6) */
+    double h_max;    /* largest step (<= 0: qpr_max_stable_dt(ctx), the RK4 stability estimate, which also
+                        keeps RKF45's fourth-order solution stable on these problems) */
+    double t_end;    /* > 0: integrate the trajectory to this time; <= 0: solve for the steady state */
+    int32_t reserved[4];
+} qpr_rkf45_options;
+
+typedef struct {
+    int64_t accepted;        /* accepted steps (the state's step index) */
+    int64_t rejected;        /* rejected attempts */
+    double t;                /* integrated time */
+    double h_next;           /* the step the next attempt would take */
+    double residual;         /* ||f(rho)||_F of the returned state (FP64, exact) */
+    double last_discrepancy; /* |z - y| of the last attempt */
+    double seconds;          /* wall time of the call */
+    int64_t kernel_launches;
+    int32_t converged;       /* 1: steady state below tol, or t_end reached */
+    int32_t reserved[3];
+} qpr_rkf45_stats;
+
+/* RKF45 from the state in rho (host or device, overwritten with the result,
+ * unit trace). Steady state (opt->t_end <= 0): until the first accepted state
+ * with ||f||_F < tol, confirmed in FP64, or max_steps accepted steps.
+ * Trajectory (t_end > 0): to time t_end (tol ignored), at most max_steps
+ * accepted steps. Attempts are bounded by 16 max_steps + 64 ref_refresh.
+ * Returns QPR_OK, QPR_E_NOT_CONVERGED, QPR_E_NONFINITE, QPR_E_ARG,
+ * QPR_E_TIMEOUT, QPR_E_CUDA, QPR_E_OOM (the first call allocates the form's
+ * extra buffers). opt and out may be NULL. */
+QPR_API qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, double tol, int64_t max_steps,
+                             qpr_rkf45_stats *out);
+
 /* ---- classical PageRank and hub classes ----
  * The main text compares the quantum PageRank ranking of the airline network
  * with the classical PageRank and sorts nodes into hubs (its airline-ranking

@@ -226,17 +226,19 @@ __device__ __forceinline__ const float *stage_input(const MixedWork &w) {
 }
 
 // The gain g = G p(delta) of rows [b np / nb, (b + 1) np / nb) (CTA b of
-// nb), from the compact diagonal p = w.pv of the stage input (written by the
-// previous epilogue): p is staged in shared memory (sp: np floats) with one
+// nb), from the compact diagonal p = w.pv (or pv_in) of the stage input
+// (written by the previous epilogue): p is staged in shared memory (sp: np floats) with one
 // coalesced round trip, together with the rows' S entries. The sums are
 // those of gain_rows on the strided diagonal, in the same order.
-__device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, int b, int nb, float *sp) {
+__device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, int b, int nb, float *sp,
+                                         const float *pv_in = nullptr) {
+    const float *pv = pv_in ? pv_in : w.pv;
     __shared__ float red[32];
     const int n = ops.n, np = ops.np;
     const int r0 = (int)((long long)b * np / nb), r1 = (int)((long long)(b + 1) * np / nb);
     float P = 0.f, Dd = 0.f;
     for (int j = threadIdx.x; j < np; j += blockDim.x) {
-        const float pj = __ldcg(w.pv + j);
+        const float pj = __ldcg(pv + j);
         sp[j] = pj;
         if (j < n) {
             P = __fadd_rn(P, pj);

@@ -357,6 +357,22 @@ __device__ __forceinline__ bool stage2_decide(const MixedWork &w, bool first) {
     return s_status != kCtlRunning;
 }
 
+// f(delta)_ab of the Lindblad right-hand side (Eq. 1) in FP32 from the
+// products X = H delta at (a, b) (Aab + i Bab) and at (b, a) (Aba + i Bba),
+// the element delta_ab = dr + i di, the column sums c_a and c_b of G and, on
+// the diagonal, the gain g_a = (G p(delta))_a:
+//   (1 - omega)[(Bab + Bba) - i (Aab - Aba)] + omega[delta_ab g_a - (c_a + c_b)/2 delta_ab].
+// Explicit round-to-nearest intrinsics: the same rounding in every kernel
+// inlining this code.
+__device__ __forceinline__ void lindblad_elem(float om, float cm, float ca, float cb, float Aab, float Bab, float Aba,
+                                              float Bba, float dr, float di, bool on_diag, float ga, float &kdr,
+                                              float &kdi) {
+    const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(ca, cb)));
+    kdr = __fmaf_rn(-omhc, dr, __fmul_rn(cm, __fadd_rn(Bab, Bba)));
+    kdi = __fmaf_rn(-omhc, di, __fmul_rn(-cm, __fsub_rn(Aab, Aba)));
+    if (on_diag) kdr = __fmaf_rn(om, ga, kdr);
+}
+
 // The RK4 step in nested form. f is linear, so the classical step
 // y + dt/6 (k1 + 2 k2 + 2 k3 + k4) equals
 //     y + dt L (y + dt/2 L (y + dt/3 L (y + dt/4 L y)))
@@ -451,12 +467,10 @@ __device__ __forceinline__ void tile_epilogue_in(const DevOps &ops, const MixedW
         const float Aab = sX1[a * LDX + b], Bab = sX1[a * LDX + TS + b];
         const float Aba = X2[b * LDX + a], Bba = X2[b * LDX + TS + a];
         const float dr = in.dr[k], di = in.di[k];
-        // kd = f(delta) in FP32; k = F + kd. Explicit round-to-nearest
-        // intrinsics: the same rounding in every kernel inlining this code.
-        const float omhc = __fmul_rn(om, __fmul_rn(0.5f, __fadd_rn(in.ca[k], in.cb)));
-        float kdr = __fmaf_rn(-omhc, dr, __fmul_rn(cm, __fadd_rn(Bab, Bba)));
-        const float kdi = __fmaf_rn(-omhc, di, __fmul_rn(-cm, __fsub_rn(Aab, Aba)));
-        if (ga == gb) kdr = __fmaf_rn(om, sg[a], kdr);
+        // kd = f(delta) in FP32; k = F + kd
+        float kdr, kdi;
+        lindblad_elem(om, cm, in.ca[k], in.cb, Aab, Bab, Aba, Bba, dr, di, ga == gb, ga == gb ? sg[a] : 0.f, kdr,
+                      kdi);
         if (STAGE <= 3) {
             const float kr = __fadd_rn(kdr, in.ur[k]), ki = __fadd_rn(kdi, in.ui[k]);
             if (STAGE == 1) nrm = __fmaf_rn(kr, kr, __fmaf_rn(ki, ki, nrm));

@@ -59,6 +59,9 @@ struct qpr_ctx {
     Ctl *d_ctl = nullptr;
     double *d_io = nullptr;     // staging for host density matrices (interleaved)
     double *d_p = nullptr;      // populations staging
+    float *d_rkf = nullptr;     // RKF45: D1, Dlo1, acc, Flo (2 planes each), the two compact diagonals
+    cudaGraphExec_t graph_rkf = nullptr;  // RKF45: refresh + ref_refresh attempts
+    double rkf_key[3] = {0, 0, 0};        // h0, Tol, h_max of the captured graph's first block (unused by kernels)
     Ctl *h_ctl = nullptr;       // pinned
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
@@ -363,6 +366,122 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     }
 }
 
+// RKF45 needs the column-block form of the mixed sparse stage: allocate
+// its buffers (the second delta pair, the running sum, the low part of F,
+// the two compact diagonals), its tensor map and kernel attributes on the
+// first call.
+qpr_status ensure_rkf(qpr_ctx *ctx) {
+    if (ctx->opt.precision != QPR_MIXED || !ctx->mw.cmaps)
+        return fail(ctx, QPR_E_ARG, "qpr_rkf45 needs QPR_MIXED with a column-block sparse form "
+                                    "(COLUMNS, COLUMNS_PERSISTENT or COLUMNS_GATHER)");
+    if (ctx->d_rkf) return QPR_OK;
+    const size_t plane = (size_t)ctx->np * ctx->np;
+    QPR_CUDA(ctx, cudaMalloc(&ctx->d_rkf, (8 * plane + 2 * (size_t)ctx->np) * sizeof(float)));
+    QPR_CUDA(ctx, cudaMemsetAsync(ctx->d_rkf, 0, (8 * plane + 2 * (size_t)ctx->np) * sizeof(float), ctx->stream));
+    qpr::MixedWork &mw = ctx->mw;
+    mw.D1 = ctx->d_rkf;
+    mw.Dlo1 = ctx->d_rkf + 2 * plane;
+    mw.acc = ctx->d_rkf + 4 * plane;
+    mw.Flo = ctx->d_rkf + 6 * plane;
+    mw.pvd = ctx->d_rkf + 8 * plane;
+    if (!qpr::make_rkf_map(ctx->ops, mw.D1, &ctx->colmaps)) return fail(ctx, QPR_E_CUDA, "cuTensorMapEncodeTiled failed");
+    QPR_CUDA(ctx, qpr::init_rkf(ctx->ops.col_smem, ctx->ops.col_gather != 0));
+    return QPR_OK;
+}
+
+void enqueue_rkf_block(qpr_ctx *ctx, int attempts) {
+    qpr::launch_rkf_refresh(ctx->ops, ctx->mw, ctx->stream);
+    for (int k = 0; k < attempts; ++k)
+        for (int s = 1; s <= qpr::kRkfStages; ++s) qpr::launch_rkf_stage(s, ctx->ops, ctx->mw, ctx->stream);
+}
+
+qpr_status ensure_rkf_graph(qpr_ctx *ctx) {
+    if (ctx->graph_rkf || ctx->opt.graph_steps <= 0) return QPR_OK;
+    cudaGraph_t g = nullptr;
+    QPR_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_rkf_block(ctx, ctx->opt.ref_refresh);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph_rkf, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph_rkf = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    return QPR_OK;
+}
+
+// Blocks of (exact refresh + ref_refresh RKF45 attempts) until the device
+// stops: the time end of a trajectory, max_steps accepted steps, a
+// non-finite value, or a residual estimate below tol, which an exact
+// refresh confirms (as in run_mixed). The run ends with a refresh, so R
+// holds the returned state. Bounded: at most max_attempts attempts.
+qpr_status run_rkf45(qpr_ctx *ctx, double h0, double step_tol, double hmax, double tend, double tol,
+                     int64_t max_steps, int64_t max_attempts) {
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->max_steps = max_steps;
+    h->tol = tol;
+    h->dt = h0;
+    h->scale = 1.0;
+    h->resid_exact_step = -1;
+    h->rk_h = h0;
+    h->rk_hmax = hmax;
+    h->rk_tol = step_tol;
+    h->rk_tend = tend;
+    h->rk_hf = (float)h0;
+    h->rk_hl = (float)(h0 - (double)(float)h0);
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    qpr_status st = ensure_rkf_graph(ctx);
+    if (st != QPR_OK) return st;
+    const int block = ctx->opt.ref_refresh;
+    int64_t attempts = 0;
+    for (;;) {
+        if (ctx->graph_rkf) {
+            QPR_CUDA(ctx, cudaGraphLaunch(ctx->graph_rkf, ctx->stream));
+        } else {
+            enqueue_rkf_block(ctx, block);
+        }
+        ctx->launches += qpr::kRkfLaunchesPerRefresh + (int64_t)qpr::kRkfLaunchesPerAttempt * block;
+        attempts += block;
+        st = read_ctl(ctx);
+        if (st != QPR_OK) return st;
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait gave up (err_timeout set by a stage kernel)");
+        if (!h->done) {
+            if (attempts >= max_attempts) break;
+            continue;
+        }
+        if (h->status == qpr::kCtlNonFinite) return QPR_OK;
+        if (h->status != qpr::kCtlTimeReached && h->resid_exact_step == h->step) return QPR_OK;
+        // confirm a candidate (or fold the final delta into R) with an exact refresh
+        h->done = 0;
+        const int prev = h->status;
+        h->status = qpr::kCtlRunning;
+        QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+        qpr::launch_rkf_refresh(ctx->ops, ctx->mw, ctx->stream);
+        ctx->launches += qpr::kRkfLaunchesPerRefresh;
+        st = read_ctl(ctx);
+        if (st != QPR_OK) return st;
+        if (h->err_timeout) return fail(ctx, QPR_E_TIMEOUT, "a device-side wait gave up (err_timeout set by a stage kernel)");
+        if (prev == qpr::kCtlTimeReached || prev == qpr::kCtlMaxSteps) {
+            if (h->status != qpr::kCtlNonFinite) h->status = prev;
+            return QPR_OK;
+        }
+        if (h->done) return QPR_OK;  // converged, max steps or non-finite, decided exactly
+        if (attempts >= max_attempts) break;
+    }
+    // attempt budget spent: fold the delta into R and report the state reached
+    h->done = 0;
+    h->status = qpr::kCtlRunning;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    qpr::launch_rkf_refresh(ctx->ops, ctx->mw, ctx->stream);
+    ctx->launches += qpr::kRkfLaunchesPerRefresh;
+    st = read_ctl(ctx);
+    if (st != QPR_OK) return st;
+    if (!h->done) h->status = qpr::kCtlMaxSteps;
+    return QPR_OK;
+}
+
 }  // namespace
 
 namespace qpr {
@@ -607,6 +726,8 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (ctx->colmaps.side) cudaStreamSynchronize(ctx->colmaps.side);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph_c) cudaGraphExecDestroy(ctx->graph_c);
+    if (ctx->graph_rkf) cudaGraphExecDestroy(ctx->graph_rkf);
+    cudaFree(ctx->d_rkf);
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_hptr);
     cudaFree(ctx->d_rowseg);
@@ -1273,6 +1394,57 @@ qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *ra
         }
     }
     return QPR_OK;
+}
+
+qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, double tol, int64_t max_steps,
+                     qpr_rkf45_stats *out) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho) return fail(ctx, QPR_E_ARG, "rho is NULL");
+    qpr_rkf45_options o{};
+    if (opt) o = *opt;
+    const double hmax = o.h_max > 0.0 ? o.h_max : qpr_max_stable_dt(ctx);
+    const double step_tol = o.step_tol > 0.0 ? o.step_tol : 1e-6;
+    const bool traj = o.t_end > 0.0;
+    double h0 = o.h0 > 0.0 ? o.h0 : 0.01;
+    if (!std::isfinite(h0) || !std::isfinite(step_tol) || !(hmax > 0.0) || !std::isfinite(hmax) ||
+        (traj && !std::isfinite(o.t_end)))
+        return fail(ctx, QPR_E_ARG, "h0, step_tol, h_max and t_end must be finite");
+    if (!traj && !(tol > 0.0)) return fail(ctx, QPR_E_ARG, "tol must be positive for a steady-state solve");
+    if (max_steps < 0) return fail(ctx, QPR_E_ARG, "max_steps must be non-negative");
+    h0 = std::min(h0, hmax);
+    if (traj) h0 = std::min(h0, o.t_end);
+    st = ensure_rkf(ctx);
+    if (st != QPR_OK) return st;
+    st = import_state(ctx, rho);
+    if (st != QPR_OK) return st;
+    const int64_t max_attempts = 16 * max_steps + 64 * (int64_t)ctx->opt.ref_refresh;
+    st = run_rkf45(ctx, h0, step_tol, hmax, traj ? o.t_end : 0.0, traj ? 0.0 : tol, max_steps, max_attempts);
+    if (st != QPR_OK) return st;
+    Ctl c = *ctx->h_ctl;
+    st = export_rho(ctx, ctx->mw.R, 0, rho);
+    if (st != QPR_OK) return st;
+    st = sync_ctx(ctx);
+    if (st != QPR_OK) return st;
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->accepted = c.step;
+        out->rejected = c.rk_rejected;
+        out->t = c.rk_t;
+        out->h_next = c.rk_h;
+        out->residual = c.resid_exact;
+        out->last_discrepancy = c.rk_err;
+        out->kernel_launches = ctx->launches;
+        out->converged = (c.status == qpr::kCtlConverged || c.status == qpr::kCtlTimeReached) ? 1 : 0;
+        out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (c.status == qpr::kCtlNonFinite) return fail(ctx, QPR_E_NONFINITE, "non-finite state, residual or discrepancy");
+    if (c.status == qpr::kCtlTimeReached || c.status == qpr::kCtlConverged) return QPR_OK;
+    return fail(ctx, QPR_E_NOT_CONVERGED, traj ? "max_steps reached before t_end"
+                                              : "max_steps reached with residual " + std::to_string(c.resid_exact));
 }
 
 qpr_status qpr_pagerank(qpr_ctx *ctx, double tol, int64_t max_iter, double *pi, int64_t *iters) {

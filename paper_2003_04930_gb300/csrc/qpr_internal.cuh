@@ -44,11 +44,22 @@ struct Ctl {
     // testing only: arrivals a grid barrier waits for beyond its grid (0, or 1
     // to make every barrier wait run out; qpr_options.test_fault)
     unsigned gb_extra, pad3_;
+    // RKF45 (qpr_rkf45): the step of the next attempt and its largest value,
+    // the tolerance Tol of Eq. S13, the integrated time and its end (0: none),
+    // the discrepancy |z - y| of the last attempt, the rejected attempts, the
+    // delta pair holding the current state (0: D, Dlo; 1: D1, Dlo1) and the
+    // step as a float-float pair (hf + hl) for the delta stages
+    double rk_h, rk_hmax, rk_tol, rk_t, rk_tend, rk_err;
+    long long rk_rejected;
+    int rk_cur, rk_pad_;
+    float rk_hf, rk_hl;
 };
 
 // kCtlCandidate: the mixed form's FP32-accurate residual estimate passed;
 // the host confirms it with an exact FP64 refresh.
-enum { kCtlRunning = 0, kCtlConverged = 1, kCtlMaxSteps = 2, kCtlNonFinite = 3, kCtlCandidate = 4 };
+// kCtlTimeReached: an RKF45 trajectory reached its end time.
+enum { kCtlRunning = 0, kCtlConverged = 1, kCtlMaxSteps = 2, kCtlNonFinite = 3, kCtlCandidate = 4,
+       kCtlTimeReached = 5 };
 
 // Operators on the device (built once by qpr_create).
 struct DevOps {
@@ -146,12 +157,19 @@ struct MixedWork {
     // kernel)
     float *X;
     const struct ColMaps *cmaps;
+    // RKF45 in the column-block form (null until the first qpr_rkf45 call):
+    // the second delta pair (D1, Dlo1; the controller's rk_cur selects the
+    // current one), the running sum of the step's power terms (acc, 2
+    // planes), the low part of F as a float-float pair with F32 (Flo, 2
+    // planes), and the compact diagonals of D and D1 (pvd, 2 np)
+    float *D1, *Dlo1, *acc, *Flo, *pvd;
 };
 
 // TMA descriptors of the stage inputs D, da, db for the column-block SpMM:
 // each pair of planes seen as 2 np rows of np FP32, boxes of 8 x 256.
 struct ColMaps {
     CUtensorMap d[3];
+    CUtensorMap d1;  // D1 of the RKF45 form (encoded by its first call)
     // host side: the gain kernel runs on a forked branch beside the SpMM
     cudaStream_t side;
     cudaEvent_t fork, join;
@@ -249,6 +267,18 @@ cudaError_t set_gather_smem(int bytes);
 cudaError_t set_cols_smem(int bytes);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
                        bool serial = false);
+// RKF45 in the column-block form (stage_rkf.cu). One attempt is six
+// stages, each the gain (forked), the SpMM and the epilogue; stage 6 ends with
+// the step-size controller. The refresh folds the current delta into R and
+// recomputes F = f(R) exactly, as the RK4 refresh does.
+constexpr int kRkfStages = 6;
+constexpr int kRkfLaunchesPerAttempt = 3 * kRkfStages;
+bool make_rkf_map(const DevOps &ops, const float *d1, ColMaps *maps);
+void launch_rkf_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s);
+void launch_rkf_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s);
+constexpr int kRkfLaunchesPerRefresh = 5;
+cudaError_t init_rkf(int spmm_smem, bool gather);
+
 // Persistent form (stage_persist.cu): one cooperative launch runs up to
 // `steps` RK4 steps of the column-block form, grid barriers between the
 // phases. persist_grid: CTAs of that launch for an np x np problem with the

@@ -32,6 +32,7 @@ EXPORTED = (
     "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
     "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune", "qpr_pagerank", "qpr_hub_classes",
+    "qpr_rkf45",
 )
 QPR_NOALLOC_MAX_N = 256
 
@@ -65,6 +66,23 @@ class qpr_profile(ctypes.Structure):
     def as_dict(self):
         return {k: getattr(self, k) for k in
                 ("product_ms", "epilogue_ms", "gain_ms", "refresh_ms", "step_ms", "launches_per_step")}
+
+
+class qpr_rkf45_options(ctypes.Structure):
+    _fields_ = [("h0", ctypes.c_double), ("step_tol", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
+class qpr_rkf45_stats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64), ("t", ctypes.c_double),
+                ("h_next", ctypes.c_double), ("residual", ctypes.c_double), ("last_discrepancy", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("converged", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in
+                ("accepted", "rejected", "t", "h_next", "residual", "last_discrepancy", "seconds",
+                 "kernel_launches", "converged")}
 
 
 class qpr_problem(ctypes.Structure):
@@ -159,6 +177,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_autotune.restype = st
     lib.qpr_populations.argtypes = [vp, vp, vp, vp]
     lib.qpr_populations.restype = st
+    lib.qpr_rkf45.argtypes = [vp, vp, ctypes.POINTER(qpr_rkf45_options), f64, i64, ctypes.POINTER(qpr_rkf45_stats)]
+    lib.qpr_rkf45.restype = st
     lib.qpr_pagerank.argtypes = [vp, f64, i64, vp, ctypes.POINTER(i64)]
     lib.qpr_pagerank.restype = st
     lib.qpr_hub_classes.argtypes = [vp, vp, f64, vp, vp]
@@ -326,6 +346,23 @@ class Solver:
         rank = np.zeros(self.n, dtype=np.int64) if with_rank else None
         self._raise(self._lib.qpr_populations(self._h, _ptr(rho), _ptr(p), _ptr(rank)))
         return (p, rank) if with_rank else p
+
+    def rkf45(self, rho, tol: float = 1e-8, max_steps: int = 400000, h0: float = 0.0, step_tol: float = 0.0,
+              h_max: float = 0.0, t_end: float = 0.0, check: bool = True):
+        """qpr_rkf45 in place on rho: adaptive RKF45 to the steady state
+        (t_end <= 0) or to time t_end. Returns the stats dict (with
+        "status"); raises on failure when ``check``."""
+        _check_rho(rho, self.n)
+        opt = qpr_rkf45_options()
+        opt.h0, opt.step_tol, opt.h_max, opt.t_end = float(h0), float(step_tol), float(h_max), float(t_end)
+        stats = qpr_rkf45_stats()
+        st = self._lib.qpr_rkf45(self._h, _ptr(rho), ctypes.byref(opt), float(tol), int(max_steps),
+                                 ctypes.byref(stats))
+        d = stats.as_dict()
+        d["status"] = int(st)
+        if check and st != QPR_OK:
+            self._raise(st)
+        return d
 
     def pagerank(self, tol: float = 1e-14, max_iter: int = 100000, out=None):
         """qpr_pagerank: the classical PageRank vector of the graph (NumPy

@@ -14,7 +14,7 @@ from paper_2003_04930_gb300 import qpr
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = [qpr.qpr_options, qpr.qpr_stats, qpr.qpr_profile, qpr.qpr_problem, qpr.qpr_gnn_sample,
-           qpr.qpr_tune_result]
+           qpr.qpr_tune_result, qpr.qpr_rkf45_options, qpr.qpr_rkf45_stats]
 
 
 @pytest.fixture(scope="module")
