@@ -262,9 +262,15 @@ QPR_API qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int
  * row sums to its node and the weights of Eq. S11 sum to one), and the step
  * factor s = (Tol h / (2 |z_{k+1} - y_{k+1}|))^(1/4) of Eq. S13. Readings
  * where the note is silent: |.| is the largest modulus over the N^2 entries;
- * an attempt is accepted when |z - y| <= Tol h, and y_{k+1} becomes the
- * state; after every attempt h <- min(s h, h_max) with s clipped to
- * [1/10, 4]; a trajectory's last step ends exactly at t_end.
+ * an attempt is accepted when |z - y| <= Tol h, and y_{k+1} (or z_{k+1},
+ * order 5) becomes the state; after every attempt h <- min(s h, h_max) with s
+ * clipped to [1/10, 4]; a trajectory's last step ends exactly at t_end.
+ * Both fourth- and fifth-order propagated solutions are slightly anti-damping
+ * near the imaginary axis (|P4(iy)| up to 1.03, |P5(iy)| up to 1.004 for y
+ * below about 2.3), which the coherences' damping omega h must offset: with
+ * order 4 steady-state solves stall near a residual of 1e-4 for omega <= 0.6
+ * on the heavy-tailed graphs, with order 5 only below omega ~ 0.3; fixed-step
+ * RK4 (qpr_steady_state) has no such limit.
  * Computed in the mixed delta form of QPR_MIXED on the column-block sparse
  * stage (COLUMNS, COLUMNS_PERSISTENT or COLUMNS_GATHER; else QPR_E_ARG): f is
  * linear, so an attempt is the polynomial P4(hL) (y) and the discrepancy
@@ -279,7 +285,9 @@ typedef struct {
     double h_max;    /* largest step (<= 0: qpr_max_stable_dt(ctx), the RK4 stability estimate, which also
                         keeps RKF45's fourth-order solution stable on these problems) */
     double t_end;    /* > 0: integrate the trajectory to this time; <= 0: solve for the steady state */
-    int32_t reserved[4];
+    int32_t order;   /* the solution an accepted attempt keeps: 4 (or 0, default) y_{k+1} of Eq. S11, which
+                        the note names the approximation; 5 z_{k+1} of Eq. S12, the alternative it offers */
+    int32_t reserved[3];
 } qpr_rkf45_options;
 
 typedef struct {
@@ -366,21 +374,29 @@ QPR_API qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *prob
                                           double tol, int64_t max_steps, const qpr_options *opt, qpr_stats *stats);
 
 /* ---- autotuner ----
- * Chooses, for one problem and one precision, the stage-kernel family
- * (QPR_BACKEND_SPARSE: CSR gathers; QPR_BACKEND_DENSE: DMMA for QPR_FP64,
- * split-BF16 tcgen05 for QPR_MIXED) and, for QPR_MIXED, ref_refresh in
- * {8, 16, 32, 64}, by timing short real runs (qpr_evolve from I/N, 4 warm-up
- * steps, then max(16, 2 ref_refresh) timed steps) of every candidate on the
- * device. The paper has no counterpart. With cache_path (nullable) the choice is read
- * from / appended to a text file keyed by GPU name, precision,
- * floor(log2 N) and floor(log2(nnz(H)/N + 1)); a cached answer sets
- * from_cache. `base` supplies the other options (NULL: defaults). */
+ * Chooses, for one problem and one precision, the configuration of the
+ * stage by timing short real runs (qpr_evolve from I/N, 4 warm-up steps,
+ * then max(32, 2 ref_refresh) timed steps) of every candidate on the device.
+ * The paper has no counterpart. QPR_MIXED: the backend (sparse, or the
+ * split-BF16 tcgen05 dense stage), for the sparse backend the stage form
+ * (COLUMNS with row splits 1-4 and the plan's own choice, COLUMNS_GATHER
+ * with the plan's splits, half and twice as many, TILES; candidates whose
+ * plan repeats an earlier one are skipped), then ref_refresh in
+ * {16, 32, 64} for the winner. QPR_FP64: the backend (CSR gathers or DMMA).
+ * With cache_path (nullable) the choice is read from / appended to a text
+ * file keyed by GPU name, precision, floor(log2 N) and
+ * floor(log2(nnz(H)/N + 1)); a cached answer sets from_cache. `base`
+ * supplies the other options (NULL: defaults); a context created with base
+ * plus backend, sparse_form, row_splits and ref_refresh from the result runs
+ * the chosen configuration. */
 typedef struct {
     int32_t backend;
     int32_t ref_refresh;
     double ms_per_step;  /* measured wall time of one step of the chosen configuration */
     int32_t from_cache;
-    int32_t reserved[3];
+    int32_t sparse_form; /* QPR_MIXED sparse: the chosen QPR_SPARSE_FORM_* (AUTO otherwise) */
+    int32_t row_splits;  /* the chosen row splits (0: the plan's own choice) */
+    int32_t reserved[1];
 } qpr_tune_result;
 
 QPR_API qpr_status qpr_autotune(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w,

@@ -72,7 +72,7 @@ def _load():
         lib.oracle_steady_state.argtypes = [vp, vp, f64, f64, i64, ctypes.POINTER(i64),
                                             ctypes.POINTER(f64), vp]
         lib.oracle_rkf45.restype = ip
-        lib.oracle_rkf45.argtypes = [vp, vp, f64, f64, f64, f64, f64, i64, ctypes.POINTER(i64),
+        lib.oracle_rkf45.argtypes = [vp, vp, f64, f64, f64, f64, f64, i64, ip, ctypes.POINTER(i64),
                                      ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64),
                                      ctypes.POINTER(f64), vp, i64]
         lib.oracle_rkf45_step.restype = f64
@@ -178,9 +178,11 @@ class Oracle:
         return out
 
     def rkf45(self, rho0: np.ndarray, h0: float, step_tol: float, h_max: float, resid_tol: float = 0.0,
-              t_end: float = float("inf"), max_steps: int = 10**7, history: bool = False, hist_cap: int = 200000):
+              t_end: float = float("inf"), max_steps: int = 10**7, history: bool = False, hist_cap: int = 200000,
+              order: int = 4):
         """Adaptive RKF45 (Supplementary Note 2, Eq. S10 - S13; readings in
-        qpr_oracle.c). Returns a dict: rho, accepted, rejected, t, h (the next
+        qpr_oracle.c; order 4 propagates y_{k+1} of Eq. S11, order 5 the
+        alternative z_{k+1} of Eq. S12). Returns a dict: rho, accepted, rejected, t, h (the next
         attempt's step), residual, status, and with ``history`` an array of
         (t, h, discrepancy, s, accepted) per attempt."""
         y = np.array(rho0, dtype=np.complex128, order="C", copy=True)
@@ -188,7 +190,7 @@ class Oracle:
         t, h, r = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
         hist = np.zeros((hist_cap, 5)) if history else None
         st = self._lib.oracle_rkf45(self._h, _ptr(y), float(h0), float(step_tol), float(h_max), float(resid_tol),
-                                    float(t_end), int(max_steps), ctypes.byref(acc), ctypes.byref(rej),
+                                    float(t_end), int(max_steps), int(order), ctypes.byref(acc), ctypes.byref(rej),
                                     ctypes.byref(t), ctypes.byref(h), ctypes.byref(r),
                                     _ptr(hist) if history else None, int(hist_cap) if history else 0)
         if st not in (OR_OK, OR_E_NOT_CONVERGED):

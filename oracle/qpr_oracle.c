@@ -403,8 +403,9 @@ static double rkf_attempt(oracle_t *o, const cplx *y, double h) {
  *   - an attempt is accepted when |z_{k+1} - y_{k+1}| <= step_tol h (a
  *     discrepancy within the tolerance per unit time), and then y_{k+1}, the
  *     fourth-order solution that Eq. S11 defines as the approximation, is
- *     the new state; otherwise the state is kept and the attempt is repeated
- *     with s h;
+ *     the new state (order = 4), or z_{k+1}, the fifth-order relationship the
+ *     note offers as the alternative (order = 5); otherwise the state is kept
+ *     and the attempt is repeated with s h;
  *   - s is clipped to [1/10, 4] and s h to h_max (a discrepancy of zero
  *     gives the largest factor), and in a trajectory the last step is
  *     shortened to end exactly at t_end;
@@ -419,10 +420,10 @@ static double rkf_attempt(oracle_t *o, const cplx *y, double h) {
  * use, the residual of the returned state; hist (nullable, 5 doubles per
  * attempt, at most hist_cap attempts): t, h, discrepancy, s, accepted. */
 int oracle_rkf45(oracle_t *o, cplx *rho, double h0, double step_tol, double h_max, double resid_tol, double t_end,
-                 int64_t max_steps, int64_t *accepted_out, int64_t *rejected_out, double *t_out, double *h_out,
-                 double *resid_out, double *hist, int64_t hist_cap) {
+                 int64_t max_steps, int order, int64_t *accepted_out, int64_t *rejected_out, double *t_out,
+                 double *h_out, double *resid_out, double *hist, int64_t hist_cap) {
     if (!(h0 > 0.0) || !(step_tol > 0.0) || !(h_max > 0.0) || !(resid_tol >= 0.0) || max_steps < 0 ||
-        !(t_end > 0.0))
+        !(t_end > 0.0) || (order != 4 && order != 5))
         return OR_E_ARG;
     double tr = oracle_prepare(o->n, rho);
     if (!(tr > 0.0) || !isfinite(tr)) return OR_E_ARG;
@@ -452,7 +453,7 @@ int oracle_rkf45(oracle_t *o, cplx *rho, double h0, double step_tol, double h_ma
         }
         ++na;
         if (ok) {
-            memcpy(rho, o->ry, nn * sizeof(cplx));
+            memcpy(rho, order == 5 ? o->rz : o->ry, nn * sizeof(cplx));
             double trc = 0.0;
             for (int64_t a = 0; a < n; ++a) trc += creal(rho[a * n + a]);
             for (size_t q = 0; q < nn; ++q) rho[q] /= trc;

@@ -417,7 +417,7 @@ qpr_status ensure_rkf_graph(qpr_ctx *ctx) {
 // refresh confirms (as in run_mixed). The run ends with a refresh, so R
 // holds the returned state. Bounded: at most max_attempts attempts.
 qpr_status run_rkf45(qpr_ctx *ctx, double h0, double step_tol, double hmax, double tend, double tol,
-                     int64_t max_steps, int64_t max_attempts) {
+                     int64_t max_steps, int64_t max_attempts, int order) {
     Ctl *h = ctx->h_ctl;
     memset(h, 0, sizeof(Ctl));
     h->max_steps = max_steps;
@@ -429,6 +429,7 @@ qpr_status run_rkf45(qpr_ctx *ctx, double h0, double step_tol, double hmax, doub
     h->rk_hmax = hmax;
     h->rk_tol = step_tol;
     h->rk_tend = tend;
+    h->rk_order = order;
     h->rk_hf = (float)h0;
     h->rk_hl = (float)(h0 - (double)(float)h0);
     QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
@@ -1415,6 +1416,8 @@ qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, doub
         return fail(ctx, QPR_E_ARG, "h0, step_tol, h_max and t_end must be finite");
     if (!traj && !(tol > 0.0)) return fail(ctx, QPR_E_ARG, "tol must be positive for a steady-state solve");
     if (max_steps < 0) return fail(ctx, QPR_E_ARG, "max_steps must be non-negative");
+    const int order = o.order == 0 ? 4 : o.order;
+    if (order != 4 && order != 5) return fail(ctx, QPR_E_ARG, "order must be 0, 4 or 5");
     h0 = std::min(h0, hmax);
     if (traj) h0 = std::min(h0, o.t_end);
     st = ensure_rkf(ctx);
@@ -1422,7 +1425,7 @@ qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, doub
     st = import_state(ctx, rho);
     if (st != QPR_OK) return st;
     const int64_t max_attempts = 16 * max_steps + 64 * (int64_t)ctx->opt.ref_refresh;
-    st = run_rkf45(ctx, h0, step_tol, hmax, traj ? o.t_end : 0.0, traj ? 0.0 : tol, max_steps, max_attempts);
+    st = run_rkf45(ctx, h0, step_tol, hmax, traj ? o.t_end : 0.0, traj ? 0.0 : tol, max_steps, max_attempts, order);
     if (st != QPR_OK) return st;
     Ctl c = *ctx->h_ctl;
     st = export_rho(ctx, ctx->mw.R, 0, rho);

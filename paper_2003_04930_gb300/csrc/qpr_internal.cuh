@@ -47,11 +47,13 @@ struct Ctl {
     // RKF45 (qpr_rkf45): the step of the next attempt and its largest value,
     // the tolerance Tol of Eq. S13, the integrated time and its end (0: none),
     // the discrepancy |z - y| of the last attempt, the rejected attempts, the
-    // delta pair holding the current state (0: D, Dlo; 1: D1, Dlo1) and the
-    // step as a float-float pair (hf + hl) for the delta stages
+    // delta pair holding the current state (0: D, Dlo; 1: D1, Dlo1), the
+    // order of the solution an accepted attempt keeps (4: y of Eq. S11, 5: z
+    // of Eq. S12) and the step as a float-float pair (hf + hl) for the delta
+    // stages
     double rk_h, rk_hmax, rk_tol, rk_t, rk_tend, rk_err;
     long long rk_rejected;
-    int rk_cur, rk_pad_;
+    int rk_cur, rk_order;
     float rk_hf, rk_hl;
 };
 

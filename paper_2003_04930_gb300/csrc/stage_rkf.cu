@@ -22,9 +22,10 @@
 // added at the end in float-float from F = F32 + Flo). Stages 2-5 evaluate
 // u_k = h f(u_{k-1}) in FP32 and add pi_k u_k to acc; stage 6 evaluates u_6,
 // the discrepancy, and the candidate D' = D + h F + acc in float-float, into
-// the other delta pair. The last CTA of stage 6 takes the controller's
-// decision (one thread, FP64): accept when |z - y| <= Tol h (then the other
-// pair becomes the state), s = (Tol h / (2 |z - y|))^(1/4) clipped to
+// the other delta pair (or D + h F + acc + (z - y), the fifth-order z of
+// Eq. S12, when the caller chose the note's alternative). The last CTA of
+// stage 6 takes the controller's decision (one thread, FP64): accept when
+// |z - y| <= Tol h (then the other pair becomes the state), s = (Tol h / (2 |z - y|))^(1/4) clipped to
 // [1/10, 4], next h = min(s h, h_max) (shortened to end a trajectory at its
 // end time). Every stage is gain (forked beside the SpMM), SpMM, epilogue,
 // exactly as an RK4 stage of the column-block form.
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
     const float *X2 = diag ? sX1 : sX2;
     const float om = ops.omega32, cm = __fsub_rn(1.0f, om);
     const float hh = w.ctl->rk_hf, hl = w.ctl->rk_hl;
+    const bool fifth = (S == 6) && w.ctl->rk_order == 5;
     float *out = (S <= 5) ? rkf_output<S>(w) : nullptr;
     float *Dn = cur ? w.D : w.D1;  // stage 6: the other pair
     float *Ln = cur ? w.Dlo : w.Dlo1;
@@ -313,8 +315,11 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
             const float ei = __fmaf_rn(kE6, u6i, __fmul_rn(kE5, in.di[k]));
             const float em = sqrtf(__fmaf_rn(er, er, __fmul_rn(ei, ei)));
             emax = (em > emax || isnan(em)) ? em : emax;
-            const ff nr = candidate(in.vr[k], in.sr[k], in.ur[k], in.lr[k], hh, hl, in.ar[k]);
-            const ff ni = candidate(in.vi[k], in.si[k], in.ui[k], in.li[k], hh, hl, in.ai[k]);
+            // fourth order: D + h F + acc; fifth order: z = y + (z - y)
+            const float ar = fifth ? __fadd_rn(in.ar[k], er) : in.ar[k];
+            const float ai = fifth ? __fadd_rn(in.ai[k], ei) : in.ai[k];
+            const ff nr = candidate(in.vr[k], in.sr[k], in.ur[k], in.lr[k], hh, hl, ar);
+            const ff ni = candidate(in.vi[k], in.si[k], in.ui[k], in.li[k], hh, hl, ai);
             o0 = nr.hi;
             o1 = ni.hi;
             o2 = nr.lo;

@@ -70,7 +70,7 @@ class qpr_profile(ctypes.Structure):
 
 class qpr_rkf45_options(ctypes.Structure):
     _fields_ = [("h0", ctypes.c_double), ("step_tol", ctypes.c_double), ("h_max", ctypes.c_double),
-                ("t_end", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+                ("t_end", ctypes.c_double), ("order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class qpr_rkf45_stats(ctypes.Structure):
@@ -97,7 +97,8 @@ class qpr_gnn_sample(ctypes.Structure):
 
 class qpr_tune_result(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int32), ("ref_refresh", ctypes.c_int32), ("ms_per_step", ctypes.c_double),
-                ("from_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("from_cache", ctypes.c_int32), ("sparse_form", ctypes.c_int32), ("row_splits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class QprError(RuntimeError):
@@ -348,13 +349,14 @@ class Solver:
         return (p, rank) if with_rank else p
 
     def rkf45(self, rho, tol: float = 1e-8, max_steps: int = 400000, h0: float = 0.0, step_tol: float = 0.0,
-              h_max: float = 0.0, t_end: float = 0.0, check: bool = True):
+              h_max: float = 0.0, t_end: float = 0.0, order: int = 4, check: bool = True):
         """qpr_rkf45 in place on rho: adaptive RKF45 to the steady state
         (t_end <= 0) or to time t_end. Returns the stats dict (with
         "status"); raises on failure when ``check``."""
         _check_rho(rho, self.n)
         opt = qpr_rkf45_options()
         opt.h0, opt.step_tol, opt.h_max, opt.t_end = float(h0), float(step_tol), float(h_max), float(t_end)
+        opt.order = int(order)
         stats = qpr_rkf45_stats()
         st = self._lib.qpr_rkf45(self._h, _ptr(rho), ctypes.byref(opt), float(tol), int(max_steps),
                                  ctypes.byref(stats))
@@ -500,9 +502,16 @@ class Gnn:
         return losses
 
 
+def tuned_options(r) -> dict:
+    """Solver keyword options of an autotune result."""
+    return {"backend": r["backend"], "ref_refresh": r["ref_refresh"], "sparse_form": r["sparse_form"],
+            "row_splits": r["row_splits"]}
+
+
 def autotune(g, omega, alpha=0.85, dt=0.01, precision=QPR_MIXED, cache_path=None, device=-1):
     """qpr_autotune for an EdgeList: returns dict(backend, ref_refresh,
-    ms_per_step, from_cache)."""
+    ms_per_step, from_cache, sparse_form, row_splits); Solver(...,
+    **tuned_options(result)) runs the chosen configuration."""
     lib = load_library()
     src = np.ascontiguousarray(g.src, dtype=np.int64)
     dst = np.ascontiguousarray(g.dst, dtype=np.int64)
@@ -517,4 +526,4 @@ def autotune(g, omega, alpha=0.85, dt=0.01, precision=QPR_MIXED, cache_path=None
     if st != QPR_OK:
         raise QprError(st, lib.qpr_last_error(None).decode())
     return {"backend": res.backend, "ref_refresh": res.ref_refresh, "ms_per_step": res.ms_per_step,
-            "from_cache": res.from_cache}
+            "from_cache": res.from_cache, "sparse_form": res.sparse_form, "row_splits": res.row_splits}

@@ -35,20 +35,21 @@ def _close(got, ref, prel):
     assert np.abs(p - pr).max() <= prel * pr.max()
 
 
-@pytest.mark.parametrize("n,omega,form,refresh", [(33, 0.8, Q.QPR_SPARSE_FORM_COLUMNS, 32),
-                                                  (200, 0.3, Q.QPR_SPARSE_FORM_COLUMNS, 7),
-                                                  (520, 0.6, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, 16),
-                                                  (300, 0.8, Q.QPR_SPARSE_FORM_COLUMNS_GATHER, 32)])
-def test_rkf45_trajectory_matches_oracle(n, omega, form, refresh):
+@pytest.mark.parametrize("n,omega,form,refresh,order", [(33, 0.8, Q.QPR_SPARSE_FORM_COLUMNS, 32, 4),
+                                                        (200, 0.3, Q.QPR_SPARSE_FORM_COLUMNS, 7, 4),
+                                                        (200, 0.3, Q.QPR_SPARSE_FORM_COLUMNS, 7, 5),
+                                                        (520, 0.6, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT, 16, 5),
+                                                        (300, 0.8, Q.QPR_SPARSE_FORM_COLUMNS_GATHER, 32, 4)])
+def test_rkf45_trajectory_matches_oracle(n, omega, form, refresh, order):
     g = graphs.heavy_tailed(n, 5)
     s = _solver(g, omega, form, refresh)
     hmax = s.max_stable_dt
     o = Oracle.from_edges(g, alpha=0.85, omega=omega)
     rho0 = graphs.random_density(n, 4, rank=3)
     t_end = 1.5
-    ref = o.rkf45(rho0, 0.01, 1e-6, hmax, t_end=t_end)
+    ref = o.rkf45(rho0, 0.01, 1e-6, hmax, t_end=t_end, max_steps=5000, order=order)
     d = torch.from_numpy(rho0.copy()).to(DEV)
-    st = s.rkf45(d, h0=0.01, step_tol=1e-6, h_max=hmax, t_end=t_end)
+    st = s.rkf45(d, h0=0.01, step_tol=1e-6, h_max=hmax, t_end=t_end, max_steps=5000, order=order)
     assert st["converged"] == 1 and st["t"] == pytest.approx(t_end, rel=1e-14)
     assert abs(st["accepted"] - ref["accepted"]) <= 2 and abs(st["rejected"] - ref["rejected"]) <= 2
     got = d.cpu().numpy()
@@ -64,32 +65,35 @@ def test_rkf45_rejections_follow_the_oracle():
     hmax = s.max_stable_dt
     o = Oracle.from_edges(g, alpha=0.85, omega=0.5)
     rho0 = graphs.random_density(150, 8, rank=1)
-    ref = o.rkf45(rho0, hmax, 1e-9, hmax, t_end=0.5)
+    ref = o.rkf45(rho0, hmax, 1e-9, hmax, t_end=0.5, max_steps=5000)
     assert ref["rejected"] >= 1
     d = torch.from_numpy(rho0.copy()).to(DEV)
-    st = s.rkf45(d, h0=hmax, step_tol=1e-9, h_max=hmax, t_end=0.5)
+    st = s.rkf45(d, h0=hmax, step_tol=1e-9, h_max=hmax, t_end=0.5, max_steps=5000)
     assert st["rejected"] >= 1 and abs(st["rejected"] - ref["rejected"]) <= 2
     assert abs(st["accepted"] - ref["accepted"]) <= 2
     _close(d.cpu().numpy(), ref["rho"], 1e-6)
 
 
-@pytest.mark.parametrize("n,omega", [(150, 0.8), (400, 0.3)])
-def test_rkf45_steady_state_matches_oracle(n, omega):
+# steady states: order 4 at omega = 0.8, order 5 (the note's alternative)
+# also at omega = 0.5, where the fourth-order solution stalls (see qpr.h)
+@pytest.mark.parametrize("n,omega,order", [(150, 0.8, 4), (150, 0.8, 5), (200, 0.5, 5)])
+def test_rkf45_steady_state_matches_oracle(n, omega, order):
     g = graphs.heavy_tailed(n, 6)
     s = _solver(g, omega)
     hmax = s.max_stable_dt
     o = Oracle.from_edges(g, alpha=0.85, omega=omega)
     rho0 = graphs.maximally_mixed(n)
-    ref = o.rkf45(rho0, 0.01, 1e-6, hmax, resid_tol=1e-8)
+    ref = o.rkf45(rho0, 0.01, 1e-6, hmax, resid_tol=1e-8, max_steps=20000, order=order)
+    assert ref["status"] == 0
     d = torch.from_numpy(rho0.copy()).to(DEV)
-    st = s.rkf45(d, tol=1e-8, h0=0.01, step_tol=1e-6, h_max=hmax)
+    st = s.rkf45(d, tol=1e-8, h0=0.01, step_tol=1e-6, h_max=hmax, max_steps=20000, order=order)
     got = d.cpu().numpy()
     assert st["converged"] == 1 and st["residual"] < 1e-8
     assert abs(st["residual"] - o.residual(got)) <= 1e-12
     assert abs(st["accepted"] - ref["accepted"]) <= 2
     _close(got, ref["rho"], 1e-7)
     # fewer steps than fixed-step RK4 at dt = 0.01 to the same tolerance, same steady state
-    _, rk4_steps, _, _ = o.steady_state(rho0, 0.01, 1e-8, 10**6)
+    _, rk4_steps, _, _ = o.steady_state(rho0, 0.01, 1e-8, 200000)
     assert st["accepted"] < rk4_steps
 
 
@@ -97,9 +101,9 @@ def test_rkf45_steady_state_equals_rk4_steady_state_polished():
     g = graphs.heavy_tailed(250, 9)
     s = _solver(g, 0.7)
     d = torch.from_numpy(graphs.maximally_mixed(250)).to(DEV)
-    s.rkf45(d, tol=1e-11)
+    s.rkf45(d, tol=1e-11, max_steps=20000, order=5)
     r = torch.from_numpy(graphs.maximally_mixed(250)).to(DEV)
-    s.steady_state(r, 0.01, 1e-11, 10**6)
+    s.steady_state(r, 0.01, 1e-11, 200000)
     a, b = d.cpu().numpy(), r.cpu().numpy()
     assert np.abs(populations(a) - populations(b)).max() <= 1e-7 * populations(b).max()
     assert np.linalg.norm(a - b) <= 1e-6
@@ -121,4 +125,7 @@ def test_rkf45_max_steps_and_arguments():
     assert e.value.status == Q.QPR_E_ARG
     with pytest.raises(Q.QprError) as e:
         s.rkf45(d, tol=0.0)
+    assert e.value.status == Q.QPR_E_ARG
+    with pytest.raises(Q.QprError) as e:
+        s.rkf45(d, tol=1e-8, order=3)
     assert e.value.status == Q.QPR_E_ARG

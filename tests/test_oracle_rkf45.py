@@ -17,7 +17,9 @@ has only when every coefficient is right:
   * a fourth-order method under per-unit-step error control takes steps
     h ~ step_tol^(1/4): dividing step_tol by 16 doubles the number of steps;
   * with the step cap at the stability estimate the loop reaches the steady
-    state (the null vector of the superoperator) like fixed-step RK4.
+    state (the null vector of the superoperator) like fixed-step RK4; where
+    the coherences are weakly damped (omega = 0.5) the fourth-order
+    propagated solution stalls and the fifth-order alternative converges.
 """
 import numpy as np
 import pytest
@@ -69,8 +71,8 @@ def test_adaptive_trajectory_within_controlled_tolerance(config1):
     rho0 = graphs.random_density(16, 7, rank=1)
     t_end = 3.0
     exact = superop.exact_solution(lsup, rho0, t_end)
-    for tol in (1e-5, 1e-7):
-        out = o.rkf45(rho0, 0.01, tol, hmax, t_end=t_end, history=True)
+    for tol, order in ((1e-5, 4), (1e-7, 4), (1e-7, 5)):
+        out = o.rkf45(rho0, 0.01, tol, hmax, t_end=t_end, history=True, order=order)
         assert out["t"] == t_end and out["status"] == 0
         hist = out["history"]
         acc = hist[hist[:, 4] == 1]
@@ -99,16 +101,34 @@ def test_step_count_scales_as_tolerance_to_the_quarter():
         assert 1.8 < b / a < 2.2, steps
 
 
-def test_steady_state_equals_null_vector(config1):
+@pytest.mark.parametrize("order", [4, 5])
+def test_steady_state_equals_null_vector(config1, order):
     g, o, lsup, hmax = config1
     rho_ss, s_min, s2 = superop.null_state(lsup)
-    out = o.rkf45(graphs.maximally_mixed(16), 0.01, 1e-4, hmax, resid_tol=1e-12)
+    out = o.rkf45(graphs.maximally_mixed(16), 0.01, 1e-4, hmax, resid_tol=1e-12, max_steps=100000, order=order)
     assert out["status"] == 0 and out["residual"] < 1e-12
     # two states with residual < r differ by at most about r / (second singular value)
     assert np.abs(out["rho"] - rho_ss).max() <= 1e-12 / s2 * 10
     # and it needs fewer steps than fixed-step RK4 at dt = 0.01
     _, rk4_steps, _, _ = o.steady_state(graphs.maximally_mixed(16), 0.01, 1e-12, 10**6)
     assert out["accepted"] < rk4_steps
+
+
+def test_fifth_order_propagation_reaches_steady_state_where_fourth_stalls():
+    # both propagated solutions are slightly anti-damping near the imaginary
+    # axis (|P4(iy)| up to 1.03 and |P5(iy)| up to 1.004 for y < ~2.3); at
+    # omega = 0.5 the coherences' damping omega h does not offset P4's, and the
+    # residual stalls, while the fifth-order solution converges
+    g = graphs.heavy_tailed(60, 6)
+    o = Oracle.from_edges(g, alpha=0.85, omega=0.5)
+    A, H, G, c = o.operators()
+    ev = np.linalg.eigvalsh(H)
+    hmax = 2.5 / ((1 - 0.5) * (ev[-1] - ev[0]) + 2 * 0.5 * c.max())
+    rho0 = graphs.maximally_mixed(60)
+    four = o.rkf45(rho0, 0.01, 1e-6, hmax, resid_tol=1e-8, max_steps=4000, order=4)
+    five = o.rkf45(rho0, 0.01, 1e-6, hmax, resid_tol=1e-8, max_steps=4000, order=5)
+    assert four["status"] != 0 and four["residual"] > 1e-6
+    assert five["status"] == 0 and five["residual"] < 1e-8
 
 
 def test_invalid_arguments():
