@@ -486,8 +486,7 @@ def form_name(s, prec):
 # (`dram__bytes_read.sum + dram__bytes_write.sum` of the stage-1 launch,
 # profiles/traffic_cols_n922_n4096.md), keyed by (kernel, N); a kernel
 # changed since its capture has no entry.
-NCU_TRAFFIC = {("cols_spmm_kernel", 922): 7033000, ("cols_epi_kernel", 922): 14043000,
-               ("cols_gather_kernel", 4096): 135267000 + 99186000, ("cols_epi_kernel", 4096): 269651000 + 101275000}
+NCU_TRAFFIC = {("cols_epi_kernel", 922): 14043000, ("cols_epi_kernel", 4096): 269651000 + 101275000}
 
 
 def roofline(s, g, n, prof, peaks, peak_src, prec):
@@ -532,7 +531,7 @@ def roofline(s, g, n, prof, peaks, peak_src, prec):
                  "gathered_gbs": rows_read / (prof["product_ms"] * 1e-3) / 1e9,
                  "flops_per_launch": 4.0 * nnz * npad,
                  "epilogue": hbm_entry("cols_epi_kernel", epi_alg, prof["epilogue_ms"]),
-                 "gain": {"kernel": "cols_gain_kernel", "launch_ms": prof["gain_ms"]},
+                 "gain": "formed by the SpMM grid's leading CTAs (cta_gain), inside launch_ms",
                  "note": "alg bytes are the DRAM floor (stage input and X once, the CSR entries once); at "
                          "N <= 1400 the state is L2-resident, so a fraction of the HBM peak is a lower bound "
                          "on what the kernel moves through the memory system"}

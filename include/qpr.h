@@ -92,9 +92,9 @@ enum { QPR_BACKEND_AUTO = 0, QPR_BACKEND_DENSE = 1, QPR_BACKEND_SPARSE = 2 };
 /* Form of the FP32 stage of QPR_MIXED with the sparse backend.
  * COLUMNS: per stage a column-block product X = H (Y_s - R), each CTA
  *   staging 16 complex columns of the delta in shared memory with TMA, then
- *   a tile-pair epilogue: 2 launches per stage (and the gain on a forked
- *   branch beside the product); where the staged operands fit one CTA's
- *   shared memory (N padded to 32 <= 1536).
+ *   a tile-pair epilogue: 2 launches per stage (the product grid's leading
+ *   CTAs form the gain G p on the SMs the product leaves free); where the
+ *   staged operands fit one CTA's shared memory (N padded to 32 <= 1536).
  * COLUMNS_PERSISTENT: the same arithmetic in one cooperative launch per
  *   block of ref_refresh steps, grid barriers between the phases (needs
  *   cooperative launch support).
@@ -237,10 +237,10 @@ QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double t
  * Means over all launches of the kind, in milliseconds. */
 typedef struct {
     double product_ms;   /* the H rho product: the column-block SpMM (COLUMNS, COLUMNS_PERSISTENT) or
-                            gather SpMM (COLUMNS_GATHER); the fused stage kernel of the other forms
-                            (product and epilogue in one launch) */
+                            gather SpMM (COLUMNS_GATHER), whose leading CTAs also form the gain; the fused
+                            stage kernel of the other forms (product and epilogue in one launch) */
     double epilogue_ms;  /* the epilogue kernel of the two-kernel column-block forms; 0 otherwise */
-    double gain_ms;      /* the gain kernel G p (0 where the stage kernel forms the gain itself) */
+    double gain_ms;      /* the gain kernel G p (0 where the product or stage kernel forms the gain) */
     double refresh_ms;   /* QPR_MIXED: one exact FP64 reference refresh, all its kernels; 0 otherwise */
     double step_ms;      /* the kernels of one RK4 step run one at a time (the sum of the above) */
     int32_t launches_per_step;

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(cols::kENT, 3) b_cols_epi_kernel(const BatchGr
 
 template <int STAGE>
 cudaError_t set_bcols_attr(int bytes) {
-    return cudaFuncSetAttribute(b_cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return raise_smem_limit_t(b_cols_spmm_kernel<STAGE>, bytes);
 }
 
 template <int STAGE>

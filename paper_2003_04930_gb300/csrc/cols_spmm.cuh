@@ -126,5 +126,22 @@ __device__ __forceinline__ void spmm_gather_body(PickInput pick_input, const Dev
     }
 }
 
+// The gain of the stage input by CTA b of the nb leading CTAs of an SpMM
+// grid (rows shared over them), from the compact diagonal that `pick_pv`
+// returns (written by the previous epilogue; called after the grid
+// dependency wait). The dynamic shared memory holds the staged diagonal (np
+// floats).
+template <typename PickPv>
+__device__ __forceinline__ void gain_role(const DevOps &ops, const MixedWork &w, int b, int nb, PickPv pick_pv) {
+    extern __shared__ uint8_t dyn_raw[];
+    __shared__ int s_done;
+    tma::grid_dependency_wait();
+    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
+    __syncthreads();
+    if (s_done) return;
+    tma::launch_dependents();
+    cta_gain(ops, w, b, nb, reinterpret_cast<float *>(dyn_raw), pick_pv());
+}
+
 }  // namespace cols
 }  // namespace qpr

@@ -385,7 +385,7 @@ qpr_status ensure_rkf(qpr_ctx *ctx) {
     mw.Flo = ctx->d_rkf + 6 * plane;
     mw.pvd = ctx->d_rkf + 8 * plane;
     if (!qpr::make_rkf_map(ctx->ops, mw.D1, &ctx->colmaps)) return fail(ctx, QPR_E_CUDA, "cuTensorMapEncodeTiled failed");
-    QPR_CUDA(ctx, qpr::init_rkf(ctx->ops.col_smem, ctx->ops.col_gather != 0));
+    QPR_CUDA(ctx, qpr::init_rkf(ctx->ops.col_launch_smem, ctx->ops.col_gather != 0));
     return QPR_OK;
 }
 
@@ -724,7 +724,6 @@ void qpr_destroy(qpr_ctx *ctx) {
     if (!ctx) return;
     DeviceGuard dg(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->colmaps.side) cudaStreamSynchronize(ctx->colmaps.side);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph_c) cudaGraphExecDestroy(ctx->graph_c);
     if (ctx->graph_rkf) cudaGraphExecDestroy(ctx->graph_rkf);
@@ -763,9 +762,6 @@ void qpr_destroy(qpr_ctx *ctx) {
     cudaFree(ctx->d_p);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     if (ctx->ev) cudaEventDestroy(ctx->ev);
-    if (ctx->colmaps.fork) cudaEventDestroy(ctx->colmaps.fork);
-    if (ctx->colmaps.join) cudaEventDestroy(ctx->colmaps.join);
-    if (ctx->colmaps.side) cudaStreamDestroy(ctx->colmaps.side);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
@@ -989,11 +985,6 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
         return bail(QPR_E_ARG);
     }
     if (cols) {
-        if (gathered) {
-            CREATE_CUDA(qpr::set_gather_smem(cplan.smem));
-        } else {
-            CREATE_CUDA(qpr::set_cols_smem(cplan.smem));
-        }
         const std::vector<int2> &kh = cplan.kh;
         // the bundle descriptors, then the cut rows
         std::vector<int4> pieces(cplan.pieces);
@@ -1103,18 +1094,21 @@ qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, c
                 qpr_destroy(ctx);
                 return QPR_E_CUDA;
             }
-            if (cudaStreamCreateWithFlags(&ctx->colmaps.side, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ctx->colmaps.fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ctx->colmaps.join, cudaEventDisableTiming) != cudaSuccess) {
+            // the SpMM grid's leading CTAs form the gain, on the SMs the product leaves free (at least 8)
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+            const int units = gathered ? cplan.splits * (np / qpr::kColGatherWidth) : (np / qpr::kColWidth) * cplan.splits;
+            ops.col_gain_ctas = std::min(64, std::max(8, sms - units));
+            ops.col_launch_smem = std::max(cplan.smem, (int)(np * sizeof(float)) + 16);
+            const cudaError_t ea = gathered ? qpr::set_gather_smem(ops.col_launch_smem)
+                                            : qpr::set_cols_smem(ops.col_launch_smem);
+            if (ea != cudaSuccess) {
                 cudaGetLastError();
-                ctx->err = "stream or event creation failed";
+                ctx->err = std::string("kernel attribute: ") + cudaGetErrorString(ea);
                 g_create_error = ctx->err;
                 qpr_destroy(ctx);
                 return QPR_E_CUDA;
             }
-            int sms = 0;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-            ctx->colmaps.gain_ctas = std::min(64, std::max(8, sms - (np / 16) * ops.col_splits));
             mw.cmaps = &ctx->colmaps;
         }
         mw.g = ctx->d_g32;
@@ -1317,12 +1311,10 @@ qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t st
     for (int64_t k = 0; k < steps && st == QPR_OK; ++k) {
         for (int s = 1; s <= 4 && st == QPR_OK; ++s) {
             if (cols) {
-                st = timed(2, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 4, true); });
-                if (st == QPR_OK)
-                    st = timed(0, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, true); });
+                st = timed(0, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, true); });
                 if (st == QPR_OK)
                     st = timed(1, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 2, true); });
-                if (k == 0) per_step += 3;
+                if (k == 0) per_step += 2;
             } else if (mixed) {
                 if (ctx->mw.splitD) {
                     st = timed(2, [&] { qpr::launch_mixed_stage(s, ctx->ops, ctx->mw, ctx->stream, 1, true); });

@@ -111,6 +111,8 @@ struct DevOps {
     int col_part_off;
     int col_epi_off;       // persistent form: byte offset of the epilogue buffers (0: over the column block)
     int col_psmem;         // persistent form: dynamic shared memory of its launch
+    int col_gain_ctas;     // two-launch forms: leading CTAs of the SpMM grid that form the gain instead
+    int col_launch_smem;   // two-launch forms: dynamic shared memory of the SpMM launch (>= np floats)
 };
 
 // RK4 work buffers. Every state buffer holds two np x np FP64 planes,
@@ -172,10 +174,6 @@ struct MixedWork {
 struct ColMaps {
     CUtensorMap d[3];
     CUtensorMap d1;  // D1 of the RKF45 form (encoded by its first call)
-    // host side: the gain kernel runs on a forked branch beside the SpMM
-    cudaStream_t side;
-    cudaEvent_t fork, join;
-    int gain_ctas;
 };
 
 constexpr int kTileTc = 128;
@@ -219,9 +217,8 @@ void launch_mixed_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s)
 // One RK4 stage: parts & 1 launches the gain of the stage delta (the
 // tensor-core form; the tile-pair stage kernel forms the gain itself), parts
 // & 2 the stage kernel (3 = both, in that order). Column-block form: parts &
-// 1 the SpMM with the gain on a forked branch beside it, parts & 2 the
-// epilogue; serial (profiling): no fork and no programmatic dependent
-// launch, and parts & 4 launches the gain on s by itself.
+// 1 the SpMM (its leading CTAs form the gain), parts & 2 the epilogue;
+// serial (profiling): no programmatic dependent launch.
 void launch_mixed_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
                         bool serial = false);
 // Opt in to the dynamic shared memory of the sparse mixed stage kernels.
@@ -270,11 +267,11 @@ cudaError_t set_cols_smem(int bytes);
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts = 3,
                        bool serial = false);
 // RKF45 in the column-block form (stage_rkf.cu). One attempt is six
-// stages, each the gain (forked), the SpMM and the epilogue; stage 6 ends with
-// the step-size controller. The refresh folds the current delta into R and
+// stages, each the SpMM (its leading CTAs form the gain) and the epilogue;
+// stage 6 ends with the step-size controller. The refresh folds the current delta into R and
 // recomputes F = f(R) exactly, as the RK4 refresh does.
 constexpr int kRkfStages = 6;
-constexpr int kRkfLaunchesPerAttempt = 3 * kRkfStages;
+constexpr int kRkfLaunchesPerAttempt = 2 * kRkfStages;
 bool make_rkf_map(const DevOps &ops, const float *d1, ColMaps *maps);
 void launch_rkf_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s);
 void launch_rkf_refresh(const DevOps &ops, const MixedWork &w, cudaStream_t s);
@@ -292,7 +289,7 @@ cudaError_t set_persist_smem(int bytes);
 cudaError_t launch_cols_block(const DevOps &ops, const MixedWork &w, int steps, int grid, cudaStream_t s);
 // Kernel launches per RK4 step and per refresh of the mixed form.
 constexpr int kMixedLaunchesPerStep = 4;   // tile-pair sparse kernel (the dense one adds 4 gain kernels)
-constexpr int kMixedLaunchesPerStepCols = 12;  // column-block form: gain, SpMM and epilogue per stage
+constexpr int kMixedLaunchesPerStepCols = 8;  // column-block form: SpMM (with the gain) and epilogue per stage
 constexpr int kMixedLaunchesPerRefresh = 5;
 // Steady-state solves with adaptive_refresh: the longest window between
 // refreshes, in multiples of ref_refresh.
@@ -312,6 +309,16 @@ cudaError_t pagerank(const DevOps &ops, double tol, int64_t max_iter, double *sc
 // (3 values) receives the class sizes.
 cudaError_t hub_classes(const double *p, int n, double c, int *classes_dev, unsigned long long *counts_dev,
                         cudaStream_t s);
+
+// Raise the dynamic shared-memory limit of `kernel` on the current device to
+// at least `bytes`; never lower it (contexts with different plans share the
+// kernel, and a limit above a launch's request is harmless). Serialised
+// over host threads.
+cudaError_t raise_smem_limit(const void *kernel, int bytes);
+template <typename K>
+cudaError_t raise_smem_limit_t(K *kernel, int bytes) {
+    return raise_smem_limit(reinterpret_cast<const void *>(kernel), bytes);
+}
 
 // ---- host assembly (qpr_api.cu) ----
 struct HostOps {

@@ -3,7 +3,8 @@
 // (rows of 16 real then 16 imaginary values), its split's CSR entries and
 // its work list with bulk copies, and forms X[:, J] = H delta[:, J] for its
 // rows; the epilogue kernel applies the RK4 stage per tile pair. Each step
-// is 8 launches (SpMM + epilogue per stage).
+// is 8 launches (SpMM + epilogue per stage); the SpMM grid's leading CTAs
+// form the gain G p of the stage input on the SMs the product leaves free.
 //
 // The SpMM reads each column block once per row split (about splits x 8 N^2
 // bytes of L2 traffic per stage) instead of gathering a row slice of delta
@@ -13,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "cols_body.cuh"
@@ -25,26 +27,31 @@ namespace {
 
 using namespace cols;
 
+// The SpMM kernels: the first ops.col_gain_ctas CTAs form the gain of the
+// stage input (gain_role), the others one (column block, row split) unit of
+// the product each (whole block: unit u = block u % ncb of split u / ncb;
+// gather: the splits of a block side by side).
 template <int STAGE>
 __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
                                                          MixedWork w) {
-    spmm_block_body([&] { return &tm; }, ops, w, blockIdx.x, blockIdx.y);
+    const int b = blockIdx.x, ng = ops.col_gain_ctas;
+    if (b < ng) {
+        gain_role(ops, w, b, ng, [&] { return w.pv; });
+        return;
+    }
+    const int u = b - ng, ncb = ops.np / kCW;
+    spmm_block_body([&] { return &tm; }, ops, w, u % ncb, u / ncb);
 }
 
 template <int STAGE>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(DevOps ops, MixedWork w) {
-    spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, blockIdx.x, blockIdx.y);
-}
-
-// The gain of the stage input, rows shared over the grid; runs beside the
-// SpMM kernel (on SMs it leaves free).
-__global__ void __launch_bounds__(kANT) cols_gain_kernel(DevOps ops, MixedWork w) {
-    extern __shared__ float sp_dyn[];
-    __shared__ int s_done;
-    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) return;
-    cta_gain(ops, w, blockIdx.x, gridDim.x, sp_dyn);
+    const int b = blockIdx.x, ng = ops.col_gain_ctas;
+    if (b < ng) {
+        gain_role(ops, w, b, ng, [&] { return w.pv; });
+        return;
+    }
+    const int u = b - ng;
+    spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, u % ops.col_splits, u / ops.col_splits);
 }
 
 // Launched with programmatic dependent launch: the elementwise operands (the
@@ -78,10 +85,6 @@ int max_smem_optin(int device) {
     return v;
 }
 
-template <int STAGE>
-cudaError_t set_spmm_attr(int bytes) {
-    return cudaFuncSetAttribute(cols_spmm_kernel<STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
 
 // The entries of row i (column relative to c0, FP32 value bits).
 using RowEntries = std::vector<std::vector<int2>>;
@@ -328,19 +331,18 @@ bool make_col_maps(const DevOps &ops, const float *const din[3], ColMaps *maps) 
 }
 
 cudaError_t set_cols_smem(int bytes) {
-    cudaError_t e = set_spmm_attr<1>(bytes);
-    if (e == cudaSuccess) e = set_spmm_attr<2>(bytes);
-    if (e == cudaSuccess) e = set_spmm_attr<3>(bytes);
-    if (e == cudaSuccess) e = set_spmm_attr<4>(bytes);
+    cudaError_t e = raise_smem_limit_t(cols_spmm_kernel<1>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_spmm_kernel<2>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_spmm_kernel<3>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_spmm_kernel<4>, bytes);
     return e;
 }
 
 cudaError_t set_gather_smem(int bytes) {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(cols_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = raise_smem_limit_t(cols_gather_kernel<1>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_gather_kernel<2>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_gather_kernel<3>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit_t(cols_gather_kernel<4>, bytes);
     return e;
 }
 
@@ -366,20 +368,12 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bo
 
 void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStream_t s, int parts, bool serial) {
     const ColMaps &m = *w.cmaps;
-    // whole block: (J, r); gather: (r, J) over 32-column blocks, the splits of a block side by side
-    const dim3 ga = ops.col_gather ? dim3(ops.col_splits, ops.np / kCWWide) : dim3(ops.np / kCW, ops.col_splits);
-    const size_t sm = (size_t)ops.col_smem;
+    const int units = ops.col_gather ? ops.col_splits * (ops.np / kCWWide) : (ops.np / kCW) * ops.col_splits;
+    const dim3 ga(ops.col_gain_ctas + units);
+    const size_t sm = (size_t)ops.col_launch_smem;
     const CUtensorMap &tm = m.d[stage == 1 ? 0 : (stage == 3 ? 2 : 1)];
     const bool pdl = !serial;
-    if (serial && (parts & 4)) cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), s>>>(ops, w);
     if (parts & 1) {
-        if (!serial) {
-            // fork: the gain on the side stream, the SpMM here; join before the epilogue
-            cudaEventRecord(m.fork, s);
-            cudaStreamWaitEvent(m.side, m.fork, 0);
-            cols_gain_kernel<<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
-            cudaEventRecord(m.join, m.side);
-        }
         if (ops.col_gather) {
             switch (stage) {
                 case 1: launch_pdl(cols_gather_kernel<1>, ga, dim3(kANT), sm, s, pdl, ops, w); break;
@@ -395,7 +389,6 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
                 default: launch_pdl(cols_spmm_kernel<4>, ga, dim3(kANT), sm, s, pdl, tm, ops, w); break;
             }
         }
-        if (!serial) cudaStreamWaitEvent(s, m.join, 0);
     }
     if (parts & 2) {
         const dim3 ge(w.npairs);
@@ -406,6 +399,16 @@ void launch_cols_stage(int stage, const DevOps &ops, const MixedWork &w, cudaStr
             default: launch_pdl(cols_epi_kernel<4>, ge, dim3(kENT), 0, s, pdl, ops, w); break;
         }
     }
+}
+
+cudaError_t raise_smem_limit(const void *kernel, int bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace qpr

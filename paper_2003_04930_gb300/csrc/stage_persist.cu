@@ -222,9 +222,7 @@ int persist_grid(int np, int splits, int smem, int device, int *persist_smem, in
     return sms;
 }
 
-cudaError_t set_persist_smem(int bytes) {
-    return cudaFuncSetAttribute(cols_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
+cudaError_t set_persist_smem(int bytes) { return raise_smem_limit_t(cols_block_kernel, bytes); }
 
 cudaError_t launch_cols_block(const DevOps &ops, const MixedWork &w, int steps, int grid, cudaStream_t s) {
     ColMaps maps = *w.cmaps;

@@ -27,8 +27,8 @@
 // stage 6 takes the controller's decision (one thread, FP64): accept when
 // |z - y| <= Tol h (then the other pair becomes the state), s = (Tol h / (2 |z - y|))^(1/4) clipped to
 // [1/10, 4], next h = min(s h, h_max) (shortened to end a trajectory at its
-// end time). Every stage is gain (forked beside the SpMM), SpMM, epilogue,
-// exactly as an RK4 stage of the column-block form.
+// end time). Every stage is an SpMM launch (whose leading CTAs form the gain)
+// and an epilogue launch, exactly as an RK4 stage of the column-block form.
 #include <math.h>
 
 #include "cols_body.cuh"
@@ -66,36 +66,45 @@ __device__ __forceinline__ float *rkf_output(const MixedWork &w) {
 
 __device__ __forceinline__ int read_cur(const MixedWork &w) { return *(volatile int *)&w.ctl->rk_cur; }
 
+// The SpMM kernels of stage S: the leading ops.col_gain_ctas CTAs form the
+// gain of the stage input (stage 1 from the compact diagonal of the current
+// delta, later stages from the one the previous epilogue wrote), the others
+// one product unit each, as in the RK4 kernels.
+template <int S>
+__device__ __forceinline__ const float *rkf_pv(const DevOps &ops, const MixedWork &w) {
+    return (S == 1) ? w.pvd + (size_t)read_cur(w) * ops.np : w.pv;
+}
+
 template <int S>
 __global__ void __launch_bounds__(kANT) rkf_spmm_kernel(const __grid_constant__ CUtensorMap tm_d0,
                                                         const __grid_constant__ CUtensorMap tm_d1,
                                                         const __grid_constant__ CUtensorMap tm_a,
                                                         const __grid_constant__ CUtensorMap tm_b, DevOps ops,
                                                         MixedWork w) {
+    const int b = blockIdx.x, ng = ops.col_gain_ctas;
+    if (b < ng) {
+        gain_role(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
+        return;
+    }
+    const int u = b - ng, ncb = ops.np / kCW;
     spmm_block_body(
         [&]() -> const CUtensorMap * {
             if (S == 1) return read_cur(w) ? &tm_d1 : &tm_d0;
             return (S & 1) ? &tm_b : &tm_a;
         },
-        ops, w, blockIdx.x, blockIdx.y);
+        ops, w, u % ncb, u / ncb);
 }
 
 template <int S>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) rkf_gather_kernel(DevOps ops, MixedWork w) {
-    spmm_gather_body([&] { return rkf_input<S>(w, S == 1 ? read_cur(w) : 0); }, ops, w, blockIdx.x, blockIdx.y);
-}
-
-// The gain of the stage input: stage 1 from the compact diagonal of the
-// current delta, later stages from the one the previous epilogue wrote.
-template <int S>
-__global__ void __launch_bounds__(kANT) rkf_gain_kernel(DevOps ops, MixedWork w) {
-    extern __shared__ float sp_dyn[];
-    __shared__ int s_done;
-    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) return;
-    const float *pv = (S == 1) ? w.pvd + (size_t)read_cur(w) * ops.np : w.pv;
-    cta_gain(ops, w, blockIdx.x, gridDim.x, sp_dyn, pv);
+    const int b = blockIdx.x, ng = ops.col_gain_ctas;
+    if (b < ng) {
+        gain_role(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
+        return;
+    }
+    const int u = b - ng;
+    spmm_gather_body([&] { return rkf_input<S>(w, S == 1 ? read_cur(w) : 0); }, ops, w, u % ops.col_splits,
+                     u / ops.col_splits);
 }
 
 // Operands of one thread's elements e = tid + k kENT of tile (I, J).
@@ -487,25 +496,21 @@ void launch_ex(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, A..
 template <int S>
 void stage_s(const DevOps &ops, const MixedWork &w, cudaStream_t s) {
     const ColMaps &m = *w.cmaps;
-    cudaEventRecord(m.fork, s);
-    cudaStreamWaitEvent(m.side, m.fork, 0);
-    rkf_gain_kernel<S><<<m.gain_ctas, kANT, (size_t)ops.np * sizeof(float), m.side>>>(ops, w);
-    cudaEventRecord(m.join, m.side);
-    const size_t sm = (size_t)ops.col_smem;
+    const size_t sm = (size_t)ops.col_launch_smem;
     if (ops.col_gather) {
-        launch_ex(rkf_gather_kernel<S>, dim3(ops.col_splits, ops.np / kCWWide), dim3(kANT), sm, s, ops, w);
+        const dim3 ga(ops.col_gain_ctas + ops.col_splits * (ops.np / kCWWide));
+        launch_ex(rkf_gather_kernel<S>, ga, dim3(kANT), sm, s, ops, w);
     } else {
-        launch_ex(rkf_spmm_kernel<S>, dim3(ops.np / kCW, ops.col_splits), dim3(kANT), sm, s, m.d[0], m.d1, m.d[1],
-                  m.d[2], ops, w);
+        const dim3 ga(ops.col_gain_ctas + (ops.np / kCW) * ops.col_splits);
+        launch_ex(rkf_spmm_kernel<S>, ga, dim3(kANT), sm, s, m.d[0], m.d1, m.d[1], m.d[2], ops, w);
     }
-    cudaStreamWaitEvent(s, m.join, 0);
     launch_ex(rkf_epi_kernel<S>, dim3(w.npairs), dim3(kENT), 0, s, ops, w);
 }
 
 template <int S>
 cudaError_t set_rkf_smem(int bytes, bool gather) {
-    if (gather) return cudaFuncSetAttribute(rkf_gather_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return cudaFuncSetAttribute(rkf_spmm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (gather) return raise_smem_limit_t(rkf_gather_kernel<S>, bytes);
+    return raise_smem_limit_t(rkf_spmm_kernel<S>, bytes);
 }
 
 }  // namespace
