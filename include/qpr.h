@@ -358,13 +358,17 @@ typedef struct {
  * omegas, shared alpha, dt, tol and options), integrated together by the
  * mixed-precision RK4 form on the sparse backend (QPR_MIXED; options
  * h_diag, dangling, ref_refresh, adaptive_refresh, device and cuda_stream
- * apply). Each block
- * of ref_refresh steps is one set of kernel launches over the tile pairs of
- * every problem still running; a problem drops out as soon as its exact
- * FP64 residual passes tol or it reaches max_steps, so problems that
- * converge early cost nothing afterwards. Every problem's result is bitwise
- * the one qpr_steady_state returns for it alone with QPR_MIXED and
- * QPR_BACKEND_SPARSE. stats (nullable) receives one entry per problem
+ * apply). Each block of ref_refresh steps (with the exact refreshes that
+ * are due) is one captured CUDA graph over work lists of every problem still
+ * running: the column-block SpMM units in size classes of the padded edge
+ * (one launch each, with the class's own shared memory), the tile pairs of
+ * the epilogues. A problem whose exact FP64 residual passes tol (or that
+ * reaches max_steps) is retired on the device at once (its kernels return
+ * immediately) and leaves the lists when they are rebuilt. Every problem's
+ * result is bitwise the one qpr_steady_state returns for it alone with
+ * QPR_MIXED, QPR_BACKEND_SPARSE and the same stage form (COLUMNS where the
+ * whole column block fits, N padded to 32 <= 1536; TILES above).
+ * stats (nullable) receives one entry per problem
  * (seconds and kernel_launches are those of the whole call). Returns
  * QPR_OK when every problem converged, QPR_E_NOT_CONVERGED when some
  * reached max_steps, QPR_E_NONFINITE, QPR_E_ARG / QPR_E_GRAPH (message of

@@ -4,12 +4,15 @@
 //
 // Every problem keeps its own operators, buffers and control block; a
 // device array of per-problem descriptors lets one kernel launch serve all of
-// them. Work is described by lists the host compacts after every block of
-// steps: the active problems (one CTA per problem for the gain, trace and
-// residual kernels) and the (problem, I, J) tile pairs of the active problems
-// (grid-stride persistent kernels for the stage and refresh products). A
-// problem leaves the lists as soon as its exact FP64 residual passes (or it
-// hits max_steps), so converged problems cost nothing afterwards. The
+// them. Work is described by lists: the active problems (one CTA per problem
+// for the trace and gain kernels of the refresh), the (problem, column
+// block, split) units of the SpMM in size classes of the padded edge (each
+// class one launch with its own shared memory), and the (problem, I, J) tile
+// pairs (grid-stride persistent kernels for the epilogue and the refresh
+// products). A block of steps (the refreshes that are due, then ref_refresh
+// steps) is one captured CUDA graph over the lists; a problem that stops is
+// retired on the device (its kernels return at once) and leaves the lists
+// when they are rebuilt, once the active set has shrunk by a quarter. The
 // per-tile and per-problem arithmetic is the single-problem code (the same
 // device functions in the same order), so every problem's result is bitwise
 // the one qpr_steady_state returns for it alone with the same options.
@@ -56,49 +59,58 @@ __device__ __forceinline__ int graph_done(const BatchGraph &sg, int *s_flag) {
     return *s_flag;
 }
 
-__global__ void __launch_bounds__(256) b_trace_kernel(const BatchGraph *gs, const int *act) {
+// The refresh kernels skip problem g when it has stopped or, with a due
+// array (one byte per problem, written by the host before each block), when
+// its refresh is not due this block.
+__device__ __forceinline__ int skip_refresh(const BatchGraph &sg, int g, const uint8_t *due, int *s_flag) {
+    if (graph_done(sg, s_flag)) return 1;
+    return due && !due[g];
+}
+
+__global__ void __launch_bounds__(256) b_trace_kernel(const BatchGraph *gs, const int *act, const uint8_t *due) {
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     load_graph(gs, act[blockIdx.x], sg);
-    if (graph_done(sg, &s_flag)) return;
+    if (skip_refresh(sg, act[blockIdx.x], due, &s_flag)) return;
     mixed::refresh_trace_body(sg.ops, sg.mw);
 }
 
-__global__ void __launch_bounds__(256) b_normalize_kernel(const BatchGraph *gs, const int *act) {
+__global__ void __launch_bounds__(256) b_normalize_kernel(const BatchGraph *gs, const int *act,
+                                                          const uint8_t *due) {
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     load_graph(gs, act[blockIdx.y], sg);
-    if (graph_done(sg, &s_flag)) return;
+    if (skip_refresh(sg, act[blockIdx.y], due, &s_flag)) return;
     mixed::refresh_normalize_body(sg.ops, sg.mw, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                                   (size_t)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(256) b_gain64_kernel(const BatchGraph *gs, const int *act) {
+__global__ void __launch_bounds__(256) b_gain64_kernel(const BatchGraph *gs, const int *act, const uint8_t *due) {
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     load_graph(gs, act[blockIdx.x], sg);
-    if (graph_done(sg, &s_flag)) return;
+    if (skip_refresh(sg, act[blockIdx.x], due, &s_flag)) return;
     gain64::gain_fp64_body<0>(sg.ops, sg.w64, sg.w64.y, 0, 1);
 }
 
 __global__ void __launch_bounds__(sparse64::NTHREADS)
-b_sparse64_kernel(const BatchGraph *gs, const int4 *items, int nitems) {
+b_sparse64_kernel(const BatchGraph *gs, const int4 *items, int nitems, const uint8_t *due) {
     extern __shared__ __align__(16) double smem[];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 t = items[it];
         load_graph(gs, t.x, sg);
-        if (!graph_done(sg, &s_flag)) sparse64::tile<0>(sg.ops, sg.w64, t.y, t.z, t.w, t.w == 0, smem);
+        if (!skip_refresh(sg, t.x, due, &s_flag)) sparse64::tile<0>(sg.ops, sg.w64, t.y, t.z, t.w, t.w == 0, smem);
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const int *act) {
+__global__ void __launch_bounds__(256) b_post_kernel(const BatchGraph *gs, const int *act, const uint8_t *due) {
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
     load_graph(gs, act[blockIdx.y], sg);
-    if (graph_done(sg, &s_flag)) return;
+    if (skip_refresh(sg, act[blockIdx.y], due, &s_flag)) return;
     mixed::refresh_post_body(sg.ops, sg.mw, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                              (size_t)gridDim.x * blockDim.x, blockIdx.x == 0);
 }
@@ -233,15 +245,35 @@ cudaError_t set_b_attr() {
                                 mixed::kMixedDynSmem);
 }
 
+// Size classes of the column-block SpMM: problems whose padded edge is at
+// most kClassNp[c] share one launch whose dynamic shared memory is the
+// largest plan of the class, so small problems are not held to the shared
+// memory (and the one CTA per SM) of the largest.
+constexpr int kClasses = 4;
+constexpr int kClassNp[kClasses] = {256, 512, 768, 1 << 30};
+int np_class(int np) {
+    int c = 0;
+    while (c + 1 < kClasses && np > kClassNp[c]) ++c;
+    return c;
+}
+
 struct Lists {
     int *act;      // device, active problem indices
     int4 *items;   // device, (problem, I, J, pair index) of the active problems
     int nact, nitems;
-    // per stage: column-block SpMM items (problem, J, split), the pairs of
-    // the column-form problems and the pairs of the tile-form problems
-    int4 *items_a, *items_b, *items_t;
-    int na, nb, nt;
-    int smem_a;    // dynamic shared memory of the SpMM kernel
+    // per stage: column-block SpMM items (problem, J, split) per size class,
+    // the pairs of the column-form problems and the pairs of the tile-form
+    // problems
+    int4 *items_a[kClasses];
+    int na[kClasses], smem_a[kClasses], grid_a[kClasses];
+    int4 *items_b, *items_t;
+    int nb, nt;
+};
+
+// Device buffers one set of lists is uploaded into.
+struct ListBufs {
+    int *act = nullptr;
+    int4 *items = nullptr, *items_a = nullptr, *items_b = nullptr, *items_t = nullptr;
 };
 
 int elem_chunks(int np) {
@@ -250,24 +282,31 @@ int elem_chunks(int np) {
     return (int)std::min<size_t>(std::max<size_t>(c, 1), 64);
 }
 
-void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream_t s, int64_t &launches) {
+void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream_t s, int64_t &launches,
+                    const uint8_t *due = nullptr) {
     if (L.nact == 0) return;
     const dim3 eg(elem_chunks(max_np), L.nact);
-    b_trace_kernel<<<L.nact, 256, 0, s>>>(gs, L.act);
-    b_normalize_kernel<<<eg, 256, 0, s>>>(gs, L.act);
-    b_gain64_kernel<<<L.nact, 256, 0, s>>>(gs, L.act);
+    b_trace_kernel<<<L.nact, 256, 0, s>>>(gs, L.act, due);
+    b_normalize_kernel<<<eg, 256, 0, s>>>(gs, L.act, due);
+    b_gain64_kernel<<<L.nact, 256, 0, s>>>(gs, L.act, due);
     b_sparse64_kernel<<<std::min(L.nitems, 152 * 3), sparse64::NTHREADS, sparse64::SMEM_BYTES, s>>>(gs, L.items,
-                                                                                                     L.nitems);
-    b_post_kernel<<<eg, 256, 0, s>>>(gs, L.act);
+                                                                                                     L.nitems, due);
+    b_post_kernel<<<eg, 256, 0, s>>>(gs, L.act, due);
     launches += 5;
 }
 
 template <int STAGE>
 void launch_stage_b(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
-    if (L.na) {
-        b_cols_spmm_kernel<STAGE><<<std::min(L.na, 152 * 2), cols::kANT, L.smem_a, s>>>(gs, L.items_a, L.na);
+    bool any = false;
+    for (int c = 0; c < kClasses; ++c)
+        if (L.na[c]) {
+            b_cols_spmm_kernel<STAGE><<<L.grid_a[c], cols::kANT, L.smem_a[c], s>>>(gs, L.items_a[c], L.na[c]);
+            launches += 1;
+            any = true;
+        }
+    if (any) {
         b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 3), cols::kENT, 0, s>>>(gs, L.items_b, L.nb);
-        launches += 2;
+        launches += 1;
     }
     if (L.nt) {
         b_stage_mixed_kernel<STAGE><<<std::min(L.nt, 152 * 3), kStageNT, mixed::kMixedDynSmem, s>>>(gs, L.items_t,
@@ -330,6 +369,13 @@ cudaError_t init_batch() {
     if (e == cudaSuccess) e = set_b_attr<3>();
     if (e == cudaSuccess) e = set_b_attr<4>();
     if (e == cudaSuccess) e = init_stage_mixed();
+    return e;
+}
+
+cudaError_t bcols_ctas_per_sm(int bytes, int *ctas) {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, b_cols_spmm_kernel<1>, cols::kANT, bytes);
+    *ctas = (e == cudaSuccess && n > 0) ? n : 1;
     return e;
 }
 
@@ -440,6 +486,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     std::vector<size_t> okh(G), oci(G), opc(G), oxc(G);
     size_t nkh = 0, nci = 0, npc = 0, nxc = 0, na_max = 0;
     int smem_a = 0;
+    int smem_class[qpr::kClasses] = {0, 0, 0, 0};
     for (size_t g = 0; g < G; ++g) {
         // one split where it fits: the batch fills the SMs with many problems
         if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g], 1)) {
@@ -460,6 +507,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         nxc += qpr::align_up(2 * (size_t)np[g] * np[g], 64);
         na_max += (size_t)(np[g] / qpr::cols::kCW) * pl.splits;
         smem_a = std::max(smem_a, pl.smem);
+        smem_class[qpr::np_class(np[g])] = std::max(smem_class[qpr::np_class(np[g])], pl.smem);
     }
 
     qpr::BatchMem mem;
@@ -489,8 +537,13 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     BCUDA(mem.alloc(&dB, nb));
     BCUDA(mem.alloc(&dCtl, G));
     BCUDA(mem.alloc(&dG, G));
-    BCUDA(mem.alloc(&dAct, G));
-    BCUDA(mem.alloc(&dItems, total_pairs));
+    qpr::ListBufs gbuf, abuf;  // lists of the captured graph; lists of ad-hoc launches (confirming refreshes)
+    uint8_t *dDue = nullptr;
+    BCUDA(mem.alloc(&gbuf.act, G));
+    BCUDA(mem.alloc(&gbuf.items, total_pairs));
+    BCUDA(mem.alloc(&abuf.act, G));
+    BCUDA(mem.alloc(&abuf.items, total_pairs));
+    BCUDA(mem.alloc(&dDue, G));
     BCUDA(mem.alloc(&dIO, 2 * max_nn));
     int2 *dKH = nullptr;
     int *dCI = nullptr;
@@ -500,12 +553,20 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     BCUDA(mem.alloc(&dCI, nci));
     BCUDA(mem.alloc(&dPC, npc));
     BCUDA(mem.alloc(&dXC, nxc));
-    BCUDA(mem.alloc(&dItemsA, na_max));
-    BCUDA(mem.alloc(&dItemsB, total_pairs));
-    BCUDA(mem.alloc(&dItemsT, total_pairs));
+    for (qpr::ListBufs *b : {&gbuf, &abuf}) {
+        BCUDA(mem.alloc(&b->items_a, na_max));
+        BCUDA(mem.alloc(&b->items_b, total_pairs));
+        BCUDA(mem.alloc(&b->items_t, total_pairs));
+    }
+    // CTAs per SM of each class's SpMM launch (its dynamic shared memory)
+    int sms = 0, class_ctas[qpr::kClasses] = {1, 1, 1, 1};
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
     if (nxc) BCUDA(cudaMemset(dXC, 0, nxc * sizeof(float)));
     if (smem_a > 0) {
         BCUDA(qpr::set_bcols_smem(smem_a));
+        for (int c = 0; c < qpr::kClasses; ++c)
+            if (smem_class[c] > 0) BCUDA(qpr::bcols_ctas_per_sm(smem_class[c], &class_ctas[c]));
     }
     for (size_t g = 0; g < G; ++g) {
         if (!colg[g]) continue;
@@ -658,9 +719,10 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     // ---- blocks of (exact refresh + ref_refresh delta steps) ----
     std::vector<int> active(G);
     for (size_t g = 0; g < G; ++g) active[g] = (int)g;
-    std::vector<int4> items, items_a, items_b, items_t;
+    std::vector<int4> items, items_b, items_t;
     items.reserve(total_pairs);
-    auto make_lists = [&](const std::vector<int> &list, qpr::Lists &L) -> cudaError_t {
+    std::vector<int4> items_cls[qpr::kClasses];
+    auto make_lists = [&](const std::vector<int> &list, const qpr::ListBufs &bufs, qpr::Lists &L) -> cudaError_t {
         items.clear();
         for (int g : list) {
             int q = 0;
@@ -668,35 +730,43 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
                 for (int J = I + 1; J < T[g]; ++J) items.push_back(make_int4(g, I, J, q++));
             for (int I = 0; I < T[g]; ++I) items.push_back(make_int4(g, I, I, q++));
         }
-        items_a.clear();
         items_b.clear();
         items_t.clear();
+        for (int c = 0; c < qpr::kClasses; ++c) items_cls[c].clear();
         for (const int4 &t : items) (colg[t.x] ? items_b : items_t).push_back(t);
         for (int g : list)
             if (colg[g])
                 for (int r = 0; r < plans[g].splits; ++r)
-                    for (int J = 0; J < np[g] / qpr::cols::kCW; ++J) items_a.push_back(make_int4(g, J, r, 0));
-        L.act = dAct;
-        L.items = dItems;
+                    for (int J = 0; J < np[g] / qpr::cols::kCW; ++J)
+                        items_cls[qpr::np_class(np[g])].push_back(make_int4(g, J, r, 0));
+        L.act = bufs.act;
+        L.items = bufs.items;
         L.nact = (int)list.size();
         L.nitems = (int)items.size();
-        L.items_a = dItemsA;
-        L.items_b = dItemsB;
-        L.items_t = dItemsT;
-        L.na = (int)items_a.size();
+        size_t off = 0;
+        for (int c = 0; c < qpr::kClasses; ++c) {
+            L.items_a[c] = bufs.items_a + off;
+            L.na[c] = (int)items_cls[c].size();
+            L.smem_a[c] = smem_class[c];
+            L.grid_a[c] = std::max(1, std::min(L.na[c], sms * class_ctas[c]));
+            off += items_cls[c].size();
+        }
+        L.items_b = bufs.items_b;
+        L.items_t = bufs.items_t;
         L.nb = (int)items_b.size();
         L.nt = (int)items_t.size();
-        L.smem_a = smem_a;
-        cudaError_t e = cudaMemcpyAsync(dAct, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(bufs.act, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dItems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && !items_a.empty())
-            e = cudaMemcpyAsync(dItemsA, items_a.data(), items_a.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(bufs.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        for (int c = 0; c < qpr::kClasses && e == cudaSuccess; ++c)
+            if (!items_cls[c].empty())
+                e = cudaMemcpyAsync(L.items_a[c], items_cls[c].data(), items_cls[c].size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && !items_b.empty())
-            e = cudaMemcpyAsync(dItemsB, items_b.data(), items_b.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(bufs.items_b, items_b.data(), items_b.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && !items_t.empty())
-            e = cudaMemcpyAsync(dItemsT, items_t.data(), items_t.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
-        // the host vectors are reused: wait until both copies have read them
+            e = cudaMemcpyAsync(bufs.items_t, items_t.data(), items_t.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+        // the host vectors are reused: wait until the copies have read them
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e;
     };
@@ -710,22 +780,50 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     std::vector<char> due(G, 1);
     std::vector<int64_t> since(G, 0);
     std::vector<double> r0(G, -1.0);
-    while (!active.empty()) {
-        qpr::Lists L{};
-        std::vector<int> refresh_list;
-        for (int g : active)
-            if (due[g]) refresh_list.push_back(g);
-        if (!refresh_list.empty() && refresh_list.size() != active.size()) {
-            // refresh a subset: its own lists first (the stream orders their
-            // kernels before the copies of the next lists into the same buffers)
-            qpr::Lists Lr{};
-            BCUDA(make_lists(refresh_list, Lr));
-            qpr::launch_refresh(dG, Lr, max_np, s, launches);
+    // The captured block: the refresh kernels (a problem's refresh runs when
+    // its due flag is set; the host writes the flags before each launch) and
+    // `block` steps, over the lists of the active set at capture time.
+    // Problems that stop later keep their items in the lists (their kernels
+    // return at once, the device retires them) until the lists are rebuilt
+    // and the graph recaptured, once the active set has shrunk by a quarter.
+    qpr::Lists LG{};
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphGuard {
+        cudaGraphExec_t *g;
+        ~GraphGuard() {
+            if (*g) cudaGraphExecDestroy(*g);
         }
-        BCUDA(make_lists(active, L));
-        if (!refresh_list.empty() && refresh_list.size() == active.size())
-            qpr::launch_refresh(dG, L, max_np, s, launches);
-        for (int k = 0; k < block; ++k) qpr::launch_step(dG, L, s, launches);
+    } gguard{&gexec};
+    int64_t graph_launches = 0;
+    size_t captured = 0;
+    std::vector<uint8_t> hDue(G, 0);
+    auto recapture = [&]() -> cudaError_t {
+        if (gexec) {
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        }
+        cudaError_t e = make_lists(active, gbuf, LG);
+        if (e != cudaSuccess) return e;
+        captured = active.size();
+        graph_launches = 0;
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        qpr::launch_refresh(dG, LG, max_np, s, graph_launches, dDue);
+        for (int k = 0; k < block; ++k) qpr::launch_step(dG, LG, s, graph_launches);
+        e = cudaStreamEndCapture(s, &gr);
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&gexec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) gexec = nullptr;
+        return e;
+    };
+    BCUDA(recapture());
+    while (!active.empty()) {
+        for (int g : active) hDue[g] = due[g] ? 1 : 0;
+        BCUDA(cudaMemcpyAsync(dDue, hDue.data(), G, cudaMemcpyHostToDevice, s));
+        BCUDA(cudaGraphLaunch(gexec, s));
+        launches += graph_launches;
         for (int g : active) since[g] = (due[g] ? 0 : since[g]) + block;
         BCUDA(cudaMemcpyAsync(hCtl, dCtl, G * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         BCUDA(cudaStreamSynchronize(s));
@@ -759,7 +857,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
             }
             BCUDA(cudaMemcpyAsync(dCtl, hCtl, G * sizeof(Ctl), cudaMemcpyHostToDevice, s));
             qpr::Lists Lc{};
-            BCUDA(make_lists(confirm, Lc));
+            BCUDA(make_lists(confirm, abuf, Lc));
             qpr::launch_refresh(dG, Lc, max_np, s, launches);
             BCUDA(cudaMemcpyAsync(hCtl, dCtl, G * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
             BCUDA(cudaStreamSynchronize(s));
@@ -773,6 +871,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         }
         std::sort(keep.begin(), keep.end());
         active.swap(keep);
+        if (!active.empty() && 4 * active.size() <= 3 * captured) BCUDA(recapture());
     }
 
     // ---- results ----

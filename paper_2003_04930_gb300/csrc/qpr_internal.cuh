@@ -342,6 +342,8 @@ void set_create_error(const std::string &msg);
 // Opt in to the dynamic shared memory of the batched kernels (batch.cu).
 cudaError_t init_batch();
 cudaError_t set_bcols_smem(int bytes);
+// Resident CTAs per SM of the batched SpMM with `bytes` of dynamic shared memory.
+cudaError_t bcols_ctas_per_sm(int bytes, int *ctas);
 double estimate_spread(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int> &col,
                        const std::vector<double> &val);
 

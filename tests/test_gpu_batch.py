@@ -62,3 +62,27 @@ def test_batch_max_steps():
         assert s["steps"] == 40 and s["converged"] == 0
         ref = Oracle.from_edges(g, alpha=0.85, omega=om).evolve(graphs.maximally_mixed(g.n), 0.01, 40)
         assert np.linalg.norm(rho.cpu().numpy() - ref) <= 1e-6
+
+
+def test_batch_size_classes_and_tile_fallback_bitwise():
+    # one problem in each size class of the batched SpMM (padded edge <= 256,
+    # 512, 768, above) and one beyond the whole-block form (N = 1600: the
+    # tile-pair form); omegas spread so problems retire at different blocks
+    # and the captured lists are rebuilt on the way
+    specs = [(100, 0.9, 2001), (300, 0.8, 2002), (600, 0.85, 2003), (900, 0.95, 2004), (1600, 0.9, 2005),
+             (120, 0.4, 2006), (80, 0.7, 2007), (60, 0.95, 2008)]
+    probs = []
+    for n, om, seed in specs:
+        g = graphs.heavy_tailed(n, seed)
+        probs.append((g, om, torch.from_numpy(graphs.maximally_mixed(n)).to(DEV)))
+    st, stats = Q.batch_steady_state(probs, ref_refresh=16)
+    assert st == Q.QPR_OK
+    for (g, om, rho), s in zip(probs, stats):
+        form = Q.QPR_SPARSE_FORM_TILES if g.n > 1536 else Q.QPR_SPARSE_FORM_COLUMNS
+        single = Solver.from_edges(g, alpha=0.85, omega=om, precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE,
+                                   ref_refresh=16, sparse_form=form)
+        r1 = torch.from_numpy(graphs.maximally_mixed(g.n)).to(DEV)
+        s1 = single.steady_state(r1, 0.01, 1e-8, 400000)
+        assert s["steps"] == s1["steps"] and s["converged"] == 1, g.n
+        assert s["residual"] == s1["residual"]
+        np.testing.assert_array_equal(rho.cpu().numpy(), r1.cpu().numpy())
