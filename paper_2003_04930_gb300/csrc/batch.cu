@@ -131,11 +131,13 @@ __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGrap
 
 // Column-block form: the SpMM over (problem, J, split) items. The split's
 // entries and bundles are staged with two bulk copies (one mbarrier), the
-// column block with plain loads, 8 in flight per thread (each problem has its
-// own layout, so no tensor map); the arithmetic is the single-problem form's
-// (warp_bundles, cta_gain), so the results are bitwise the same.
+// column block with plain loads (each problem has its own layout, so no
+// tensor map); the arithmetic is the single-problem form's (warp_bundles,
+// cta_gain), so the results are bitwise the same. Registers are capped for
+// two resident CTAs per SM, so that the small size classes (less shared
+// memory) overlap one CTA's staging with another's products.
 template <int STAGE>
-__global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
+__global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
                                                                  int nitems) {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     __shared__ BatchGraph sg;
@@ -171,12 +173,13 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
                         tma::load_bulk(sP, ops.col_pieces + cols::kBundleInt4 * (size_t)p_base, p_bytes, &bar);
                 }
             }
-            // the column block with plain loads, 8 float4 in flight per thread
-            // (parts 0..3: real quads, 4..7: imaginary quads of a row)
-            for (int u0 = threadIdx.x; u0 < np * 8; u0 += 8 * (int)blockDim.x) {
-                float4 v[8];
+            // the column block with plain loads, kStageLoads float4 in flight per
+            // thread (parts 0..3: real quads, 4..7: imaginary quads of a row)
+            constexpr int kStageLoads = 4;  // (8 spilled under the 2-CTA register cap)
+            for (int u0 = threadIdx.x; u0 < np * 8; u0 += kStageLoads * (int)blockDim.x) {
+                float4 v[kStageLoads];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < kStageLoads; ++i) {
                     const int u = u0 + i * (int)blockDim.x;
                     if (u < np * 8) {
                         const int k = u >> 3, part = u & 7;
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(cols::kANT) b_cols_spmm_kernel(const BatchGrap
                     }
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < kStageLoads; ++i) {
                     const int u = u0 + i * (int)blockDim.x;
                     if (u < np * 8) *reinterpret_cast<float4 *>(sD + (u >> 3) * cols::kRowFloats + 4 * (u & 7)) = v[i];
                 }
@@ -248,9 +251,11 @@ cudaError_t set_b_attr() {
 // Size classes of the column-block SpMM: problems whose padded edge is at
 // most kClassNp[c] share one launch whose dynamic shared memory is the
 // largest plan of the class, so small problems are not held to the shared
-// memory (and the one CTA per SM) of the largest.
-constexpr int kClasses = 4;
-constexpr int kClassNp[kClasses] = {256, 512, 768, 1 << 30};
+// memory (and the one CTA per SM) of the largest: up to np = 512 two CTAs fit
+// an SM. Within a launch the units go largest problem first (the grid-stride
+// loop then ends on short units).
+constexpr int kClasses = 2;
+constexpr int kClassNp[kClasses] = {512, 1 << 30};
 int np_class(int np) {
     int c = 0;
     while (c + 1 < kClasses && np > kClassNp[c]) ++c;
@@ -486,7 +491,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     std::vector<size_t> okh(G), oci(G), opc(G), oxc(G);
     size_t nkh = 0, nci = 0, npc = 0, nxc = 0, na_max = 0;
     int smem_a = 0;
-    int smem_class[qpr::kClasses] = {0, 0, 0, 0};
+    int smem_class[qpr::kClasses] = {};
     for (size_t g = 0; g < G; ++g) {
         // one split where it fits: the batch fills the SMs with many problems
         if (o.sparse_form == QPR_SPARSE_FORM_TILES || !qpr::plan_columns(H[g], np[g], dev, plans[g], 1)) {
@@ -559,7 +564,8 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         BCUDA(mem.alloc(&b->items_t, total_pairs));
     }
     // CTAs per SM of each class's SpMM launch (its dynamic shared memory)
-    int sms = 0, class_ctas[qpr::kClasses] = {1, 1, 1, 1};
+    int sms = 0, class_ctas[qpr::kClasses];
+    for (int &c : class_ctas) c = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
     if (nxc) BCUDA(cudaMemset(dXC, 0, nxc * sizeof(float)));
@@ -734,7 +740,9 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         items_t.clear();
         for (int c = 0; c < qpr::kClasses; ++c) items_cls[c].clear();
         for (const int4 &t : items) (colg[t.x] ? items_b : items_t).push_back(t);
-        for (int g : list)
+        std::vector<int> by_size(list);
+        std::stable_sort(by_size.begin(), by_size.end(), [&](int a, int b) { return np[a] > np[b]; });
+        for (int g : by_size)
             if (colg[g])
                 for (int r = 0; r < plans[g].splits; ++r)
                     for (int J = 0; J < np[g] / qpr::cols::kCW; ++J)

@@ -65,10 +65,10 @@ def test_batch_max_steps():
 
 
 def test_batch_size_classes_and_tile_fallback_bitwise():
-    # one problem in each size class of the batched SpMM (padded edge <= 256,
-    # 512, 768, above) and one beyond the whole-block form (N = 1600: the
-    # tile-pair form); omegas spread so problems retire at different blocks
-    # and the captured lists are rebuilt on the way
+    # problems in both size classes of the batched SpMM (padded edge <= 512
+    # and above) and one beyond the whole-block form (N = 1600: the tile-pair
+    # form); omegas spread so problems retire at different blocks and the
+    # captured lists are rebuilt on the way
     specs = [(100, 0.9, 2001), (300, 0.8, 2002), (600, 0.85, 2003), (900, 0.95, 2004), (1600, 0.9, 2005),
              (120, 0.4, 2006), (80, 0.7, 2007), (60, 0.95, 2008)]
     probs = []
