@@ -131,7 +131,16 @@ __device__ __forceinline__ void spmm_gather_body(PickInput pick_input, const Dev
 // returns (written by the previous epilogue; called after the grid
 // dependency wait). The dynamic shared memory holds the staged diagonal (np
 // floats).
-template <typename PickPv>
+//
+// DECIDE (the stage-2 grid): CTA 0 first takes the stop decision of the
+// step from the stage-1 epilogue's residual partials (stage1_decision, the
+// same sum as the epilogue's last CTA would form: both kernels have 512
+// threads). The gain CTAs finish well before the product CTAs, so the
+// decision is off the critical path; the product CTAs of this grid do not
+// wait for it (a stage-2 product of a step that stops is scratch), and the
+// stage-2 epilogue, which reads `done` after its grid dependency wait,
+// leaves the state as it was.
+template <bool DECIDE = false, typename PickPv>
 __device__ __forceinline__ void gain_role(const DevOps &ops, const MixedWork &w, int b, int nb, PickPv pick_pv) {
     extern __shared__ uint8_t dyn_raw[];
     __shared__ int s_done;
@@ -140,6 +149,7 @@ __device__ __forceinline__ void gain_role(const DevOps &ops, const MixedWork &w,
     __syncthreads();
     if (s_done) return;
     tma::launch_dependents();
+    if (DECIDE && b == 0) stage1_decision(w, w.npairs, *(volatile long long *)&w.ctl->step, true);
     cta_gain(ops, w, b, nb, reinterpret_cast<float *>(dyn_raw), pick_pv());
 }
 

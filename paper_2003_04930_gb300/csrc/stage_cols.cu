@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__
                                                          MixedWork w) {
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
-        gain_role(ops, w, b, ng, [&] { return w.pv; });
+        gain_role<STAGE == 2>(ops, w, b, ng, [&] { return w.pv; });
         return;
     }
     const int u = b - ng, ncb = ops.np / kCW;
@@ -47,12 +47,15 @@ template <int STAGE>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(DevOps ops, MixedWork w) {
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
-        gain_role(ops, w, b, ng, [&] { return w.pv; });
+        gain_role<STAGE == 2>(ops, w, b, ng, [&] { return w.pv; });
         return;
     }
     const int u = b - ng;
     spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, u % ops.col_splits, u / ops.col_splits);
 }
+
+static_assert(kANT == kENT, "the stop decision sums the residual partials with the same block size in the "
+                            "stage-2 SpMM grid as in a stage-1 epilogue CTA");
 
 // Launched with programmatic dependent launch: the elementwise operands (the
 // stage input, F32, D, S, ...: written two kernels back, complete once the
@@ -73,7 +76,8 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     __syncthreads();
     if (s_done) return;
     tma::launch_dependents();
-    epilogue_pair_in<STAGE>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
+    // no ticket: the stage-2 SpMM grid takes the stop decision (gain_role)
+    epilogue_pair_in<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
 }
 
 int max_smem_optin(int device) {
