@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
             }
             const int warp = threadIdx.x >> 5;
             float *parts = reinterpret_cast<float *>(dyn_smem + ops.col_part_off);
-            cols::warp_bundles(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
+            cols::warp_bundles<false, false, 1>(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
                                ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X, parts);
             const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
             if (cb1 > cb0) {

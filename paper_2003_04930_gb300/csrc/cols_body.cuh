@@ -10,16 +10,20 @@
 // applies the RK4 stage to every tile pair (I, J), I <= J, from X_IJ and
 // X_JI, as the tile-pair form does.
 //
-// Work list: the rows of a split are cut into bundles handled by one warp:
-// 4 kRPG rows of similar length, kRPG per 8-lane group (lane p of a group
-// holds 4 of the 32 values of a staged row: one 16-byte read per nonzero, a
-// whole row per group, no bank conflict), or one row longer than kLongRow
-// nonzeros whose nonzeros are dealt to the 4 groups, kRPG at a time. A
-// bundle's CSR entries are stored interleaved and zero-padded to its T
-// rounds (round t, group g, slot s at 4 kRPG t + kRPG g + s), so each round is
-// kRPG / 2 16-byte entry reads and kRPG independent row reads per group,
-// without predicates. Bundles go to warps longest first, each to the least
-// loaded warp.
+// Work list: the rows of a split are cut into bundles handled by one warp.
+// Whole-block (narrow) layout: a bundle is 8 rows of similar length, one
+// per lane quad, or one row longer than kLongRow nonzeros whose nonzeros
+// are dealt to the 8 quads. Lane l of a quad holds 8 of the 32 values of a
+// staged row (two 16-byte chunks), the two quads of a quarter-warp reading
+// complementary halves of their rows so that their 8 lanes hit 8 distinct
+// bank quads whatever rows they read. A bundle's CSR entries are stored
+// interleaved and zero-padded to its T rounds (round t, quad q at 8 t + q),
+// so each round's 8 entries are 64 contiguous bytes (one 8-byte read per
+// lane: 2 wavefronts for 8 nonzeros, against 4 when 8 lanes share a row and
+// read its entry together). Gather (wide) layout: a pair of 8-lane groups
+// per row (one per plane of a 32-column block), kRPG rows per pair and
+// round (entries at 4 t + kRPG h + s). Bundles go to warps longest first,
+// each to the least loaded warp.
 #pragma once
 
 #include "mixed_body.cuh"
@@ -62,13 +66,15 @@ constexpr int kPiecePart = 2;      // bundle flags: one part of a cut row (its s
 // form there sums each row the same way.
 constexpr int kPartMax = 256;
 constexpr int kCutMaxWaves = 12;
-constexpr int kRPG = 2;            // rows (slots) per 8-lane group of a bundle (4 measured slower: more padding)
+constexpr int kRPG = 2;            // gather layout: rows (slots) per group pair and round
+constexpr int kNarrowRows = 8;     // whole-block layout: rows per round (one per lane quad)
 
-// A bundle descriptor is 1 + kRPG int4: {first entry (relative to its
-// split's entries, even), rounds T, flags, 0} and the rows of the 4 kRPG
-// slots, int4 k + 1 holding slot k of groups 0..3 (-1: none; a long-row
-// bundle has only the first).
-constexpr int kBundleInt4 = 1 + kRPG;
+// A bundle descriptor is 3 int4: {first entry (relative to its split's
+// entries, even), rounds T, flags, 0} and its row slots rows[0..7] (int4
+// 1 + j / 4, component j % 4; -1: none; a long-row bundle has only
+// rows[0]). Slot s of group g is rows[g + groups s]: rows[quad] in the
+// whole-block layout, rows[h + 2 s] (pair h) in the gather layout.
+constexpr int kBundleInt4 = 3;
 
 __device__ __forceinline__ float4 f4fma(float h, float4 v, float4 acc) { return mixed::f4fma(h, v, acc); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
@@ -76,24 +82,24 @@ __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
 }
 __device__ __forceinline__ int pick(int4 v, int g) { return (g == 0) ? v.x : (g == 1) ? v.y : (g == 2) ? v.z : v.w; }
 
-// Bundles [b0, b1) of one warp: X[row, J] for each row, from the staged
-// block sD ([row][kRowFloats]), the split's staged entries sKH and the
-// staged bundles sP (bundle b at sP[kBundleInt4 (b - p_base)]). Sums are
-// formed in a fixed order (per row in entry order; for a long row per group
-// kRPG interleaved sums added in slot order, then over the groups by
-// xor-shuffle), so the result does not depend on timing.
+// Bundles [b0, b1) of one warp in the gather layout: X[row, J] for each
+// row, from the split's staged entries sKH and bundles sP (bundle b at
+// sP[kBundleInt4 (b - p_base)]). Sums are formed in a fixed order (per row
+// in entry order; for a long row per group kRPG interleaved sums added in
+// slot order, then over the group pairs by xor-shuffle), so the result does
+// not depend on timing.
 //
-// GMEM (the gather form): sD is the stage input in global memory (two np x
-// np planes); row q's 16 values of block J are read there with L1-cached
-// loads (hub rows, referenced by many rows of a split, hit L1). The input
-// was written by the previous kernel; every load is issued after
-// griddepcontrol.wait, which makes that kernel's writes visible, and no
-// kernel reads the stage inputs through L1 before it.
-template <bool GMEM = false, bool WIDE = false>
-__device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
+// sD is the stage input in global memory (two np x np planes); row q's 32
+// values per plane of block J are read there with L1-cached loads (hub
+// rows, referenced by many rows of a split, hit L1). The input was written
+// by the previous kernel; every load is issued after griddepcontrol.wait,
+// which makes that kernel's writes visible, and no kernel reads the stage
+// inputs through L1 before it.
+template <bool GMEM = true, bool WIDE = true>
+__device__ __forceinline__ void wide_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
                                              float *__restrict__ X, float *parts) {
-    static_assert(!WIDE || GMEM, "the wide layout is the gather form's");
+    static_assert(WIDE && GMEM, "the wide layout is the gather form's");
     const int lane = threadIdx.x & 31, g = lane >> 3, p = lane & 7;
     const size_t plane = (size_t)np * np;
     // narrow: group g = one row, lanes 0-3 real and 4-7 imaginary values of
@@ -190,11 +196,80 @@ __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const
         } else {
 #pragma unroll
             for (int s = 0; s < kRPG; ++s) {
-                const int row = pick(bd[1 + s], h);
+                const int row = pick(bd[1], h + 2 * s);
                 if (row >= 0) put(row, acc[s]);
             }
         }
     }
+}
+
+// Bundles [b0, b1) of one warp in the whole-block layout: X[row, J] for
+// each row from the staged block sD ([row][kRowFloats]), the split's staged
+// entries sKH and bundles sP. Each row's sum runs over its entries in CSR
+// order (one FMA chain per column); a long row's 8 partial sums are added
+// by an xor butterfly over the quads. The result does not depend on timing.
+template <int UNROLL>
+__device__ __forceinline__ void narrow_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
+                                               const int4 *__restrict__ sP, int p_base, int b0, int b1, int J,
+                                               int np, float *__restrict__ X, float *parts) {
+    const int lane = threadIdx.x & 31, quad = lane >> 2, l = lane & 3, par = quad & 1;
+    const size_t plane = (size_t)np * np;
+    // lane l of a quad holds chunks 2l and 2l + 1 (16 bytes each) of a staged
+    // row; read i takes chunk 2l + (i ^ par), so the two quads of a
+    // quarter-warp read complementary halves of their rows (no bank conflict)
+    const int c0 = 2 * l + par, c1 = 2 * l + (1 - par);
+    const int o0 = 4 * c0, o1 = 4 * c1;
+    float *__restrict__ X0 = X + (c0 < 4 ? 0 : plane) + J * kCW + 4 * (c0 & 3);
+    float *__restrict__ X1 = X + (c1 < 4 ? 0 : plane) + J * kCW + 4 * (c1 & 3);
+    for (int b = b0; b < b1; ++b) {
+        const int4 *bd = sP + kBundleInt4 * (b - p_base);
+        const int4 d0 = bd[0];
+        const int2 *__restrict__ kh = sKH + d0.x + quad;
+        const int T = d0.y;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll UNROLL
+        for (int t = 0; t < T; ++t) {
+            const int2 e = kh[kNarrowRows * t];
+            const float hv = __int_as_float(e.y);
+            const float *__restrict__ row = sD + e.x * kRowFloats;
+            a0 = f4fma(hv, *reinterpret_cast<const float4 *>(row + o0), a0);
+            a1 = f4fma(hv, *reinterpret_cast<const float4 *>(row + o1), a1);
+        }
+        if (d0.z & kPieceLong) {
+            // chunks 2l and 2l + 1, then the sum over the 8 quads
+            float4 u0 = par ? a1 : a0, u1 = par ? a0 : a1;
+            u0 = mixed::f4xor(mixed::f4xor(mixed::f4xor(u0, 4), 8), 16);
+            u1 = mixed::f4xor(mixed::f4xor(mixed::f4xor(u1, 4), 8), 16);
+            if (quad == 0) {
+                const int row = bd[1].x;
+                if (d0.z & kPiecePart) {
+                    *reinterpret_cast<float4 *>(parts + row * kRowFloats + 8 * l) = u0;
+                    *reinterpret_cast<float4 *>(parts + row * kRowFloats + 8 * l + 4) = u1;
+                } else {
+                    // quad 0 has par = 0: c0 = 2l, c1 = 2l + 1
+                    *reinterpret_cast<float4 *>(X0 + (size_t)row * np) = u0;
+                    *reinterpret_cast<float4 *>(X1 + (size_t)row * np) = u1;
+                }
+            }
+        } else {
+            const int row = pick(bd[1 + (quad >> 2)], quad & 3);
+            if (row >= 0) {
+                *reinterpret_cast<float4 *>(X0 + (size_t)row * np) = a0;
+                *reinterpret_cast<float4 *>(X1 + (size_t)row * np) = a1;
+            }
+        }
+    }
+}
+
+// Bundles [b0, b1) of one warp: the whole-block layout from shared memory
+// (default), or the gather layout from global memory (GMEM, WIDE).
+template <bool GMEM = false, bool WIDE = false, int UNROLL = 2>
+__device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
+                                             const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
+                                             float *__restrict__ X, float *parts) {
+    static_assert(GMEM == WIDE, "whole-block layout from shared memory, gather layout from global memory");
+    if constexpr (WIDE) wide_bundles<true, true>(sD, sKH, sP, p_base, b0, b1, J, np, X, parts);
+    else narrow_bundles<UNROLL>(sD, sKH, sP, p_base, b0, b1, J, np, X, parts);
 }
 
 // The rows cut into parts, cuts[0 .. ncut) = {row, first slot, parts, 0}:
@@ -270,15 +345,15 @@ __device__ __forceinline__ void cta_gain(const DevOps &ops, const MixedWork &w, 
     }
 }
 
-// Stop decision after stage 1, taken by the last epilogue CTA to finish
-// (a ticket in the control block; release/acquire through fences): it sums
-// the nparts residual-estimate partials in index order, records the
-// estimate and, when the run stops here, sets done so that the kernels of
-// stages 2..4 return at once. A step whose exact residual a refresh already
-// decided is not decided again. Called by every thread after tile_epilogue.
-// Stop decision from the stage-1 partials of step `step` (every thread of
-// the CTA calls it; all CTAs that call it compute the same sum in index
-// order). Returns the status; the CTA with `record` writes it to ctl.
+// Stop decision from the nparts stage-1 residual-estimate partials of step
+// `step` (every thread of the CTA calls it; every caller forms the same sum
+// in index order with a 512-thread block): the CTA with `record` writes the
+// estimate to ctl and, when the run stops here, sets done so that the later
+// kernels of the step return at once. A step whose exact residual a refresh
+// already decided is not decided again. Returns the status. Callers: the
+// first gain CTA of the stage-2 SpMM grid (single-problem column forms, RK4
+// and RKF45), every CTA of the persistent form's stage 2, and the last CTA
+// of a problem's stage-1 epilogue in the batched solver.
 __device__ __forceinline__ int stage1_decision(const MixedWork &w, int nparts, long long step, bool record) {
     __shared__ float red[32];
     __shared__ int s_status;
@@ -308,6 +383,8 @@ __device__ __forceinline__ int stage1_decision(const MixedWork &w, int nparts, l
     return s_status;
 }
 
+// The last CTA to finish a stage-1 epilogue (a ticket in the control block;
+// release/acquire through fences) takes the stop decision.
 __device__ __forceinline__ void stage1_last_decides(const MixedWork &w, int nparts) {
     __shared__ int s_last;
     if (threadIdx.x == 0) {

@@ -94,22 +94,24 @@ int max_smem_optin(int device) {
 using RowEntries = std::vector<std::vector<int2>>;
 
 // Bundles of one split's rows [r0, r1) with the entries ent[i - r0]: long
-// rows alone, the others 4 kRPG at a time by decreasing length; dealt to the
-// warps longest first, each to the least loaded warp. Appends, per warp, the
-// bundles' descriptors and their interleaved, zero-padded entries (relative
-// offsets from `kh_base`), and the warps' first bundles.
+// rows alone, the others groups x rpg at a time by decreasing length; dealt
+// to the warps longest first, each to the least loaded warp. Appends, per
+// warp, the bundles' descriptors and their interleaved, zero-padded entries
+// (relative offsets from `kh_base`), and the warps' first bundles.
 // skip_empty: rows without entries get no bundle (their sums are kept
 // elsewhere); otherwise they get zero rounds, which store zeros. part_max >
 // 0: rows longer than part_max are cut into parts (bundles whose sums go to
 // partial slots 0, 1, ... of this block); each cut row appends {row, first
 // slot, parts, 0} to `cuts`. Returns the number of partial slots.
-// groups: row slots per round of a bundle, 4 (one per 8-lane group) or 2 (the
-// wide layout: one per group pair).
+// groups x rpg: row slots per round of a bundle, 8 x 1 (the whole-block
+// layout: one per lane quad) or 2 x kRPG (the gather layout: kRPG per group
+// pair).
 int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::vector<int2> &kh,
                   std::vector<int4> &pieces, std::vector<int> &wb, std::vector<int4> &cuts, int part_max,
-                  bool skip_empty = false, int groups = 4) {
-    constexpr int kMaxSlots = 4 * kRPG;
-    const int kSlots = groups * kRPG;
+                  bool skip_empty, int groups, int rpg) {
+    constexpr int kMaxSlots = 4 * (kBundleInt4 - 1);
+    const int kSlots = groups * rpg;
+    if (kSlots > kMaxSlots) return -1;
     struct Bundle {
         int rows[kMaxSlots];
         int T;
@@ -129,7 +131,7 @@ int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::ve
         b.part = false;
         b.src = -1;
         b.e0 = b.e1 = 0;
-        b.cost = (long long)kRPG * T + 8;
+        b.cost = (long long)rpg * T + 8;
         return b;
     };
     for (int i = r0; i < r1; ++i) {
@@ -181,17 +183,15 @@ int split_bundles(int r0, int r1, const RowEntries &ent, size_t kh_base, std::ve
             pieces.push_back(make_int4((int)(kh.size() - kh_base), b.T,
                                        (b.lng ? kPieceLong : 0) | (b.part ? kPiecePart : 0), 0));
             // slot s of group g is rows[g + groups s]
-            for (int s = 0; s < kRPG; ++s) {
-                const int *rw = b.rows + groups * s;
-                pieces.push_back(make_int4(rw[0], rw[1], groups > 2 ? rw[2] : -1, groups > 3 ? rw[3] : -1));
-            }
-            // round t, group g, slot s -> position kSlots t + kRPG g + s
+            for (int j = 0; j < kMaxSlots; j += 4)
+                pieces.push_back(make_int4(b.rows[j], b.rows[j + 1], b.rows[j + 2], b.rows[j + 3]));
+            // round t, group g, slot s -> position kSlots t + rpg g + s
             for (int t = 0; t < b.T; ++t)
                 for (int g = 0; g < groups; ++g)
-                    for (int sl = 0; sl < kRPG; ++sl) {
+                    for (int sl = 0; sl < rpg; ++sl) {
                         int2 v = make_int2(0, 0);
                         if (b.lng) {
-                            const int e = b.e0 + kSlots * t + kRPG * g + sl;
+                            const int e = b.e0 + kSlots * t + rpg * g + sl;
                             if (e < b.e1) v = ent[b.src - r0][e];
                         } else {
                             const int row = b.rows[g + groups * sl];
@@ -273,8 +273,10 @@ bool plan_columns(const HostOps &h, int np, int device, ColPlan &plan, int min_s
             pl.cutb.push_back((int)pl.cuts.size());
             RowEntries ent;
             for (int i = rows[k]; i < rows[k + 1]; ++i) ent.push_back(row_entries(h, i, 0, np));
-            slots_max = std::max(slots_max, split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb,
-                                                          pl.cuts, cut ? kPartMax : 0, false, gather ? 2 : 4));
+            const int ns = split_bundles(rows[k], rows[k + 1], ent, kb, pl.kh, pl.pieces, pl.wb, pl.cuts,
+                                         cut ? kPartMax : 0, false, gather ? 2 : kNarrowRows, gather ? kRPG : 1);
+            if (ns < 0) return false;
+            slots_max = std::max(slots_max, ns);
             if (pl.kh.size() % 2) pl.kh.push_back(make_int2(0, 0));
             pl.q.push_back((int)kb);
             pl.q.push_back((int)pl.kh.size());

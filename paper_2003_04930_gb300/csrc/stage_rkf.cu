@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kANT) rkf_spmm_kernel(const __grid_constant__ 
                                                         MixedWork w) {
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
-        gain_role(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
+        gain_role<S == 2>(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
         return;
     }
     const int u = b - ng, ncb = ops.np / kCW;
@@ -99,7 +99,7 @@ template <int S>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) rkf_gather_kernel(DevOps ops, MixedWork w) {
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
-        gain_role(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
+        gain_role<S == 2>(ops, w, b, ng, [&] { return rkf_pv<S>(ops, w); });
         return;
     }
     const int u = b - ng;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
         }
     }
     __syncthreads();
-    if (S == 1) stage1_last_decides(w, w.npairs);
+    // (the stop decision of stage 1 is taken by the stage-2 SpMM grid, gain_role)
     if (S == 6) rkf_decide(w, w.npairs);
 }
 
