@@ -3,6 +3,10 @@
 Each ``csrc/*.cu`` file is compiled by nvcc in parallel and the objects are
 linked into ``paper_2003_04930_gb300/_build/libqpr.so`` (static CUDA runtime,
 so the library loads with or without PyTorch in the process).
+
+``build_library(timeline=True)`` builds the diagnostic variant
+``_build/libqpr_timeline.so`` (-DQPR_TIMELINE: the column-block kernels
+record their timeline, include/qpr_timeline.h); it is never the product.
 """
 from __future__ import annotations
 
@@ -18,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpr.so")
+TIMELINE_LIB = os.path.join(BUILD, "libqpr_timeline.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -39,14 +44,16 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build_library(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+def build_library(force: bool = False, verbose: bool = False, extra_flags=None, timeline: bool = False) -> str:
+    lib = TIMELINE_LIB if timeline else LIB
+    objdir = os.path.join(BUILD, "timeline") if timeline else BUILD
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(objdir, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DQPR_TIMELINE"] if timeline else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [nvcc()] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -59,15 +66,15 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=None) 
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build_library(force="--force" in sys.argv, verbose=True))
+    print(build_library(force="--force" in sys.argv, verbose=True, timeline="--timeline" in sys.argv))

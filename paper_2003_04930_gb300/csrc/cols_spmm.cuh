@@ -8,6 +8,7 @@
 
 #include "cols_body.cuh"
 #include "qpr_internal.cuh"
+#include "timeline.cuh"
 #include "tma_util.cuh"
 
 namespace qpr {
@@ -19,8 +20,9 @@ namespace cols {
 // previous kernel wrote). Launched with programmatic dependent launch: the
 // prologue (barriers, this CTA's CSR entries and bundles, which no kernel
 // writes) overlaps the end of the previous kernel; the stage input is read
-// after grid_dependency_wait.
-template <typename PickMap>
+// after grid_dependency_wait. TL: record the timeline marks of the
+// diagnostic build (timeline.cuh).
+template <bool TL = false, typename PickMap>
 __device__ __forceinline__ void spmm_block_body(PickMap pick_map, const DevOps &ops, const MixedWork &w, int J,
                                                 int r) {
     extern __shared__ uint8_t dyn_raw[];
@@ -60,6 +62,7 @@ __device__ __forceinline__ void spmm_block_body(PickMap pick_map, const DevOps &
         for (int b = 0; b < np; b += kBoxRows) tma::load_3d(sD + (size_t)b * kRowFloats, tm, &bar_d, J * kCW, 0, b);
     }
     const bool ok = tma::mbar_wait(&bar_csr, 0) && tma::mbar_wait(&bar_d, 0);
+    timeline::mark<TL>(2);
     if (__syncthreads_or(!ok)) {
         // bounded wait gave up: report, give the copies one more bounded wait, return
         if (tid == 0) atomicExch(&w.ctl->err_timeout, 1);
@@ -74,6 +77,7 @@ __device__ __forceinline__ void spmm_block_body(PickMap pick_map, const DevOps &
         __syncthreads();
         combine_cuts(ops.col_cut + cb0, cb1 - cb0, parts, J, np, w.X);
     }
+    timeline::mark_all<TL>(3);
 }
 
 // Body of the gather form of the SpMM, for N too large to stage a column

@@ -31,27 +31,33 @@ using namespace cols;
 // stage input (gain_role), the others one (column block, row split) unit of
 // the product each (whole block: unit u = block u % ncb of split u / ncb;
 // gather: the splits of a block side by side).
+// (timeline::enter / leave and the body's marks record the kernel timeline
+// in the diagnostic build only; they are empty otherwise)
 template <int STAGE>
 __global__ void __launch_bounds__(kANT) cols_spmm_kernel(const __grid_constant__ CUtensorMap tm, DevOps ops,
                                                          MixedWork w) {
+    timeline::enter((STAGE - 1) * 2);
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
         gain_role<STAGE == 2>(ops, w, b, ng, [&] { return w.pv; });
-        return;
+    } else {
+        const int u = b - ng, ncb = ops.np / kCW;
+        spmm_block_body<true>([&] { return &tm; }, ops, w, u % ncb, u / ncb);
     }
-    const int u = b - ng, ncb = ops.np / kCW;
-    spmm_block_body([&] { return &tm; }, ops, w, u % ncb, u / ncb);
+    timeline::leave();
 }
 
 template <int STAGE>
 __global__ void __launch_bounds__(kANT, kGatherCtasPerSm) cols_gather_kernel(DevOps ops, MixedWork w) {
+    timeline::enter((STAGE - 1) * 2);
     const int b = blockIdx.x, ng = ops.col_gain_ctas;
     if (b < ng) {
         gain_role<STAGE == 2>(ops, w, b, ng, [&] { return w.pv; });
-        return;
+    } else {
+        const int u = b - ng;
+        spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, u % ops.col_splits, u / ops.col_splits);
     }
-    const int u = b - ng;
-    spmm_gather_body([&] { return stage_input<STAGE>(w); }, ops, w, u % ops.col_splits, u / ops.col_splits);
+    timeline::leave();
 }
 
 static_assert(kANT == kENT, "the stop decision sums the residual partials with the same block size in the "
@@ -68,16 +74,20 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     __shared__ __align__(16) float sO[4 * TS * LDO];
     __shared__ float sg[TS];
     __shared__ int s_done;
+    timeline::enter((STAGE - 1) * 2 + 1);
     const int2 pr = w.pairs[blockIdx.x];
     mixed::EpiIn<STAGE, kENT> in;
     mixed::epi_load<STAGE, kENT>(ops, w, pr.x, pr.y, in);
     tma::grid_dependency_wait();
     if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
     __syncthreads();
-    if (s_done) return;
-    tma::launch_dependents();
-    // no ticket: the stage-2 SpMM grid takes the stop decision (gain_role)
-    epilogue_pair_in<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO, in);
+    if (!s_done) {
+        tma::launch_dependents();
+        // no ticket: the stage-2 SpMM grid takes the stop decision (gain_role)
+        epilogue_pair_in<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO,
+                                       in);
+    }
+    timeline::leave();
 }
 
 int max_smem_optin(int device) {
@@ -418,3 +428,30 @@ cudaError_t raise_smem_limit(const void *kernel, int bytes) {
 }
 
 }  // namespace qpr
+
+#ifdef QPR_TIMELINE
+// Entry points of the diagnostic build (include/qpr_timeline.h).
+extern "C" {
+__attribute__((visibility("default"))) int qpr_timeline_reset(void) {
+    using namespace qpr::timeline;
+    static unsigned long long h[kKinds][kInst][2 * kFields];
+    for (int k = 0; k < kKinds; ++k)
+        for (int i = 0; i < kInst; ++i)
+            for (int f = 0; f < kFields; ++f) {
+                h[k][i][2 * f] = ~0ull;  // first: a minimum
+                h[k][i][2 * f + 1] = 0;  // last: a maximum
+            }
+    const unsigned long long z[kKinds] = {0};
+    if (cudaMemcpyToSymbol(g_stamp, h, sizeof(h)) != cudaSuccess) return 1;
+    if (cudaMemcpyToSymbol(g_count, z, sizeof(z)) != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}
+__attribute__((visibility("default"))) int qpr_timeline_read(unsigned long long *stamps,
+                                                            unsigned long long *counts) {
+    using namespace qpr::timeline;
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(stamps, g_stamp, sizeof(g_stamp)) != cudaSuccess) return 1;
+    return cudaMemcpyFromSymbol(counts, g_count, sizeof(g_count)) == cudaSuccess ? 0 : 1;
+}
+}
+#endif
