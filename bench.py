@@ -486,8 +486,8 @@ def form_name(s, prec):
 # (`dram__bytes_read.sum + dram__bytes_write.sum` of the stage-1 launch,
 # profiles/traffic_cols_n922_n4096.md), keyed by (kernel, N); a kernel
 # changed since its capture has no entry.
-NCU_TRAFFIC = {("cols_spmm_kernel", 922): 7114000, ("cols_epi_kernel", 922): 14045000,
-               ("cols_gather_kernel", 4096): 135473000 + 101318000, ("cols_epi_kernel", 4096): 269644000 + 101282000}
+NCU_TRAFFIC = {("cols_spmm_kernel", 922): 7115776, ("cols_epi_kernel", 922): 14042112,
+               ("cols_gather_kernel", 4096): 135333888 + 100642816, ("cols_epi_kernel", 4096): 269617152 + 100662784}
 
 
 def roofline(s, g, n, prof, peaks, peak_src, prec):
