@@ -707,29 +707,60 @@ def batch_case(a, local):
             "converged": int(sum(x["converged"] for x in stats)), "gpu_launches": int(stats[0]["kernel_launches"])}
 
 
+def shard_time(local_total, steps, dist=None, device=None):
+    """Shards (the batch split over the ranks, every rank solving its own
+    problems): the batch is done when the slowest rank is, so the time per
+    step is the max over ranks of the timed totals over the steps. Returns
+    (seconds per step, max total)."""
+    import torch
+
+    total = float(local_total)
+    if dist is not None:
+        t = torch.tensor([total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total / steps, total
+
+
 def run_batch(a):
-    """One step = one qpr_batch_steady_state call over the whole batch."""
+    """One step = one qpr_batch_steady_state call over the whole batch; with
+    N ranks each rank solves its shard of the problems (shard.partition, no
+    collective on the data path) and the step ends with the slowest rank."""
     import numpy as np
     import torch
 
-    from paper_2003_04930_gb300 import graphs, qpr
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2003_04930_gb300 import graphs, qpr, shard
     from paper_2003_04930_gb300.build import build_library
     build_library()
     specs = graphs.batch_specs(a.batch_count)
-    gs = [graphs.heavy_tailed(n, seed) for n, om, seed in specs]
-    rho0 = [torch.from_numpy(graphs.maximally_mixed(g.n)).cuda() for g in gs]
+    mine = shard.partition([shard.batch_cost(n, om) for n, om, seed in specs], world)[rank]
+    gs = [graphs.heavy_tailed(specs[i][0], specs[i][2]) for i in mine]
+    rho0 = [torch.from_numpy(graphs.maximally_mixed(g.n)).to(dev) for g in gs]
     rho = [r.clone() for r in rho0]
-    probs = [(g, om, r) for g, (n, om, seed), r in zip(gs, specs, rho)]
+    probs = [(g, specs[i][1], r) for g, i, r in zip(gs, mine, rho)]
 
     def solve():
         for r, r0 in zip(rho, rho0):
             r.copy_(r0)
-        return qpr.batch_steady_state(probs, dt=a.dt, tol=a.tol, max_steps=a.max_steps, ref_refresh=a.ref_refresh)
+        return qpr.batch_steady_state(probs, dt=a.dt, tol=a.tol, max_steps=a.max_steps, ref_refresh=a.ref_refresh,
+                                      device=local)
 
     for _ in range(a.warmup):
         solve()
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(local)
     sampler.start()
     times, stats = [], None
     for _ in range(a.steps):
@@ -740,19 +771,36 @@ def run_batch(a):
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     clocks = sampler.stop()
+    value, _ = shard_time(sum(times), a.steps, dist, dev)
     steps = [s["steps"] for s in stats]
-    value = sum(times) / a.steps
+    loc = torch.tensor([max(steps), float(np.sum(steps)), len(steps), sum(s["converged"] for s in stats),
+                        int(stats[0]["kernel_launches"])], dtype=torch.float64, device=dev)
+    if dist is not None:
+        parts = [torch.zeros_like(loc) for _ in range(world)]
+        dist.all_gather(parts, loc)
+        dist.destroy_process_group()
+    else:
+        parts = [loc]
+    if rank != 0:
+        return 0
+    parts = [p.cpu().tolist() for p in parts]
     line = {"metric": "time-to-steady-state of the whole batch (resid 1e-8)", "value": value, "unit": "s",
-            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
+            "higher_is_better": False, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{a.batch_count} heavy-tailed graphs, N ~ U[32,1024], omega ~ U[0.1,0.95], "
                                    f"alpha=0.85, rho0=I/N, RK4 dt={a.dt}, tol={a.tol}",
-                       "sum_n2": int(sum(g.n ** 2 for g in gs)), "ref_refresh": a.ref_refresh},
-            "rk4_steps_max": max(steps), "rk4_steps_mean": float(np.mean(steps)),
-            "converged": int(sum(s["converged"] for s in stats)), "clocks": clocks,
-            "gpu_launches": int(stats[0]["kernel_launches"])}
+                       "sum_n2": int(sum(n * n for n, om, seed in specs)), "ref_refresh": a.ref_refresh,
+                       "parallelism": f"batch shards {world}" if world > 1 else "one batch",
+                       "problems_per_rank": [int(p[2]) for p in parts]},
+            "rk4_steps_max": int(max(p[0] for p in parts)),
+            "rk4_steps_mean": float(sum(p[1] for p in parts) / sum(p[2] for p in parts)),
+            "converged": int(sum(p[3] for p in parts)), "clocks": clocks,
+            "gpu_launches": int(a.steps * sum(p[4] for p in parts))}
     print(json.dumps(line), flush=True)
     return 0
 
