@@ -68,6 +68,7 @@ constexpr int kPartMax = 256;
 constexpr int kCutMaxWaves = 12;
 constexpr int kRPG = 2;            // gather layout: rows (slots) per group pair and round
 constexpr int kNarrowRows = 8;     // whole-block layout: rows per round (one per lane quad)
+constexpr int kNarrowUnroll = 4;   // whole-block layout: rounds whose shared-memory reads are issued together
 
 // A bundle descriptor is 3 int4: {first entry (relative to its split's
 // entries, even), rounds T, flags, 0} and its row slots rows[0..7] (int4
@@ -227,8 +228,28 @@ __device__ __forceinline__ void narrow_bundles(const float *__restrict__ sD, con
         const int2 *__restrict__ kh = sKH + d0.x + quad;
         const int T = d0.y;
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-#pragma unroll UNROLL
-        for (int t = 0; t < T; ++t) {
+        int t = 0;
+        // UNROLL rounds at a time: their entries, then their row reads, then
+        // the FMAs in round order (the same sums as one round at a time)
+        for (; UNROLL > 1 && t + UNROLL <= T; t += UNROLL) {
+            int2 e[UNROLL];
+            float4 v0[UNROLL], v1[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) e[u] = kh[kNarrowRows * (t + u)];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const float *__restrict__ row = sD + e[u].x * kRowFloats;
+                v0[u] = *reinterpret_cast<const float4 *>(row + o0);
+                v1[u] = *reinterpret_cast<const float4 *>(row + o1);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                a0 = f4fma(__int_as_float(e[u].y), v0[u], a0);
+                a1 = f4fma(__int_as_float(e[u].y), v1[u], a1);
+            }
+        }
+#pragma unroll 1
+        for (; t < T; ++t) {
             const int2 e = kh[kNarrowRows * t];
             const float hv = __int_as_float(e.y);
             const float *__restrict__ row = sD + e.x * kRowFloats;
@@ -263,7 +284,7 @@ __device__ __forceinline__ void narrow_bundles(const float *__restrict__ sD, con
 
 // Bundles [b0, b1) of one warp: the whole-block layout from shared memory
 // (default), or the gather layout from global memory (GMEM, WIDE).
-template <bool GMEM = false, bool WIDE = false, int UNROLL = 2>
+template <bool GMEM = false, bool WIDE = false, int UNROLL = kNarrowUnroll>
 __device__ __forceinline__ void warp_bundles(const float *__restrict__ sD, const int2 *__restrict__ sKH,
                                              const int4 *__restrict__ sP, int p_base, int b0, int b1, int J, int np,
                                              float *__restrict__ X, float *parts) {
