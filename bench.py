@@ -630,6 +630,32 @@ def warm_solve(s, g, omega, a, local, rho, flush, reps):
                        "steady states (N in [64, 1024])"}
 
 
+def tuned_solve(g, a, local, rho0, rho_solved, flush, t_fixed):
+    """The autotuner's choice (qpr_autotune: backend, stage form, row splits,
+    then the reference-refresh block, timed on the device; no cache file),
+    one untimed and one timed solve of it, and its steady state against the
+    fixed rule's."""
+    import torch
+    from paper_2003_04930_gb300 import Solver, qpr
+    t0 = time.perf_counter()
+    r = qpr.autotune(g, a.omega, dt=a.dt, precision=qpr.QPR_MIXED, device=local)
+    tune_s = time.perf_counter() - t0
+    st = Solver.from_edges(g, alpha=0.85, omega=a.omega, precision=qpr.QPR_MIXED, device=local,
+                           **qpr.tuned_options(r))
+    rho = torch.empty_like(rho0)
+    rho.copy_(rho0)
+    st.steady_state(rho, a.dt, a.tol, a.max_steps)
+    t, stt = timed_solve(st, rho, rho0, a, flush)
+    p, pr = st.populations(rho), st.populations(rho_solved)
+    out = {"choice": {k: r[k] for k in ("backend", "sparse_form", "row_splits", "ref_refresh")},
+           "sparse_plan": st.sparse_plan, "tune_s": tune_s, "tuner_ms_per_step": r["ms_per_step"],
+           "time_to_steady_state_s": t, "steps": stt["steps"], "fixed_rule_s": t_fixed,
+           "speedup_vs_fixed_rule": t_fixed / t,
+           "max_dp_rel_vs_fixed_rule": float(abs(p - pr).max() / abs(pr).max())}
+    st.close()
+    return out
+
+
 def large_case(a, local, peaks, peak_src, flush):
     """The metric's second size: the same generator at N = 4096 (seed 3),
     omega = 0.8. Mixed cold and warm-started solves (one timed each after one
@@ -663,6 +689,7 @@ def large_case(a, local, peaks, peak_src, flush):
     if ws is not None:
         out["warm_start"] = ws
     out["rkf45"] = rkf45_solve(s, la, rho0, rho_solved, flush, 1, t_cold, st["steps"])
+    out["autotuned"] = tuned_solve(g, la, local, rho0, rho_solved, flush, t_cold)
     s.close()
     out["fp64_sparse"] = fp64_sparse_solve(g, la, local, rho0, rho_solved, flush, warm=False)
     out["plain_fp64_dense"] = dense_projection(g, la.omega, local, rho_solved, la.dt, st["steps"], peaks, peak_src,
