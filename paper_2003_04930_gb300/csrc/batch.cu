@@ -36,7 +36,8 @@ namespace qpr {
 struct BatchGraph {
     DevOps ops;
     MixedWork mw;
-    Work w64;  // the FP64 refresh: y = R, z = F
+    Work w64;              // the FP64 refresh: y = R, z = F
+    const ColMaps *dmaps;  // column form: tensor maps of D, da, db (device memory); else null
 };
 static_assert(sizeof(BatchGraph) % 4 == 0, "descriptor copied as 32-bit words");
 
@@ -130,12 +131,13 @@ __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGrap
 }
 
 // Column-block form: the SpMM over (problem, J, split) items. The split's
-// entries and bundles are staged with two bulk copies (one mbarrier), the
-// column block with plain loads (each problem has its own layout, so no
-// tensor map); the arithmetic is the single-problem form's (warp_bundles,
-// cta_gain), so the results are bitwise the same. Registers are capped for
-// two resident CTAs per SM, so that the small size classes (less shared
-// memory) overlap one CTA's staging with another's products.
+// entries and bundles (two bulk copies) and the column block (3-D tensor
+// loads through the problem's own tensor map, kept in device memory) land
+// on one mbarrier while the CTA forms its share of the problem's gain; the
+// arithmetic is the single-problem form's (warp_bundles, cta_gain), so the
+// results are bitwise the same. Registers are capped for two resident CTAs
+// per SM, so that the small size classes (less shared memory) overlap one
+// CTA's staging with another's products.
 template <int STAGE>
 __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
                                                                  int nitems) {
@@ -154,11 +156,12 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
         if (!graph_done(sg, &s_flag)) {
             const DevOps &ops = sg.ops;
             const int J = t.y, r = t.z, np = ops.np;
-            const size_t plane = (size_t)np * np;
-            float *sD = reinterpret_cast<float *>(dyn_smem);
-            int2 *sKH = reinterpret_cast<int2 *>(dyn_smem + (size_t)np * cols::kRowFloats * 4);
-            int4 *sP = reinterpret_cast<int4 *>(dyn_smem + ops.col_p_off);
-            const float *din = cols::stage_input<STAGE>(sg.mw);
+            // 128-byte aligned for the tensor loads (the plan's size leaves the slack)
+            const uint32_t s0 = tma::smem_u32(dyn_smem);
+            uint8_t *base = dyn_smem + (((s0 + 127) & ~127u) - s0);
+            float *sD = reinterpret_cast<float *>(base);
+            int2 *sKH = reinterpret_cast<int2 *>(base + (size_t)np * cols::kRowFloats * 4);
+            int4 *sP = reinterpret_cast<int4 *>(base + ops.col_p_off);
             const int q_base = ops.col_q[2 * r], q_end = ops.col_q[2 * r + 1];
             const int p_base = ops.col_sb[r], p_end = ops.col_sb[r + 1];
             if (threadIdx.x < 32) {
@@ -166,37 +169,21 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 const uint32_t kh_bytes = (uint32_t)((q_end - q_base) * 8);
                 const uint32_t p_bytes = (uint32_t)((p_end - p_base) * 16 * cols::kBundleInt4);
+                const uint32_t d_bytes = (uint32_t)np * cols::kRowFloats * 4;
                 if (threadIdx.x == 0) {
-                    tma::mbar_expect_tx(&bar, kh_bytes + p_bytes);
+                    tma::mbar_expect_tx(&bar, kh_bytes + p_bytes + d_bytes);
                     if (kh_bytes) tma::load_bulk(sKH, ops.col_kh + q_base, kh_bytes, &bar);
                     if (p_bytes)
                         tma::load_bulk(sP, ops.col_pieces + cols::kBundleInt4 * (size_t)p_base, p_bytes, &bar);
-                }
-            }
-            // the column block with plain loads, kStageLoads float4 in flight per
-            // thread (parts 0..3: real quads, 4..7: imaginary quads of a row)
-            constexpr int kStageLoads = 4;  // (8 spilled under the 2-CTA register cap)
-            for (int u0 = threadIdx.x; u0 < np * 8; u0 += kStageLoads * (int)blockDim.x) {
-                float4 v[kStageLoads];
-#pragma unroll
-                for (int i = 0; i < kStageLoads; ++i) {
-                    const int u = u0 + i * (int)blockDim.x;
-                    if (u < np * 8) {
-                        const int k = u >> 3, part = u & 7;
-                        v[i] = __ldcg(reinterpret_cast<const float4 *>(din + (part < 4 ? 0 : plane) +
-                                                                       (size_t)k * np + J * cols::kCW +
-                                                                       4 * (part & 3)));
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < kStageLoads; ++i) {
-                    const int u = u0 + i * (int)blockDim.x;
-                    if (u < np * 8) *reinterpret_cast<float4 *>(sD + (u >> 3) * cols::kRowFloats + 4 * (u & 7)) = v[i];
+                    // the stage input's map: D (stage 1), da (stages 2 and 4), db (stage 3)
+                    const CUtensorMap *tm = &sg.dmaps->d[STAGE == 1 ? 0 : (STAGE == 3 ? 2 : 1)];
+                    for (int b = 0; b < np; b += cols::kBoxRows)
+                        tma::load_3d(sD + (size_t)b * cols::kRowFloats, tm, &bar, J * cols::kCW, 0, b);
                 }
             }
             const int ncb = np / cols::kCW;
             cols::cta_gain(ops, sg.mw, r * ncb + J, ncb * ops.col_splits,
-                           reinterpret_cast<float *>(dyn_smem + ops.col_sp_off));
+                           reinterpret_cast<float *>(base + ops.col_sp_off));
             const bool ok = tma::mbar_wait(&bar, phase & 1);
             ++phase;
             if (__syncthreads_or(!ok)) {
@@ -205,8 +192,8 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
                 return;
             }
             const int warp = threadIdx.x >> 5;
-            float *parts = reinterpret_cast<float *>(dyn_smem + ops.col_part_off);
-            cols::warp_bundles<false, false, 1>(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
+            float *parts = reinterpret_cast<float *>(base + ops.col_part_off);
+            cols::warp_bundles(sD, sKH, sP, p_base, ops.col_wb[r * cols::kAWarps + warp],
                                ops.col_wb[r * cols::kAWarps + warp + 1], J, np, sg.mw.X, parts);
             const int cb0 = ops.col_cutb[r], cb1 = ops.col_cutb[r + 1];
             if (cb1 > cb0) {
@@ -706,6 +693,19 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     BCUDA(cudaMemcpyAsync(dF, hF.data(), nf * sizeof(float), cudaMemcpyHostToDevice, s));
     BCUDA(cudaMemcpyAsync(dI, hI.data(), ni * sizeof(int), cudaMemcpyHostToDevice, s));
     BCUDA(cudaMemcpyAsync(dB, hB.data(), nb, cudaMemcpyHostToDevice, s));
+    // the column form's tensor maps (D, da, db of each problem), read by the
+    // SpMM kernels from device memory
+    qpr::ColMaps *dMaps = nullptr;
+    BCUDA(mem.alloc(&dMaps, G));
+    std::vector<qpr::ColMaps> hMaps(G);
+    memset(hMaps.data(), 0, G * sizeof(qpr::ColMaps));
+    for (size_t g = 0; g < G; ++g) {
+        if (!colg[g]) continue;
+        const float *din[3] = {desc[g].mw.D, desc[g].mw.da, desc[g].mw.db};
+        if (!qpr::make_col_maps(desc[g].ops, din, &hMaps[g])) return err(QPR_E_CUDA, "cuTensorMapEncodeTiled failed");
+        desc[g].dmaps = dMaps + g;
+    }
+    BCUDA(cudaMemcpyAsync(dMaps, hMaps.data(), G * sizeof(qpr::ColMaps), cudaMemcpyHostToDevice, s));
     BCUDA(cudaMemcpyAsync(dG, desc.data(), G * sizeof(BatchGraph), cudaMemcpyHostToDevice, s));
     BCUDA(cudaMemcpyAsync(dCtl, hCtl, G * sizeof(Ctl), cudaMemcpyHostToDevice, s));
     int64_t launches = 0;
