@@ -53,6 +53,16 @@ __device__ __forceinline__ void load_graph(const BatchGraph *gs, int g, BatchGra
     __syncthreads();
 }
 
+// load_graph and the stop flag of problem g (ctls: the problems' control
+// blocks) in the same round trip; returns the flag, the same value for
+// every thread of the CTA (ends synced).
+__device__ __forceinline__ int load_graph_done(const BatchGraph *gs, const Ctl *ctls, int g, BatchGraph &sg,
+                                               int *s_flag) {
+    if (threadIdx.x == 0) *s_flag = *(volatile const int *)&ctls[g].done;
+    load_graph(gs, g, sg);
+    return *s_flag;
+}
+
 // 1 if problem `sg` has stopped; the same value for every thread of the CTA.
 __device__ __forceinline__ int graph_done(const BatchGraph &sg, int *s_flag) {
     if (threadIdx.x == 0) *s_flag = *(volatile int *)&sg.mw.ctl->done;
@@ -139,8 +149,8 @@ __global__ void __launch_bounds__(kStageNT) b_stage_mixed_kernel(const BatchGrap
 // per SM, so that the small size classes (less shared memory) overlap one
 // CTA's staging with another's products.
 template <int STAGE>
-__global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchGraph *gs, const int4 *items,
-                                                                 int nitems) {
+__global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchGraph *gs, const Ctl *ctls,
+                                                                 const int4 *items, int nitems) {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
@@ -150,10 +160,11 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
         tma::mbar_init_fence();
     }
     uint32_t phase = 0;
+    int4 tn = blockIdx.x < nitems ? items[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int4 t = items[it];
-        load_graph(gs, t.x, sg);
-        if (!graph_done(sg, &s_flag)) {
+        const int4 t = tn;
+        if (it + (int)gridDim.x < nitems) tn = items[it + gridDim.x];  // the next item, in flight meanwhile
+        if (!load_graph_done(gs, ctls, t.x, sg, &s_flag)) {
             const DevOps &ops = sg.ops;
             const int J = t.y, r = t.z, np = ops.np;
             // 128-byte aligned for the tensor loads (the plan's size leaves the slack)
@@ -207,18 +218,19 @@ __global__ void __launch_bounds__(cols::kANT, 2) b_cols_spmm_kernel(const BatchG
 
 // Column-block form: the epilogue over (problem, I, J, pair) items.
 template <int STAGE>
-__global__ void __launch_bounds__(cols::kENT, 3) b_cols_epi_kernel(const BatchGraph *gs, const int4 *items,
-                                                                 int nitems) {
+__global__ void __launch_bounds__(cols::kENT, 3) b_cols_epi_kernel(const BatchGraph *gs, const Ctl *ctls,
+                                                                 const int4 *items, int nitems) {
     __shared__ __align__(16) float sX1[mixed::TS * mixed::LDX];
     __shared__ __align__(16) float sX2[mixed::TS * mixed::LDX];
     __shared__ __align__(16) float sO[4 * mixed::TS * mixed::LDO];
     __shared__ float sg32[mixed::TS];
     __shared__ BatchGraph sg;
     __shared__ int s_flag;
+    int4 tn = blockIdx.x < nitems ? items[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int4 t = items[it];
-        load_graph(gs, t.x, sg);
-        if (!graph_done(sg, &s_flag))
+        const int4 t = tn;
+        if (it + (int)gridDim.x < nitems) tn = items[it + gridDim.x];  // the next item, in flight meanwhile
+        if (!load_graph_done(gs, ctls, t.x, sg, &s_flag))
             cols::epilogue_pair<STAGE>(sg.ops, sg.mw, t.y, t.z, t.w, t.w == 0, sg.mw.npairs, sX1, sX2, sg32, sO);
         __syncthreads();
     }
@@ -288,16 +300,16 @@ void launch_refresh(const BatchGraph *gs, const Lists &L, int max_np, cudaStream
 }
 
 template <int STAGE>
-void launch_stage_b(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
+void launch_stage_b(const BatchGraph *gs, const Ctl *ctls, const Lists &L, cudaStream_t s, int64_t &launches) {
     bool any = false;
     for (int c = 0; c < kClasses; ++c)
         if (L.na[c]) {
-            b_cols_spmm_kernel<STAGE><<<L.grid_a[c], cols::kANT, L.smem_a[c], s>>>(gs, L.items_a[c], L.na[c]);
+            b_cols_spmm_kernel<STAGE><<<L.grid_a[c], cols::kANT, L.smem_a[c], s>>>(gs, ctls, L.items_a[c], L.na[c]);
             launches += 1;
             any = true;
         }
     if (any) {
-        b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 3), cols::kENT, 0, s>>>(gs, L.items_b, L.nb);
+        b_cols_epi_kernel<STAGE><<<std::min(L.nb, 152 * 3), cols::kENT, 0, s>>>(gs, ctls, L.items_b, L.nb);
         launches += 1;
     }
     if (L.nt) {
@@ -307,11 +319,11 @@ void launch_stage_b(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_
     }
 }
 
-void launch_step(const BatchGraph *gs, const Lists &L, cudaStream_t s, int64_t &launches) {
-    launch_stage_b<1>(gs, L, s, launches);
-    launch_stage_b<2>(gs, L, s, launches);
-    launch_stage_b<3>(gs, L, s, launches);
-    launch_stage_b<4>(gs, L, s, launches);
+void launch_step(const BatchGraph *gs, const Ctl *ctls, const Lists &L, cudaStream_t s, int64_t &launches) {
+    launch_stage_b<1>(gs, ctls, L, s, launches);
+    launch_stage_b<2>(gs, ctls, L, s, launches);
+    launch_stage_b<3>(gs, ctls, L, s, launches);
+    launch_stage_b<4>(gs, ctls, L, s, launches);
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -818,7 +830,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         qpr::launch_refresh(dG, LG, max_np, s, graph_launches, dDue);
-        for (int k = 0; k < block; ++k) qpr::launch_step(dG, LG, s, graph_launches);
+        for (int k = 0; k < block; ++k) qpr::launch_step(dG, dCtl, LG, s, graph_launches);
         e = cudaStreamEndCapture(s, &gr);
         if (e != cudaSuccess) return e;
         e = cudaGraphInstantiate(&gexec, gr, 0);
