@@ -229,11 +229,12 @@ QPR_API qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double t
 
 /* Per-kernel timing of the RK4 step, for roofline measurements (the paper
  * has no counterpart). Runs `steps` RK4 steps (steps >= 1) from rho (rho
- * itself is not modified) on the context's stream without CUDA graphs,
- * without programmatic dependent launch and without the forked gain branch:
- * every kernel runs alone, between two CUDA events, so each time below is
- * one kernel's own duration (plus the event granularity, about a
- * microsecond), not the overlapped time of the solve's graph launches.
+ * itself is not modified) on the context's stream without CUDA graphs and
+ * without programmatic dependent launch: every kernel runs alone, between
+ * two CUDA events, so each time below is one kernel's own duration (plus
+ * the launch and event granularity, about a microsecond), not the
+ * overlapped time of the solve's graph launches (there the SpMM grid and the
+ * epilogue overlap their prologues with the previous kernel).
  * Means over all launches of the kind, in milliseconds. */
 typedef struct {
     double product_ms;   /* the H rho product: the column-block SpMM (COLUMNS, COLUMNS_PERSISTENT) or
