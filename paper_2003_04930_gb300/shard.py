@@ -6,7 +6,7 @@ with qpr_batch_steady_state and nothing is exchanged on the data path; the
 batch is done when the slowest rank is. The subsets balance an estimate of
 each problem's work: N^2 elements per stage times a step count that grows
 as the dissipative part weakens (the spectral gap of the Lindblad
-superoperator scales with omega for these graphs), i.e. N^2 / omega.
+superoperator shrinks roughly with omega on these graphs), i.e. N^2 / omega.
 """
 
 
