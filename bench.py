@@ -337,14 +337,16 @@ def run_ours(a):
     # per-kernel durations on the solver's stream, same workload and state: each kernel alone between events
     peaks, peak_src = load_peaks()
     prof = s.profile_step(rho, a.dt, 20)
-    roof = roofline(s, g, a.n, prof, peaks, peak_src, prec)
+    chain = s.profile_chain(rho, a.dt, CHAIN_REPS) if column_form(s, prec) else None
+    roof = roofline(s, g, a.n, prof, peaks, peak_src, prec, chain)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == qpr.QPR_FP64 else "f32+f64", "data": "synthetic",
             "config": dict(workload_config(a), form=form_name(s, prec), ref_refresh=a.ref_refresh,
                            sparse_plan=s.sparse_plan, parallelism=f"replicas{world}"),
             "rk4_steps_to_converge": steps_conv, "rk4_steps_per_s": steps_conv / (total / a.steps),
-            "residual": stats[-1]["residual"], "roofline": roof, "profile_ms": prof, "clocks": clocks,
+            "residual": stats[-1]["residual"], "roofline": roof, "profile_ms": prof, "profile_chain_ms": chain,
+            "clocks": clocks,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats))}
 
     # the paper's own integrator: adaptive RKF45 (Supplementary Note 2) on the same problem and stop rule
@@ -483,25 +485,41 @@ def form_name(s, prec):
 
 
 # DRAM bytes per launch of the current kernels from one ncu capture each
-# (`dram__bytes_read.sum + dram__bytes_write.sum` of the stage-1 launch,
+# (`dram__bytes_read.sum + dram__bytes_write.sum` of the stage-1 launch, and
+# of the stage-2 epilogue,
 # profiles/traffic_cols_n922_n4096.md), keyed by (kernel, N); a kernel
 # changed since its capture has no entry.
 NCU_TRAFFIC = {("cols_spmm_kernel", 922): 7115776, ("cols_epi_kernel", 922): 14042112,
-               ("cols_gather_kernel", 4096): 135333888 + 100642816, ("cols_epi_kernel", 4096): 269617152 + 100662784}
+               ("cols_epi_kernel_stage2", 922): 17601536,
+               ("cols_gather_kernel", 4096): 135333888 + 100642816, ("cols_epi_kernel", 4096): 269617152 + 100662784,
+               ("cols_epi_kernel_stage2", 4096): 337257472 + 105124608}
 
 
-def roofline(s, g, n, prof, peaks, peak_src, prec):
+def column_form(s, prec):
+    """True when the solver runs a column-block form (qpr_profile_chain applies)."""
+    from paper_2003_04930_gb300 import qpr
+    return (prec == qpr.QPR_MIXED and s.backend == qpr.QPR_BACKEND_SPARSE and
+            s.sparse_form != qpr.QPR_SPARSE_FORM_TILES)
+
+
+CHAIN_REPS = 20
+CHAIN_SOURCE = (f"qpr_profile_chain: {CHAIN_REPS} launches of the kernel back to back with programmatic dependent "
+                "launch (as in the solve's graphs), CUDA events around the chain on the launching stream")
+ALONE_SOURCE = "qpr_profile_step: the kernel alone on the stream between two CUDA events"
+
+
+def roofline(s, g, n, prof, peaks, peak_src, prec, chain=None):
     """Roofline of the dominant kernel of the form in use, from the kernel's
-    own duration (qpr_profile_step: each kernel alone between CUDA events)."""
+    duration inside a chain of launches (qpr_profile_chain, column-block
+    forms: `chain`) or launched alone (qpr_profile_step: `prof`)."""
     from paper_2003_04930_gb300 import qpr
     hbm = peaks["hbm_gbs"]
 
-    def hbm_entry(kernel, alg, ms, extra=None):
+    def hbm_entry(kernel, alg, ms, extra=None, source=ALONE_SOURCE, key=None):
         ach = alg / (ms * 1e-3) / 1e9
         d = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-             "traffic": NCU_TRAFFIC.get((kernel, n)), "kernel": kernel, "alg_bytes_per_launch": alg,
-             "launch_ms": ms, "peak_source": f"hbm_gbs of {peak_src}",
-             "launch_ms_source": "qpr_profile_step: the kernel alone on the stream between two CUDA events"}
+             "traffic": NCU_TRAFFIC.get(key or (kernel, n)), "kernel": kernel, "alg_bytes_per_launch": alg,
+             "launch_ms": ms, "peak_source": f"hbm_gbs of {peak_src}", "launch_ms_source": source}
         if extra:
             d.update(extra)
         return d
@@ -528,15 +546,25 @@ def roofline(s, g, n, prof, peaks, peak_src, prec):
         # stage 4 X, the input, D, Dlo, Ghi, Glo, D and Dlo written (64): mean (32 + 40 + 40 + 64) / 4 = 44
         epi_alg = 44 * n * n
         rows_read = nnz * npad * 8  # each nonzero's row of the stage input, per column block (L1/L2 or smem)
+        if chain is not None:
+            # the chains repeat the stage-2 kernels: its epilogue moves 40 bytes per element
+            spmm_ms, src = chain["product_ms"], CHAIN_SOURCE
+            epi = hbm_entry("cols_epi_kernel", 40 * n * n, chain["epilogue_ms"], source=CHAIN_SOURCE,
+                            key=("cols_epi_kernel_stage2", n),
+                            extra={"stage": 2, "launch_ms_alone_mean_of_4_stages": prof["epilogue_ms"]})
+        else:
+            spmm_ms, src = prof["product_ms"], ALONE_SOURCE
+            epi = hbm_entry("cols_epi_kernel", epi_alg, prof["epilogue_ms"])
         extra = {"gathered_bytes_per_launch": rows_read,
-                 "gathered_gbs": rows_read / (prof["product_ms"] * 1e-3) / 1e9,
+                 "gathered_gbs": rows_read / (spmm_ms * 1e-3) / 1e9,
                  "flops_per_launch": 4.0 * nnz * npad,
-                 "epilogue": hbm_entry("cols_epi_kernel", epi_alg, prof["epilogue_ms"]),
+                 "launch_ms_alone": prof["product_ms"],
+                 "epilogue": epi,
                  "gain": "formed by the SpMM grid's leading CTAs (cta_gain), inside launch_ms",
                  "note": "alg bytes are the DRAM floor (stage input and X once, the CSR entries once); at "
                          "N <= 1400 the state is L2-resident, so a fraction of the HBM peak is a lower bound "
                          "on what the kernel moves through the memory system"}
-        return hbm_entry(kernel, alg, prof["product_ms"], extra)
+        return hbm_entry(kernel, alg, spmm_ms, extra, source=src)
     if s.backend == qpr.QPR_BACKEND_SPARSE:
         if prec == qpr.QPR_MIXED:
             alg, kname = 52 * n * n, "stage_mixed_sparse_kernel"
@@ -684,7 +712,9 @@ def large_case(a, local, peaks, peak_src, flush):
                     "gpu_launches": st["kernel_launches"]}}
     prof = s.profile_step(rho_solved, la.dt, 4)
     out["profile_ms"] = prof
-    out["roofline"] = roofline(s, g, n, prof, peaks, peak_src, qpr.QPR_MIXED)
+    chain = s.profile_chain(rho_solved, la.dt, CHAIN_REPS) if column_form(s, qpr.QPR_MIXED) else None
+    out["profile_chain_ms"] = chain
+    out["roofline"] = roofline(s, g, n, prof, peaks, peak_src, qpr.QPR_MIXED, chain)
     ws = warm_solve(s, g, la.omega, la, local, rho, flush, 1)
     if ws is not None:
         out["warm_start"] = ws

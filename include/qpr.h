@@ -250,6 +250,20 @@ typedef struct {
 
 QPR_API qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, qpr_profile *out);
 
+/* The same kernels inside a chain of launches with programmatic dependent
+ * launch, as the solve runs them (for roofline measurements; the paper has
+ * no counterpart). From rho (not modified) it runs one exact refresh and
+ * stage 1, then launches the stage-2 SpMM grid `reps` times back to back
+ * (each launch reads the same stage input and writes the same X and gain)
+ * and the stage-2 epilogue `reps` times (each reads X and the stage input
+ * and writes the same next stage input), each launch allowed to start its
+ * prologue while the previous one finishes, with CUDA events around each
+ * chain on the context's stream. out_ms[0] = mean time per SpMM launch,
+ * out_ms[1] = per epilogue launch (milliseconds; 2 doubles, host). QPR_MIXED
+ * with a column-block form (COLUMNS, COLUMNS_PERSISTENT's kernels,
+ * COLUMNS_GATHER) only, else QPR_E_ARG; reps in [1, 4096]. */
+QPR_API qpr_status qpr_profile_chain(qpr_ctx *ctx, const void *rho, double dt, int32_t reps, double *out_ms);
+
 /* p[i] = Re rho_ii (the probability at node i); p: N doubles, host or
  * device. rank (nullable): N int64 node indices in descending order of p,
  * ties to the lower index (the ranking of the main text's airline study). */

@@ -1262,6 +1262,62 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
     return QPR_OK;
 }
 
+qpr_status qpr_profile_chain(qpr_ctx *ctx, const void *rho, double dt, int32_t reps, double *out_ms) {
+    if (!ctx) return QPR_E_ARG;
+    DeviceGuard dg(ctx->device);
+    qpr_status st = begin_call(ctx);
+    if (st != QPR_OK) return st;
+    if (!rho || !out_ms || reps < 1 || reps > 4096) return fail(ctx, QPR_E_ARG, "rho/out_ms NULL or reps not in [1, 4096]");
+    if (!(dt > 0.0) || dt > qpr_max_stable_dt(ctx)) return fail(ctx, QPR_E_ARG, "dt not positive or unstable");
+    if (ctx->opt.precision != QPR_MIXED || !ctx->mw.cmaps)
+        return fail(ctx, QPR_E_ARG, "qpr_profile_chain needs QPR_MIXED with a column-block sparse form");
+    st = import_state(ctx, rho);
+    if (st != QPR_OK) return st;
+    Ctl *h = ctx->h_ctl;
+    memset(h, 0, sizeof(Ctl));
+    h->max_steps = 1 << 30;
+    h->tol = 0.0;
+    h->dt = dt;
+    h->scale = 1.0;
+    h->resid_exact_step = -1;
+    QPR_CUDA(ctx, cudaMemcpyAsync(ctx->d_ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    // the stage-2 input: a refresh, then stage 1 (SpMM and epilogue)
+    qpr::launch_mixed_refresh(ctx->ops, ctx->mw, ctx->stream);
+    qpr::launch_mixed_stage(1, ctx->ops, ctx->mw, ctx->stream, 1, true);
+    qpr::launch_mixed_stage(1, ctx->ops, ctx->mw, ctx->stream, 2, true);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    auto destroy = [&]() {
+        for (cudaEvent_t &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (cudaEvent_t &e : ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            destroy();
+            return fail(ctx, QPR_E_CUDA, "cudaEventCreate failed");
+        }
+    }
+    // each chain repeats one kernel: the SpMM grid reads the stage input and
+    // writes X and g, the epilogue reads X and the stage input and writes the
+    // next stage input, so every launch does the same work on the same data
+    cudaEventRecord(ev[0], ctx->stream);
+    for (int r = 0; r < reps; ++r) qpr::launch_mixed_stage(2, ctx->ops, ctx->mw, ctx->stream, 1, false);
+    cudaEventRecord(ev[1], ctx->stream);
+    cudaEventRecord(ev[2], ctx->stream);
+    for (int r = 0; r < reps; ++r) qpr::launch_mixed_stage(2, ctx->ops, ctx->mw, ctx->stream, 2, false);
+    cudaEventRecord(ev[3], ctx->stream);
+    ctx->launches += 3 + qpr::kMixedLaunchesPerRefresh + 2 * (int64_t)reps;
+    st = sync_ctx(ctx);
+    if (st == QPR_OK) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[2], ev[3]);
+        out_ms[0] = a / reps;
+        out_ms[1] = b / reps;
+    }
+    destroy();
+    return st;
+}
+
 qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, qpr_profile *out) {
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);

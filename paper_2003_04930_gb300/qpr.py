@@ -29,7 +29,7 @@ QPR_BACKEND_AUTO, QPR_BACKEND_DENSE, QPR_BACKEND_SPARSE = 0, 1, 2
 EXPORTED = (
     "qpr_default_options", "qpr_create", "qpr_destroy", "qpr_last_error", "qpr_status_string",
     "qpr_n", "qpr_backend", "qpr_sparse_form", "qpr_sparse_plan", "qpr_h_spread", "qpr_max_stable_dt", "qpr_rhs", "qpr_residual", "qpr_evolve",
-    "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_rhs_noalloc", "qpr_batch_steady_state",
+    "qpr_steady_state", "qpr_populations", "qpr_profile_step", "qpr_profile_chain", "qpr_rhs_noalloc", "qpr_batch_steady_state",
     "qpr_gnn_param_count", "qpr_gnn_create", "qpr_gnn_destroy", "qpr_gnn_get_params", "qpr_gnn_set_params",
     "qpr_gnn_predict", "qpr_gnn_loss_grad", "qpr_gnn_train", "qpr_autotune", "qpr_pagerank", "qpr_hub_classes",
     "qpr_rkf45",
@@ -151,6 +151,8 @@ def load_library(path: str = LIB_PATH):
     lib.qpr_steady_state.restype = st
     lib.qpr_profile_step.argtypes = [vp, vp, f64, i64, ctypes.POINTER(qpr_profile)]
     lib.qpr_profile_step.restype = st
+    lib.qpr_profile_chain.argtypes = [vp, vp, f64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    lib.qpr_profile_chain.restype = st
     lib.qpr_rhs_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, f64, f64, ctypes.c_int32, vp, vp, vp]
     lib.qpr_rhs_noalloc.restype = st
     lib.qpr_batch_steady_state.argtypes = [i64, ctypes.POINTER(qpr_problem), f64, f64, f64, i64,
@@ -391,6 +393,15 @@ class Solver:
         out = qpr_profile()
         self._raise(self._lib.qpr_profile_step(self._h, _ptr(rho), float(dt), int(steps), ctypes.byref(out)))
         return out.as_dict()
+
+    def profile_chain(self, rho, dt: float, reps: int = 20):
+        """qpr_profile_chain: the stage-2 SpMM grid and epilogue each
+        launched `reps` times back to back with programmatic dependent
+        launch; mean time per launch (ms) as {"product_ms", "epilogue_ms"}."""
+        _check_rho(rho, self.n)
+        out = (ctypes.c_double * 2)()
+        self._raise(self._lib.qpr_profile_chain(self._h, _ptr(rho), float(dt), int(reps), out))
+        return {"product_ms": out[0], "epilogue_ms": out[1]}
 
 
 def batch_steady_state(problems, alpha=0.85, dt=0.01, tol=1e-8, max_steps=400000, ref_refresh=32,

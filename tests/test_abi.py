@@ -86,6 +86,7 @@ def test_null_out_rejected(lib):
 
 def test_null_context_calls(lib):
     assert lib.qpr_evolve(None, None, 0.01, 1) == qpr.QPR_E_ARG
+    assert lib.qpr_profile_chain(None, None, 0.01, 1, None) == qpr.QPR_E_ARG
     assert lib.qpr_n(None) == 0
     lib.qpr_destroy(None)
 
