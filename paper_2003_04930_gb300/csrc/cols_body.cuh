@@ -424,10 +424,10 @@ __device__ __forceinline__ void stage1_last_decides(const MixedWork &w, int npar
 // with the ticket of the stop decision (TICKET),
 // stage 4 advances the step counter (first pair). kENT threads. Shared
 // memory: sX1, sX2 (TS * LDX floats each), sg (TS), sO (4 * TS * LDO).
-template <int STAGE, bool TICKET = true>
-__device__ __forceinline__ void epilogue_pair_in(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
-                                                 bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO,
-                                                 const mixed::EpiIn<STAGE, kENT> &in) {
+// The X tiles of pair (I, J) into sX1 (X_IJ) and sX2 (X_JI, off-diagonal
+// pairs), and the gain of a diagonal pair into sg; no barrier at the end.
+__device__ __forceinline__ void epilogue_load_x(const DevOps &ops, const MixedWork &w, int I, int J, float *sX1,
+                                                float *sX2, float *sg) {
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const bool diag = (I == J);
@@ -447,10 +447,26 @@ __device__ __forceinline__ void epilogue_pair_in(const DevOps &ops, const MixedW
         dst[3] = v.w;
     }
     if (diag && threadIdx.x < TS) sg[threadIdx.x] = __ldcg(w.g + I * TS + threadIdx.x);
-    __syncthreads();
+}
+
+// The epilogue of pair (I, J) once its X tiles and gain are in shared memory
+// (after a barrier).
+template <int STAGE, bool TICKET = true>
+__device__ __forceinline__ void epilogue_pair_staged(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                     bool first, int nparts, const float *sX1, const float *sX2,
+                                                     const float *sg, float *sO, const mixed::EpiIn<STAGE, kENT> &in) {
     mixed::tile_epilogue_in<STAGE, kENT>(ops, w, I, J, pidx, sX1, sX2, sg, sO, in);
     if (STAGE == 1 && TICKET) stage1_last_decides(w, nparts);
     if (STAGE == 4 && first && threadIdx.x == 0) w.ctl->step += 1;
+}
+
+template <int STAGE, bool TICKET = true>
+__device__ __forceinline__ void epilogue_pair_in(const DevOps &ops, const MixedWork &w, int I, int J, int pidx,
+                                                 bool first, int nparts, float *sX1, float *sX2, float *sg, float *sO,
+                                                 const mixed::EpiIn<STAGE, kENT> &in) {
+    epilogue_load_x(ops, w, I, J, sX1, sX2, sg);
+    __syncthreads();
+    epilogue_pair_staged<STAGE, TICKET>(ops, w, I, J, pidx, first, nparts, sX1, sX2, sg, sO, in);
 }
 
 // The same with the elementwise operands loaded first, so that their loads

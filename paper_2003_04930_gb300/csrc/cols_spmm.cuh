@@ -49,17 +49,22 @@ __device__ __forceinline__ void spmm_block_body(PickMap pick_map, const DevOps &
     }
     const int wb0 = ops.col_wb[r * kAWarps + warp], wb1 = ops.col_wb[r * kAWarps + warp + 1];
     tma::grid_dependency_wait();
-    if (tid == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) {
-        tma::mbar_wait(&bar_csr, 0);  // the copies in flight land before the CTA leaves (bounded)
-        return;
-    }
     tma::launch_dependents();
+    // the stop flag and the column block in one round trip (the block is
+    // staged whatever the flag says; nothing is written unless the run goes on)
     if (tid == 0) {
+        const int done = *(volatile int *)&w.ctl->done;
         const CUtensorMap *tm = pick_map();
         tma::mbar_expect_tx(&bar_d, (uint32_t)np * kRowFloats * 4);
         for (int b = 0; b < np; b += kBoxRows) tma::load_3d(sD + (size_t)b * kRowFloats, tm, &bar_d, J * kCW, 0, b);
+        s_done = done;
+    }
+    __syncthreads();
+    if (s_done) {
+        // the copies in flight land before the CTA leaves (bounded)
+        tma::mbar_wait(&bar_csr, 0);
+        tma::mbar_wait(&bar_d, 0);
+        return;
     }
     const bool ok = tma::mbar_wait(&bar_csr, 0) && tma::mbar_wait(&bar_d, 0);
     timeline::mark<TL>(2);

@@ -66,7 +66,7 @@ static_assert(kANT == kENT, "the stop decision sums the residual partials with t
 // Launched with programmatic dependent launch: the elementwise operands (the
 // stage input, F32, D, S, ...: written two kernels back, complete once the
 // SpMM kernel has passed its own dependency wait) are loaded before
-// grid_dependency_wait; X, the gain and the control block after it.
+// grid_dependency_wait; X, the gain and the stop flag after it, together.
 template <int STAGE>
 __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork w) {
     __shared__ __align__(16) float sX1[TS * LDX];
@@ -79,13 +79,17 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     mixed::EpiIn<STAGE, kENT> in;
     mixed::epi_load<STAGE, kENT>(ops, w, pr.x, pr.y, in);
     tma::grid_dependency_wait();
-    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
+    tma::launch_dependents();
+    // the stop flag and the X tiles in one round trip (X is read whatever the
+    // flag says; nothing is written unless the run goes on)
+    const int done = (threadIdx.x == 0) ? *(volatile int *)&w.ctl->done : 0;
+    epilogue_load_x(ops, w, pr.x, pr.y, sX1, sX2, sg);
+    if (threadIdx.x == 0) s_done = done;
     __syncthreads();
     if (!s_done) {
-        tma::launch_dependents();
         // no ticket: the stage-2 SpMM grid takes the stop decision (gain_role)
-        epilogue_pair_in<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO,
-                                       in);
+        epilogue_pair_staged<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg,
+                                           sO, in);
     }
     timeline::leave();
 }
