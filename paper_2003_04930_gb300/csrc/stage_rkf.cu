@@ -261,14 +261,14 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
     RkfIn<S> in;
     rkf_load<S>(ops, w, I, J, cur, in);
     tma::grid_dependency_wait();
-    if (threadIdx.x == 0) s_done = *(volatile int *)&w.ctl->done;
-    __syncthreads();
-    if (s_done) return;
     tma::launch_dependents();
     const int np = ops.np;
     const size_t plane = (size_t)np * np;
     const bool diag = (I == J);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the stop flag and the X tiles in one round trip (X is read whatever the
+    // flag says; nothing is written unless the run goes on)
+    const int done = (tid == 0) ? *(volatile int *)&w.ctl->done : 0;
     // X tiles as [a][LDX] rows (real part, then imaginary part)
     for (int t = tid; t < (diag ? 1 : 2) * TS * (2 * TS / 4); t += kENT) {
         const int which = t / (TS * (2 * TS / 4));
@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
         dst[3] = v.w;
     }
     if (diag && tid < TS) sg[tid] = __ldcg(w.g + I * TS + tid);
+    if (tid == 0) s_done = done;
     __syncthreads();
+    if (s_done) return;
     const float *X2 = diag ? sX1 : sX2;
     const float om = ops.omega32, cm = __fsub_rn(1.0f, om);
     const float hh = w.ctl->rk_hf, hl = w.ctl->rk_hl;
