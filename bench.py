@@ -85,6 +85,9 @@ def parse_args():
     ap.add_argument("--large-n", type=int, default=4096)
     ap.add_argument("--large-seed", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batch sub-object")
+    ap.add_argument("--no-omega-sweep", action="store_true", help="skip the omega in {0.2, 0.5, 1.0} sub-object")
+    ap.add_argument("--cpu-omega-sweep", action="store_true",
+                    help="add the CPU oracle's whole solves to the omega sweep (minutes of host time)")
     ap.add_argument("--cpu-full-max-s", type=float, default=90.0,
                     help="run the oracle solve to completion when its estimate is below this many seconds")
     return ap.parse_args()
@@ -392,6 +395,8 @@ def run_ours(a):
         line["n4096"] = large_case(a, local, peaks, peak_src, flush)
     if not a.no_batch and rank == 0:
         line["batch512"] = batch_case(a, local)
+    if not a.no_omega_sweep and rank == 0 and a.n == 922:
+        line["omega_sweep"] = omega_sweep(a, local, flush, cpu=a.cpu_omega_sweep and world == 1)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, steps_conv, a.cpu_sample_steps)
@@ -656,6 +661,61 @@ def warm_solve(s, g, omega, a, local, rho, flush, reps):
             "timed": "GNN inference (qpr_gnn_predict) + rho0 = diag(p_hat) upload + solve",
             "network": "4-layer message passing, width 64, BF16 weights, trained on 256 solver-generated "
                        "steady states (N in [64, 1024])"}
+
+
+SWEEP_OMEGAS = (0.2, 0.5, 1.0)
+
+
+def omega_sweep(a, local, flush, cpu=False):
+    """The headline graph at the other mixing values of the plain-FP64
+    configuration (omega in {0.2, 0.5, 1.0}; 0.8 is the headline): per omega
+    the mixed solve and the FP64 sparse solve (one untimed, one timed each),
+    their steady states against each other, and RKF45 (fifth order, bounded);
+    with `cpu`, the CPU oracle's whole solve on all host cores too."""
+    import torch
+    from paper_2003_04930_gb300 import Solver, graphs, qpr
+    g = graphs.heavy_tailed(a.n, a.seed)
+    dev = torch.device("cuda", local)
+    rho0 = torch.from_numpy(graphs.maximally_mixed(a.n)).to(dev)
+    out = {}
+    for om in SWEEP_OMEGAS:
+        sa = argparse.Namespace(**vars(a))
+        sa.omega = om
+        s = Solver.from_edges(g, alpha=0.85, omega=om, precision=qpr.QPR_MIXED, device=local,
+                              ref_refresh=a.ref_refresh)
+        rho = torch.empty_like(rho0)
+        rho.copy_(rho0)
+        s.steady_state(rho, a.dt, a.tol, a.max_steps)
+        t_mixed, st = timed_solve(s, rho, rho0, sa, flush)
+        rho_mixed = rho.clone()
+        d = {"mixed": {"time_to_steady_state_s": t_mixed, "steps": st["steps"], "residual": st["residual"]}}
+        rk = torch.empty_like(rho0)
+        rk.copy_(rho0)
+        # bounded by the RK4 step count: where the fifth-order solution stalls it is no alternative
+        kmax = int(st["steps"])
+        r = s.rkf45(rk, tol=a.tol, max_steps=kmax, h0=a.dt, step_tol=1e-6, order=5, check=False)
+        rk.copy_(rho0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = s.rkf45(rk, tol=a.tol, max_steps=kmax, h0=a.dt, step_tol=1e-6, order=5, check=False)
+        e1.record()
+        e1.synchronize()
+        d["rkf45"] = {"converged": r["converged"], "accepted_steps": r["accepted"], "rejected": r["rejected"],
+                      "time_s": e0.elapsed_time(e1) / 1e3, "residual": r["residual"]}
+        s.close()
+        d["fp64_sparse"] = fp64_sparse_solve(g, sa, local, rho0, rho_mixed, flush, warm=True)
+        d["speedup_vs_fp64_sparse"] = d["fp64_sparse"]["time_to_steady_state_s"] / t_mixed
+        if cpu:
+            from oracle import Oracle
+            from oracle.cpu import max_threads
+            o = Oracle.from_edges(g, alpha=0.85, omega=om)
+            t = time.perf_counter()
+            _, steps, resid, _ = o.steady_state(graphs.maximally_mixed(a.n), a.dt, a.tol, a.max_steps)
+            d["cpu_oracle"] = {"time_to_steady_state_s": time.perf_counter() - t, "steps": steps,
+                               "residual": resid, "cores": max_threads()}
+        out[f"omega={om}"] = d
+    return out
 
 
 def tuned_solve(g, a, local, rho0, rho_solved, flush, t_fixed):
