@@ -73,6 +73,7 @@ bool cache_lookup(const char *path, const std::string &key, qpr_tune_result *out
 extern "C" qpr_status qpr_autotune(int64_t n, int64_t m, const int64_t *src, const int64_t *dst, const double *w,
                                    double alpha, double omega, double dt, const qpr_options *base,
                                    const char *cache_path, qpr_tune_result *out) {
+    qpr::NvtxRange nvtx_range("qpr_autotune");
     if (!out) return QPR_E_ARG;
     memset(out, 0, sizeof(*out));
     qpr_options o;

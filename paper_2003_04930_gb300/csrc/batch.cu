@@ -399,6 +399,7 @@ using qpr::Ctl;
 extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *problems, double alpha, double dt,
                                              double tol, int64_t max_steps, const qpr_options *opt,
                                              qpr_stats *stats) {
+    qpr::NvtxRange nvtx_range("qpr_batch_steady_state");
     auto t0 = std::chrono::steady_clock::now();
     auto err = [&](qpr_status st, const std::string &msg) {
         qpr::set_create_error(msg);
@@ -840,6 +841,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     };
     BCUDA(recapture());
     while (!active.empty()) {
+        qpr::NvtxRange nvtx_block("batch block");
         for (int g : active) hDue[g] = due[g] ? 1 : 0;
         BCUDA(cudaMemcpyAsync(dDue, hDue.data(), G, cudaMemcpyHostToDevice, s));
         BCUDA(cudaGraphLaunch(gexec, s));

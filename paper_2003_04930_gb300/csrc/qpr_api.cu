@@ -317,6 +317,7 @@ qpr_status run_mixed(qpr_ctx *ctx, double dt, double tol, int64_t max_steps) {
     int64_t since = 0;  // steps since the last refresh
     double r0 = -1.0;
     for (;;) {
+        qpr::NvtxRange nvtx_block(refresh ? "block (refresh + steps)" : "block (steps)");
         if (ctx->persist_grid > 0) {
             st = launch_mixed_block(ctx, block, refresh);
             if (st != QPR_OK) return st;
@@ -769,6 +770,7 @@ void qpr_destroy(qpr_ctx *ctx) {
 
 qpr_status qpr_create(qpr_ctx **out, int64_t n, int64_t m, const int64_t *src, const int64_t *dst,
                       const double *w, double alpha, double omega, const qpr_options *opt) {
+    qpr::NvtxRange nvtx_range("qpr_create");
     g_create_error.clear();
     if (!out) {
         g_create_error = "out is NULL";
@@ -1197,6 +1199,7 @@ qpr_status qpr_residual(qpr_ctx *ctx, const void *rho, double *resid_out) {
 }
 
 qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps) {
+    qpr::NvtxRange nvtx_range("qpr_evolve");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     qpr_status st = begin_call(ctx);
@@ -1221,6 +1224,7 @@ qpr_status qpr_evolve(qpr_ctx *ctx, void *rho, double dt, int64_t steps) {
 
 qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int64_t max_steps,
                             qpr_stats *out) {
+    qpr::NvtxRange nvtx_range("qpr_steady_state");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
@@ -1256,6 +1260,10 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
         out->kernel_launches = ctx->launches;
         out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    if (qpr::log_enabled())
+        fprintf(stderr, "qpr_steady_state: N=%lld steps=%lld dt=%g residual=%.3e status=%d launches=%lld %.4f s\n",
+                (long long)ctx->n, (long long)c.step, h, c.resid, c.status, (long long)ctx->launches,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     if (c.status == qpr::kCtlNonFinite) return fail(ctx, QPR_E_NONFINITE, "non-finite trace or residual");
     if (c.status != qpr::kCtlConverged)
         return fail(ctx, QPR_E_NOT_CONVERGED, "max_steps reached with residual " + std::to_string(c.resid));
@@ -1263,6 +1271,7 @@ qpr_status qpr_steady_state(qpr_ctx *ctx, void *rho, double dt, double tol, int6
 }
 
 qpr_status qpr_profile_chain(qpr_ctx *ctx, const void *rho, double dt, int32_t reps, double *out_ms) {
+    qpr::NvtxRange nvtx_range("qpr_profile_chain");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     qpr_status st = begin_call(ctx);
@@ -1319,6 +1328,7 @@ qpr_status qpr_profile_chain(qpr_ctx *ctx, const void *rho, double dt, int32_t r
 }
 
 qpr_status qpr_profile_step(qpr_ctx *ctx, const void *rho, double dt, int64_t steps, qpr_profile *out) {
+    qpr::NvtxRange nvtx_range("qpr_profile_step");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     qpr_status st = begin_call(ctx);
@@ -1447,6 +1457,7 @@ qpr_status qpr_populations(qpr_ctx *ctx, const void *rho, double *p, int64_t *ra
 
 qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, double tol, int64_t max_steps,
                      qpr_rkf45_stats *out) {
+    qpr::NvtxRange nvtx_range("qpr_rkf45");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
@@ -1499,6 +1510,7 @@ qpr_status qpr_rkf45(qpr_ctx *ctx, void *rho, const qpr_rkf45_options *opt, doub
 }
 
 qpr_status qpr_pagerank(qpr_ctx *ctx, double tol, int64_t max_iter, double *pi, int64_t *iters) {
+    qpr::NvtxRange nvtx_range("qpr_pagerank");
     if (!ctx) return QPR_E_ARG;
     DeviceGuard dg(ctx->device);
     qpr_status st = begin_call(ctx);

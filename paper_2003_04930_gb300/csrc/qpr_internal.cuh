@@ -7,12 +7,37 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "qpr.h"
 
 namespace qpr {
+
+// A named NVTX range for the length of a scope: every C-ABI call and every
+// block of steps shows up on an Nsight timeline (a no-op when no tool is
+// attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// QPR_LOG=1 in the environment: one line per solve on stderr.
+inline bool log_enabled() {
+    static const bool on = [] {
+        const char *v = getenv("QPR_LOG");
+        return v && v[0] && v[0] != '0';
+    }();
+    return on;
+}
+
 
 struct HostOps;
 

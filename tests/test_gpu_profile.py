@@ -49,3 +49,18 @@ def test_chain_refuses_other_forms_and_bad_arguments():
         with pytest.raises(Q.QprError) as e:
             s.profile_chain(rho, 0.01, reps)
         assert e.value.status == Q.QPR_E_ARG
+
+
+def test_log_line_on_stderr():
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import torch; from paper_2003_04930_gb300 import Solver, graphs; "
+            "g = graphs.heavy_tailed(120, 4); s = Solver.from_edges(g, alpha=0.85, omega=0.8); "
+            "r = torch.from_numpy(graphs.maximally_mixed(120)).to('cuda:0'); s.steady_state(r, 0.01, 1e-6, 100000)")
+    env = dict(os.environ, QPR_LOG="1")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    line = [l for l in out.stderr.splitlines() if l.startswith("qpr_steady_state:")]
+    assert len(line) == 1 and "N=120" in line[0] and "status=" in line[0]
