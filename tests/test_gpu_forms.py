@@ -54,6 +54,22 @@ def test_default_form_is_columns_where_it_fits():
     assert fp64.sparse_form == 0
 
 
+def test_largest_whole_block_against_oracle():
+    # N = 1530 (1536 padded rows): the largest column block a CTA stages
+    # whole (196 KB); the default plan picks the whole-block form there
+    n = 1530
+    g = graphs.heavy_tailed(n, 8)
+    rho0 = graphs.random_density(n, 9, rank=2)
+    ref = Oracle.from_edges(g, alpha=0.85, omega=0.6).evolve(rho0, 0.01, 20)
+    s = Solver.from_edges(g, alpha=0.85, omega=0.6, precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE)
+    assert s.sparse_form == Q.QPR_SPARSE_FORM_COLUMNS and s.sparse_plan["block_cols"] == 16
+    d = torch.from_numpy(rho0.copy()).to(DEV)
+    s.evolve(d, 0.01, 20)
+    got = d.cpu().numpy()
+    _close(got, ref, 1e-6)
+    assert np.abs(got - got.conj().T).max() == 0.0
+
+
 @pytest.mark.parametrize("form", [Q.QPR_SPARSE_FORM_COLUMNS, Q.QPR_SPARSE_FORM_COLUMNS_PERSISTENT])
 def test_whole_block_forms_refused_where_they_do_not_fit(form):
     with pytest.raises(Q.QprError) as e:
