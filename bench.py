@@ -600,6 +600,23 @@ def dense_projection(g, omega, local, rho, dt, steps_conv, peaks, peak_src, prof
             "fp64_peak_tflops": fp64_peak, "peak_source": f"bf16_tflops of {peak_src} x 1.25/2250"}
 
 
+def tc_bf16_stage(g, omega, local, rho, dt, steps_conv, peaks, peak_src, prof_steps=2):
+    """The dense split-BF16 tcgen05 form (the benchmark spec's tensor-core GEMM
+    stage) on the same problem: its stage GEMM's rate against the measured
+    BF16 peak (qpr_profile_step), and its step time times the step count of
+    the solve (projected; the sparse forms are faster on these graphs)."""
+    from paper_2003_04930_gb300 import Solver, qpr
+    st = Solver.from_edges(g, alpha=0.85, omega=omega, backend=qpr.QPR_BACKEND_DENSE, precision=qpr.QPR_MIXED,
+                           device=local)
+    pd = st.profile_step(rho, dt, prof_steps)
+    roof = roofline(st, g, g.n, pd, peaks, peak_src, qpr.QPR_MIXED)
+    st.close()
+    return {"kernel": roof["kernel"], "stage_tflops": roof["achieved"], "frac_of_bf16_peak": roof["frac"],
+            "bf16_peak_tflops": roof["peak"], "peak_source": roof["peak_source"], "launch_ms": pd["product_ms"],
+            "ms_per_rk4_step": pd["step_ms"], "projected_time_to_steady_state_s": pd["step_ms"] * 1e-3 * steps_conv,
+            "projected": True}
+
+
 def timed_solve(s, rho, rho0, a, flush):
     import torch
     rho.copy_(rho0)
@@ -784,6 +801,7 @@ def large_case(a, local, peaks, peak_src, flush):
     out["fp64_sparse"] = fp64_sparse_solve(g, la, local, rho0, rho_solved, flush, warm=False)
     out["plain_fp64_dense"] = dense_projection(g, la.omega, local, rho_solved, la.dt, st["steps"], peaks, peak_src,
                                                prof_steps=1)
+    out["tc_bf16"] = tc_bf16_stage(g, la.omega, local, rho_solved, la.dt, st["steps"], peaks, peak_src)
     best = min(t_cold, ws["value"]) if ws is not None else t_cold
     out["speedup_vs_fp64_sparse"] = out["fp64_sparse"]["time_to_steady_state_s"] / best
     out["speedup_vs_plain_fp64_dense_projected"] = out["plain_fp64_dense"]["projected_time_to_steady_state_s"] / best
