@@ -885,6 +885,8 @@ def run_batch(a):
     probs = [(g, specs[i][1], r) for g, i, r in zip(gs, mine, rho)]
 
     def solve():
+        if not probs:  # more ranks than problems: this rank has none
+            return qpr.QPR_OK, [{"steps": 0, "converged": 0, "kernel_launches": 0}]
         for r, r0 in zip(rho, rho0):
             r.copy_(r0)
         return qpr.batch_steady_state(probs, dt=a.dt, tol=a.tol, max_steps=a.max_steps, ref_refresh=a.ref_refresh,
@@ -912,7 +914,7 @@ def run_batch(a):
     clocks = sampler.stop()
     value, _ = shard_time(sum(times), a.steps, dist, dev)
     steps = [s["steps"] for s in stats]
-    loc = torch.tensor([max(steps), float(np.sum(steps)), len(steps), sum(s["converged"] for s in stats),
+    loc = torch.tensor([max(steps), float(np.sum(steps)), len(probs), sum(s["converged"] for s in stats),
                         int(stats[0]["kernel_launches"])], dtype=torch.float64, device=dev)
     if dist is not None:
         parts = [torch.zeros_like(loc) for _ in range(world)]
