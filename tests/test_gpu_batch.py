@@ -86,3 +86,32 @@ def test_batch_size_classes_and_tile_fallback_bitwise():
         assert s["steps"] == s1["steps"] and s["converged"] == 1, g.n
         assert s["residual"] == s1["residual"]
         np.testing.assert_array_equal(rho.cpu().numpy(), r1.cpu().numpy())
+
+
+def test_batch_tiny_problems_and_a_non_finite_start():
+    # the smallest problems the method has (N = 2, 3: one padded 32 x 32 tile)
+    # beside a regular one, and a problem whose start holds a NaN: the call
+    # reports QPR_E_NONFINITE for the batch, that problem is not converged,
+    # and the others are solved exactly as they are alone
+    specs = [(2, 0.7, 2001), (3, 0.4, 2002), (140, 0.8, 2003), (90, 0.6, 2004)]
+    probs = []
+    for k, (n, om, seed) in enumerate(specs):
+        g = graphs.erdos_renyi(n, 0.6, seed) if n < 10 else graphs.heavy_tailed(n, seed)
+        rho = graphs.maximally_mixed(n)
+        if k == 3:
+            rho[1, 2] = np.nan
+            rho[2, 1] = np.nan
+        probs.append((g, om, torch.from_numpy(rho).to(DEV)))
+    st, stats = Q.batch_steady_state(probs, check=False)
+    assert st == Q.QPR_E_NONFINITE
+    assert stats[3]["converged"] == 0
+    for (g, om, rho), s in zip(probs[:3], stats[:3]):
+        assert s["converged"] == 1
+        single = Solver.from_edges(g, alpha=0.85, omega=om, precision=Q.QPR_MIXED, backend=Q.QPR_BACKEND_SPARSE)
+        r1 = torch.from_numpy(graphs.maximally_mixed(g.n)).to(DEV)
+        s1 = single.steady_state(r1, 0.01, 1e-8, 400000)
+        assert s["steps"] == s1["steps"]
+        np.testing.assert_array_equal(rho.cpu().numpy(), r1.cpu().numpy())
+        ref, steps, _, _ = Oracle.from_edges(g, alpha=0.85, omega=om).steady_state(graphs.maximally_mixed(g.n),
+                                                                                   0.01, 1e-8, 400000)
+        assert np.abs(populations(rho.cpu().numpy()) - populations(ref)).max() <= 1e-7 * populations(ref).max()
