@@ -11,7 +11,9 @@ graphs and programmatic dependent launch.
     graph, at 1e-12 of max |f|);
   * the properties every state keeps at any size: unit trace, exact
     Hermiticity, and for the steady state the exact FP64 residual below the
-    tolerance, with the populations of the FP64 sparse form's steady state.
+    tolerance, with the populations of the FP64 sparse form's steady state;
+  * a short RKF45 trajectory (fifth order, to t = 0.25) against the oracle's
+    RKF45, accepted and rejected attempts within 2.
 """
 import numpy as np
 import pytest
@@ -76,3 +78,22 @@ def test_steady_state_properties_at_n4096(graph):
     assert abs(st64["steps"] - st["steps"]) <= 1
     p, p64 = populations(got), populations(r.cpu().numpy())
     assert np.abs(p - p64).max() <= 1e-7 * p64.max()
+
+
+def test_rkf45_trajectory_at_n4096_against_oracle(graph):
+    # the paper's integrator in the same plan (gather SpMM): a short adaptive
+    # trajectory to t = 0.25 against the oracle's RKF45 (same h0, Tol, h_max)
+    s = Solver.from_edges(graph, alpha=0.85, omega=OMEGA, precision=Q.QPR_MIXED)
+    hmax = s.max_stable_dt
+    rho0 = graphs.random_density(N, 13, rank=2)
+    ref = Oracle.from_edges(graph, alpha=0.85, omega=OMEGA).rkf45(rho0, 0.01, 1e-6, hmax, t_end=0.25,
+                                                                   max_steps=200, order=5)
+    d = torch.from_numpy(rho0.copy()).to(DEV)
+    st = s.rkf45(d, h0=0.01, step_tol=1e-6, h_max=hmax, t_end=0.25, max_steps=200, order=5)
+    assert st["converged"] == 1 and st["t"] == pytest.approx(0.25, rel=1e-14)
+    assert abs(st["accepted"] - ref["accepted"]) <= 2 and abs(st["rejected"] - ref["rejected"]) <= 2
+    got = d.cpu().numpy()
+    p, pr = populations(got), populations(ref["rho"])
+    assert np.linalg.norm(got - ref["rho"]) <= 1e-6
+    assert np.abs(p - pr).max() <= 1e-6 * pr.max()
+    assert np.abs(got - got.conj().T).max() == 0.0
