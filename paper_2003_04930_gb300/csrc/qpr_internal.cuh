@@ -59,7 +59,7 @@ struct Ctl {
     double resid_exact; // exact FP64 residual of the last reference refresh (mixed form)
     long long resid_exact_step;
     int err_timeout;    // a bounded device-side wait gave up
-    int ticket;         // CTAs of the current stage-1 epilogue that finished (column-block form)
+    int ticket;         // CTAs that finished the current ticketed epilogue (a problem's stage 1 in the batch, RKF45 stage 6)
     // FP32 forms of dt for the mixed form's delta stages, written by its
     // refresh: dtf = fl(dt), dt = dtf + dtl as a float-float pair, dt3 =
     // fl(dt / 3)
