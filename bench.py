@@ -390,12 +390,13 @@ def run_ours(a):
                    "d2h_bytes_per_step": 16 * n * n}
     s.close()
 
-    # the other size the metric names, and the batched form
-    if not a.no_large and rank == 0:
+    # the other size the metric names, the batched form and the omega sweep: one-GPU facts, measured in the
+    # N = 1 run only (with N ranks every GPU would wait on rank 0 meanwhile)
+    if not a.no_large and rank == 0 and world == 1:
         line["n4096"] = large_case(a, local, peaks, peak_src, flush)
-    if not a.no_batch and rank == 0:
+    if not a.no_batch and rank == 0 and world == 1:
         line["batch512"] = batch_case(a, local)
-    if not a.no_omega_sweep and rank == 0 and a.n == 922:
+    if not a.no_omega_sweep and rank == 0 and world == 1 and a.n == 922:
         line["omega_sweep"] = omega_sweep(a, local, flush, cpu=a.cpu_omega_sweep and world == 1)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
