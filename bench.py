@@ -602,8 +602,8 @@ def dense_projection(g, omega, local, rho, dt, steps_conv, peaks, peak_src, prof
 
 
 def tc_bf16_stage(g, omega, local, rho, dt, steps_conv, peaks, peak_src, prof_steps=2):
-    """The dense split-BF16 tcgen05 form (the benchmark spec's tensor-core GEMM
-    stage) on the same problem: its stage GEMM's rate against the measured
+    """The dense split-BF16 tcgen05 form (the stage as one tensor-core GEMM
+    of H against the split delta planes) on the same problem: its stage GEMM's rate against the measured
     BF16 peak (qpr_profile_step), and its step time times the step count of
     the solve (projected; the sparse forms are faster on these graphs)."""
     from paper_2003_04930_gb300 import Solver, qpr
