@@ -170,6 +170,7 @@ struct MixedWork {
     double *partials;     // exact residual partials of the refresh
     float *partials32;    // residual-estimate partials of the stage-1 kernel
     int2 *pairs;          // 32 x 32 tile pairs (refresh and sparse stage kernel)
+    int4 *epi_pairs;      // the same pairs in the column-block epilogues' CTA order: {I, J, index in pairs, 0}
     int npairs;
     int tiles;
     Ctl *ctl;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     __shared__ float sg[TS];
     __shared__ int s_done;
     timeline::enter((STAGE - 1) * 2 + 1);
-    const int2 pr = w.pairs[blockIdx.x];
+    const int4 pr = w.epi_pairs[blockIdx.x];  // {I, J, partial slot}
     mixed::EpiIn<STAGE, kENT> in;
     mixed::epi_load<STAGE, kENT>(ops, w, pr.x, pr.y, in);
     tma::grid_dependency_wait();
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(kENT, 3) cols_epi_kernel(DevOps ops, MixedWork
     __syncthreads();
     if (!s_done) {
         // no ticket: the stage-2 SpMM grid takes the stop decision (gain_role)
-        epilogue_pair_staged<STAGE, false>(ops, w, pr.x, pr.y, blockIdx.x, blockIdx.x == 0, w.npairs, sX1, sX2, sg,
-                                           sO, in);
+        epilogue_pair_staged<STAGE, false>(ops, w, pr.x, pr.y, pr.z, blockIdx.x == 0, w.npairs, sX1, sX2, sg, sO,
+                                           in);
     }
     timeline::leave();
 }

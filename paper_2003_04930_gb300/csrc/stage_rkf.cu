@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
     __shared__ float sg[TS];
     __shared__ float red[kENT / 32];
     __shared__ int s_done;
-    const int2 pr = w.pairs[blockIdx.x];
+    const int4 pr = w.epi_pairs[blockIdx.x];  // {I, J, partial slot}: the column forms' epilogue order
     const int I = pr.x, J = pr.y;
     const int cur = read_cur(w);
     RkfIn<S> in;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kENT, 3) rkf_epi_kernel(DevOps ops, MixedWork 
             float acc = red[0];
             for (int q = 1; q < kENT / 32; ++q)
                 acc = (S == 1) ? __fadd_rn(acc, red[q]) : ((red[q] > acc || isnan(red[q])) ? red[q] : acc);
-            w.partials32[blockIdx.x] = (S == 1 && !diag) ? __fmul_rn(2.0f, acc) : acc;
+            w.partials32[pr.z] = (S == 1 && !diag) ? __fmul_rn(2.0f, acc) : acc;
         }
     }
     if (!diag) {
