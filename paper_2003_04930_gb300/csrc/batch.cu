@@ -522,8 +522,6 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     unsigned char *dB = nullptr;
     Ctl *dCtl = nullptr;
     BatchGraph *dG = nullptr;
-    int *dAct = nullptr;
-    int4 *dItems = nullptr;
     double *dIO = nullptr;
     size_t total_pairs = 0;
     for (size_t g = 0; g < G; ++g) total_pairs += npairs[g];
@@ -552,7 +550,7 @@ extern "C" qpr_status qpr_batch_steady_state(int64_t count, const qpr_problem *p
     BCUDA(mem.alloc(&dIO, 2 * max_nn));
     int2 *dKH = nullptr;
     int *dCI = nullptr;
-    int4 *dPC = nullptr, *dItemsA = nullptr, *dItemsB = nullptr, *dItemsT = nullptr;
+    int4 *dPC = nullptr;
     float *dXC = nullptr;
     BCUDA(mem.alloc(&dKH, nkh));
     BCUDA(mem.alloc(&dCI, nci));
