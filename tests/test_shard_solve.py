@@ -1,10 +1,12 @@
 """The plan for sharding one solve over ranks (shard.partition_tile_pairs),
-run as a CPU model with world_size-2 gloo process groups: each rank forms
-the Lindblad right-hand side of Eq. 1 on its own tile pairs from the whole
-stage input, the ranks exchange their tiles (an all-reduce of disjoint
-tiles, i.e. an all-gather) and add their trace and residual partials, and
-one classical RK4 step must equal the oracle's step. The GPU path of this
-plan (NCCL between GB300s) is not built: every machine here has one GPU."""
+run as a CPU model with world_size-2 gloo process groups on the padded
+layout of the GPU forms: each rank forms the Lindblad right-hand side of
+Eq. 1 on its own tile pairs from the whole stage input, the ranks all-gather
+the tiles they wrote (each placing the others' by the plan) and add their
+trace and residual partials. One classical RK4 step must equal the oracle's
+step, the padding must stay zero, and the bytes each rank receives must be
+those shard.stage_exchange_bytes gives. The GPU path of this plan (NCCL
+between GB300s) is not built: every machine here has one GPU."""
 import os
 import sys
 
@@ -41,26 +43,50 @@ def _rank(rank, world, port, out):
     try:
         g = graphs.heavy_tailed(N, 12)
         o = Oracle.from_edges(g, alpha=ALPHA, omega=OMEGA)
-        _, H, G, c = o.operators()
+        _, H0, G0, c0 = o.operators()
+        # the padded layout of the GPU forms: np_ a multiple of the tile, zero rows and columns beyond N
         np_ = ((N + TILE - 1) // TILE) * TILE
-        mine = shard.partition_tile_pairs(np_, world, tile=TILE)[rank]
-        sl = lambda t: slice(t * TILE, min((t + 1) * TILE, N))
+        H = np.zeros((np_, np_)); H[:N, :N] = H0
+        G = np.zeros((np_, np_)); G[:N, :N] = G0
+        c = np.zeros(np_); c[:N] = c0
+        parts = shard.partition_tile_pairs(np_, world, tile=TILE)
+        mine = parts[rank]
+        sl = lambda t: slice(t * TILE, (t + 1) * TILE)
 
-        def gather(local):  # disjoint tiles from every rank: the all-gather of the plan
-            t = torch.from_numpy(local.view(np.float64).copy())
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            return t.numpy().view(np.complex128).reshape(N, N)
+        def written(pairs):  # the tiles a rank writes, in its order: (I, J) and the mirror (J, I)
+            return [t for i, j in pairs for t in ([(i, j)] if i == j else [(i, j), (j, i)])]
+
+        owned = [written(p) for p in parts]
+        slots = max(len(t) for t in owned)
+
+        def gather(kpad):
+            # the plan's all-gather: every rank sends the tiles it wrote (padded to a common count)
+            # and places every other rank's tiles by the plan; returns the whole matrix and the
+            # bytes of tiles this rank received
+            buf = np.zeros((slots, TILE, TILE), dtype=np.complex128)
+            for q, (i, j) in enumerate(owned[rank]):
+                buf[q] = kpad[sl(i), sl(j)]
+            t = torch.from_numpy(buf.view(np.float64).copy())
+            bufs = [torch.empty_like(t) for _ in range(world)]
+            dist.all_gather(bufs, t)
+            full = np.zeros((np_, np_), dtype=np.complex128)
+            received = 0
+            for r in range(world):
+                b = bufs[r].numpy().view(np.complex128)
+                for q, (i, j) in enumerate(owned[r]):
+                    full[sl(i), sl(j)] = b[q]
+                if r != rank:
+                    received += len(owned[r]) * TILE * TILE * 16
+            return full, received
 
         def f_tiles(y):
             # this rank's tiles of f(y) (Eq. 1 with L_ij = sqrt(G_ij) |i><j|): the commutator from
             # X_IJ = H_I. y_.J and X_JI, the dissipator from diag(G p) and the column sums c
-            k = np.zeros((N, N), dtype=np.complex128)
+            k = np.zeros((np_, np_), dtype=np.complex128)
             gp = G @ np.real(np.diag(y))
             res = 0.0
             for i, j in mine:
                 a, b = sl(i), sl(j)
-                if a.start >= N or b.start >= N:
-                    continue
                 xij = H[a, :] @ y[:, b]
                 xji = H[b, :] @ y[:, a]
                 kij = -1j * (1 - OMEGA) * (xij - xji.conj().T) - OMEGA * 0.5 * (c[a][:, None] + c[b][None, :]) * y[a, b]
@@ -72,24 +98,27 @@ def _rank(rank, world, port, out):
                     k[b, a] = kij.conj().T
             return k, res
 
-        y = graphs.random_density(N, 5, rank=3)
+        y0 = graphs.random_density(N, 5, rank=3)
+        y = np.zeros((np_, np_), dtype=np.complex128); y[:N, :N] = y0
         # residual partials of the start: ||f(y)||_F^2 summed over the ranks
         k1, r = f_tiles(y)
         rt = torch.tensor([r], dtype=torch.float64)
         dist.all_reduce(rt, op=dist.ReduceOp.SUM)
-        k1 = gather(k1)
-        k2 = gather(f_tiles(y + 0.5 * DT * k1)[0])
-        k3 = gather(f_tiles(y + 0.5 * DT * k2)[0])
-        k4 = gather(f_tiles(y + DT * k3)[0])
+        k1, received = gather(k1)
+        k2 = gather(f_tiles(y + 0.5 * DT * k1)[0])[0]
+        k3 = gather(f_tiles(y + 0.5 * DT * k2)[0])[0]
+        k4 = gather(f_tiles(y + DT * k3)[0])[0]
         yn = y + DT / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
         # the trace renormalisation from the diagonal tiles' partials
-        tr = sum(float(np.real(np.trace(yn[sl(i), sl(i)]))) for i, j in mine if i == j and sl(i).start < N)
+        tr = sum(float(np.real(np.trace(yn[sl(i), sl(i)]))) for i, j in mine if i == j)
         tt = torch.tensor([tr], dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         yn = yn / float(tt.item())
-        ref = o.evolve(y, DT, 1)
-        out[rank] = (float(np.abs(yn - ref).max()), float(np.sqrt(rt.item())), o.residual(y),
-                     float(np.abs(k1 - o.rhs(y)).max()))
+        ref = o.evolve(y0, DT, 1)
+        plan_bytes = shard.stage_exchange_bytes(np_, world, tile=TILE, element_bytes=16)[rank]
+        out[rank] = (float(np.abs(yn[:N, :N] - ref).max()), float(np.sqrt(rt.item())), o.residual(y0),
+                     float(np.abs(k1[:N, :N] - o.rhs(y0)).max()), float(np.abs(yn[N:, :]).max(initial=0.0)),
+                     received, plan_bytes)
     finally:
         dist.destroy_process_group()
 
@@ -99,7 +128,9 @@ def test_sharded_rk4_step_equals_the_oracle():
     out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, 29781, out), nprocs=world, join=True)
     for r in range(world):
-        step_err, resid, resid_ref, rhs_err = out[r]
+        step_err, resid, resid_ref, rhs_err, pad, received, plan_bytes = out[r]
         assert rhs_err <= 1e-13
         assert step_err <= 1e-14
         assert resid == pytest.approx(resid_ref, rel=1e-12)
+        assert pad == 0.0  # the padding stays zero
+        assert received == plan_bytes > 0  # the exchange moves what the plan says
